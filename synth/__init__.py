@@ -1,0 +1,173 @@
+"""Seeded synthetic image stacks shaped like the paper's DDM workloads.
+
+The paper measured 16-bit microscopy image sets of up to 2^14 frames (Sec. 2); those sets
+are not available, so these generators stand in for them.  This module is shared by the
+oracle side and the CUDA side as *input only*: it holds none of the structure-function
+arithmetic, and every random number is drawn here, on the host, from numpy's PCG64.
+
+Two families:
+
+* :func:`ou_stack` -- a real random field whose every Fourier mode is an independent complex
+  Ornstein-Uhlenbeck process with rate Gamma(q) = D0 q^2 and stationary power S(q), plus
+  white pixel noise sigma.  For the unnormalised spatial DFT it gives
+  E[D(q, dt)] = H W (2 S(q) (1 - exp(-Gamma(q) dt)) + 2 sigma^2), which the oracle tests use.
+* :func:`blob_stack` -- Brownian Gaussian particles on a periodic field, a background that
+  makes the frame mean ``mean``, Poisson shot noise, clamping to 12 bits, uint16 output.
+  Options cover two species, a log-normal spread of D0 and a slow illumination drift.
+
+|q| is in rad/px: q = 2 pi sqrt((ky'/H)^2 + (kx'/W)^2) with signed DFT indices ky', kx'.
+"""
+from __future__ import annotations
+
+import math
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+
+def q_magnitude(H: int, W: int) -> np.ndarray:
+    """|q| [H, W] in rad/px for DFT indices in numpy order."""
+    ky = np.fft.fftfreq(H) * 2.0 * np.pi
+    kx = np.fft.fftfreq(W) * 2.0 * np.pi
+    return np.sqrt(ky[:, None] ** 2 + kx[None, :] ** 2)
+
+
+def gaussian_spectrum(width: float):
+    """S(q) = exp(-q^2 / (2 width^2))."""
+    return lambda q: np.exp(-(q ** 2) / (2.0 * width ** 2))
+
+
+def power_law_spectrum(q_cut: float = 0.02):
+    """S(q) = 1 / max(q, q_cut)^2."""
+    return lambda q: 1.0 / np.maximum(q, q_cut) ** 2
+
+
+def ou_stack(H: int, W: int, N: int, D0: float, spectrum, sigma: float, seed: int,
+             dtype=np.float32) -> np.ndarray:
+    """Fourier-mode Ornstein-Uhlenbeck stack, [N, H, W] of ``dtype``.
+
+    G(k, 0) ~ CN(0, S); G(k, t+1) = e^{-Gamma} G(k, t) + sqrt(S (1 - e^{-2 Gamma})) xi_t with
+    E|xi|^2 = 1, independently for every k; the frame is sqrt(2) Re(IDFT_ortho(G_t)) plus
+    N(0, sigma^2) pixel noise.  D0 may be a float or a callable ``rng -> float``.
+    """
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), 0x0A1])))
+    if callable(D0):
+        D0 = float(D0(rng))
+    q = q_magnitude(H, W)
+    S = np.asarray(spectrum(q), dtype=np.float64)
+    gamma = D0 * q ** 2
+    decay = np.exp(-gamma)
+    drive = np.sqrt(S * (1.0 - np.exp(-2.0 * gamma)))
+
+    def cnormal():
+        return (rng.standard_normal((H, W)) + 1j * rng.standard_normal((H, W))) / math.sqrt(2.0)
+
+    G = np.sqrt(S) * cnormal()
+    out = np.empty((N, H, W), dtype=dtype)
+    for t in range(N):
+        if t > 0:
+            G = decay * G + drive * cnormal()
+        field = math.sqrt(2.0) * np.fft.ifft2(G, norm="ortho").real
+        if sigma > 0:
+            field = field + sigma * rng.standard_normal((H, W))
+        out[t] = field.astype(dtype)
+    return out
+
+
+def ou_params(D0: float, spectrum_width: float):
+    """Parameters of the small OU workload: 64x64 float32, N = 128."""
+    return dict(D0=D0, spectrum=gaussian_spectrum(spectrum_width))
+
+
+def _profile(H_or_W: int, centres: np.ndarray, sigma: float, reach: int) -> tuple:
+    """Sparse periodic 1D Gaussian profiles: rows, columns and values for every particle.
+
+    The profile of a particle at u0 is exp(-d(u, u0)^2 / (2 sigma^2)) for the periodic
+    (minimum-image) distance d <= reach pixels, and zero further away.
+    """
+    P = centres.shape[0]
+    base = np.floor(centres).astype(np.int64)
+    offs = np.arange(-reach, reach + 1, dtype=np.int64)
+    idx = base[:, None] + offs[None, :]
+    d = idx.astype(np.float64) - centres[:, None]
+    vals = np.exp(-(d ** 2) / (2.0 * sigma ** 2))
+    vals[np.abs(d) > reach] = 0.0
+    rows = np.repeat(np.arange(P), offs.size)
+    return rows, np.mod(idx, H_or_W).ravel(), vals.ravel()
+
+
+def blob_stack(H: int, W: int, N: int, n_particles: int, sigma_px: float, D0, seed: int,
+               mean: float = 2000.0, amplitude: float = 1000.0, max_count: int = 4095,
+               drift: float = 0.0, threads: int | None = None) -> np.ndarray:
+    """Brownian Gaussian-blob stack with Poisson noise, [N, H, W] uint16.
+
+    D0: a float (one species), or an array of per-particle D0 (px^2/frame).  Each frame
+    step moves every particle by N(0, 2 D0) px per axis, with periodic wrap.  The
+    expected frame is bg + amplitude * sum_p g_y(p) g_x(p) with bg chosen so the mean is
+    ``mean``; drift multiplies frame t by 1 + drift * t / (N - 1) (illumination ramp);
+    counts are Poisson, clamped to ``max_count``.
+    """
+    ss = np.random.SeedSequence([int(seed), 0xB10B])
+    rng = np.random.Generator(np.random.PCG64(ss.spawn(1)[0]))
+    P = int(n_particles)
+    d0 = np.broadcast_to(np.asarray(D0, dtype=np.float64), (P,)).copy()
+    start = rng.uniform(0.0, 1.0, size=(P, 2)) * np.array([H, W], dtype=np.float64)
+    steps = rng.standard_normal((N, P, 2)) * np.sqrt(2.0 * d0)[None, :, None]
+    steps[0] = 0.0
+    pos = start[None] + np.cumsum(steps, axis=0)
+    pos[..., 0] = np.mod(pos[..., 0], H)
+    pos[..., 1] = np.mod(pos[..., 1], W)
+    reach = int(math.ceil(4.0 * sigma_px))
+    bg = mean - P * amplitude * (2.0 * math.pi * sigma_px ** 2) / float(H * W)
+    frame_seeds = ss.spawn(N + 1)[1:]
+    out = np.empty((N, H, W), dtype=np.uint16)
+
+    def render(t):
+        ry, cy, vy = _profile(H, pos[t, :, 0], sigma_px, reach)
+        rx, cx, vx = _profile(W, pos[t, :, 1], sigma_px, reach)
+        Gy = np.zeros((P, H), np.float32)
+        Gx = np.zeros((P, W), np.float32)
+        np.add.at(Gy, (ry, cy), vy.astype(np.float32))
+        np.add.at(Gx, (rx, cx), vx.astype(np.float32))
+        lam = (amplitude * (Gy.T @ Gx)).astype(np.float64) + bg
+        if drift:
+            lam *= 1.0 + drift * t / max(N - 1, 1)
+        np.maximum(lam, 0.0, out=lam)
+        r = np.random.Generator(np.random.PCG64(frame_seeds[t]))
+        counts = r.poisson(lam)
+        np.minimum(counts, max_count, out=counts)
+        out[t] = counts.astype(np.uint16)
+
+    n_threads = threads or min(16, os.cpu_count() or 1)
+    if n_threads <= 1 or N < 4:
+        for t in range(N):
+            render(t)
+    else:
+        with ThreadPoolExecutor(max_workers=n_threads) as ex:
+            list(ex.map(render, range(N)))
+    return out
+
+
+def lognormal_d0(n: int, median: float, sigma_ln: float, seed: int) -> np.ndarray:
+    """Per-particle D0 drawn log-normally (polydisperse sample)."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), 0x1D0])))
+    return median * np.exp(sigma_ln * rng.standard_normal(n))
+
+
+def two_species_d0(n: int, d_a: float, d_b: float) -> np.ndarray:
+    """Half the particles with D0 = d_a, half with d_b."""
+    d = np.full(n, d_a, dtype=np.float64)
+    d[n // 2:] = d_b
+    return d
+
+
+# Workloads named by what they are, with their sizes.
+def ou_64x64x128(seed: int = 0) -> np.ndarray:
+    """64x64 float32, N = 128, D0 = 0.5, S = exp(-q^2 / (2 * 0.3^2)), sigma = 0.01."""
+    return ou_stack(64, 64, 128, 0.5, gaussian_spectrum(0.3), 0.01, seed)
+
+
+def blobs_512x512x1024(seed: int = 0, N: int = 1024, H: int = 512, W: int = 512) -> np.ndarray:
+    """512x512 uint16, N = 1024, 3000 blobs (sigma 2 px), D0 = 0.2, mean 2000, Poisson."""
+    return blob_stack(H, W, N, 3000, 2.0, 0.2, seed)
