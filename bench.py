@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Frames/s to the full structure function D(q, dt) of a 512x512 uint16 stack, N = 1024.
+
+One step = one pass of the whole D path through the C ABI on one synthetic stack:
+  ddm_spatial_fft   (step one: real-to-complex 2D DFT of every frame, 2 kernels)
+  ddm_temporal_sf   (step two: per-q power sums + zero-padded transform in time, 1 kernel)
+  ddm_azimuthal_average (radial average over 362 |q| bins, 1 kernel)
+The frames (537 MB) and the spectrum (1.08 GB) are larger than L2, so no flush is needed
+between timed steps.
+
+Prints ONE JSON line.  --impl reference times the FP64 CPU oracle instead, on a bounded
+sample of the same workload (one kx column of the spectrum, every ky, every lag),
+extrapolated linearly in the number of wave vectors.
+Under torchrun (N > 1) every rank processes its own stack (independent replicas, weak
+scaling, no collective on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+H = W = 512
+N_FRAMES = 1024
+N_BINS = 362
+WORKLOAD = "blobs_512x512x1024_u16"
+METRIC = "frames/s to full D(q,Δt) at 512²×1024, % of HBM roofline, max rel err vs FP64"
+FALLBACK_HBM_GBS = 6400.0
+N_Q = H * (W // 2 + 1)
+SPATIAL_BYTES = N_FRAMES * H * W * 2 + N_Q * N_FRAMES * 8      # read frames, write spectrum
+TEMPORAL_BYTES = N_Q * N_FRAMES * 8 + N_Q * N_FRAMES * 4       # read spectrum, write D
+STEP_BYTES = SPATIAL_BYTES + TEMPORAL_BYTES
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("ddm_temporal.cu", "ddm_fft.cuh"):
+        with open(os.path.join(ROOT, "paper_2012_05695_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the temporal kernel from the committed ncu summary, or None
+    when the kernel source changed since that capture."""
+    p = os.path.join(ROOT, "profiles", "temporal_sf_512x512x1024.md")
+    if not os.path.exists(p):
+        return None
+    src = None
+    bytes_ = None
+    for line in open(p):
+        if line.startswith("source_sha256_16:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            bytes_ = float(line.split(":", 1)[1].strip())
+    if src != kernel_source_hash():
+        return None
+    return bytes_
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 50 ms) while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        return time.time()
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.12)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [l for (ts, l) in self.lines if t0 - 0.06 <= ts <= t1 + 0.06]
+        if not rows and self.lines:
+            rows = [min(self.lines, key=lambda x: abs(x[0] - (t0 + t1) / 2))[1]]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            parts = [p.strip() for p in r.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(frames, cols, nthreads):
+    """Run the FP64 oracle on kx columns `cols` (every ky, every lag); returns (seconds, D, s_q)."""
+    import oracle
+    t0 = time.perf_counter()
+    D, s_q = oracle.structure_function(frames, kx_sel=cols, nthreads=nthreads)
+    return time.perf_counter() - t0, D, s_q
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    oracle.build()
+    frames = synth.blobs_512x512x1024(seed=args.seed)
+    cores = os.cpu_count() or 1
+    cols = [1]
+    times = []
+    for k in range(args.warmup + args.steps):
+        t, _, _ = oracle_sample(frames, cols, cores)
+        if k >= args.warmup:
+            times.append(t)
+    t_step = sum(times) / len(times)
+    q_sample = H * len(cols)
+    t_full = t_step * N_Q / q_sample
+    value = N_FRAMES / t_full
+    sample = (f"{len(cols)} kx column x {H} ky x {N_FRAMES} frames x all lags per step "
+              f"({q_sample} of {N_Q} wave vectors); frames/s extrapolated linearly in the q count")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "N": N_FRAMES, "n_bins": N_BINS},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2012_05695_b300 as ddm
+    import synth
+
+    frames_np = synth.blobs_512x512x1024(seed=args.seed + rank)
+    plan = ddm.Plan(H, W, N_FRAMES, dtype="u16", n_bins=N_BINS)
+    dev = torch.device("cuda", local)
+    frames = torch.from_numpy(frames_np).to(dev)
+    spec = torch.empty(2 * N_FRAMES * plan.n_q, dtype=torch.float32, device=dev)
+    D = torch.empty(plan.n_q * N_FRAMES, dtype=torch.float32, device=dev)
+    Dr = torch.empty(N_BINS * N_FRAMES, dtype=torch.float32, device=dev)
+    counts = torch.empty(N_BINS, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        plan.spatial_fft(frames, spec, stream)
+        if ev:
+            ev[1].record(stream)
+        plan.temporal_sf(spec, D, stream)
+        if ev:
+            ev[2].record(stream)
+        plan.azimuthal_average(D, Dr, counts, stream)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = clk.mark()
+        start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        end.record(stream)
+        torch.cuda.synchronize()
+        t1 = clk.mark()
+        if dist:
+            dist.barrier()
+    clocks = clk.summary(t0, t1)
+    ms_total = start.elapsed_time(end)
+    if dist:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    sp_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    tm_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    rd_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / args.steps
+    n_gpus = ws
+    value = n_gpus * N_FRAMES * args.steps / (ms_total / 1e3)
+    peak, peak_kind = measured_peaks()
+
+    # ---- end to end through the public API: pinned host frames in, radial average out
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(frames_np).pin_memory()
+        Dr_host = torch.empty(N_BINS * N_FRAMES, dtype=torch.float32).pin_memory()
+        frames_e2e = torch.empty_like(frames)
+
+        def e2e_step():
+            frames_e2e.copy_(host, non_blocking=True)
+            plan.structure_function(frames_e2e, D, stream)
+            plan.azimuthal_average(D, Dr, counts, stream)
+            Dr_host.copy_(Dr, non_blocking=True)
+
+        for _ in range(max(2, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        k_e2e = max(3, min(args.steps, 20))
+        if dist:
+            dist.barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(k_e2e):
+            e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = s0.elapsed_time(s1)
+        if dist:
+            tt = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": n_gpus * N_FRAMES * k_e2e / (e_ms / 1e3), "unit": "frames/s",
+               "h2d_bytes_per_step": int(host.numel() * host.element_size()),
+               "d2h_bytes_per_step": int(Dr_host.numel() * Dr_host.element_size()),
+               "steps": k_e2e}
+
+    # ---- FP64 oracle on a bounded sample: CPU baseline and max scaled error of this run
+    cpu = None
+    max_err = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        cols = [1, 200]
+        t_s, D_or, s_q = oracle_sample(frames_np, cols, cores)
+        q_sample = H * len(cols)
+        cpu_value = N_FRAMES / (t_s * N_Q / q_sample)
+        cpu = {"value": cpu_value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(cols)} kx columns x {H} ky x {N_FRAMES} frames x all lags "
+                         f"({q_sample} of {N_Q} wave vectors), {t_s:.1f} s; frames/s extrapolated "
+                         f"linearly in the q count"}
+        plan.structure_function(frames, D, stream)
+        torch.cuda.synchronize()
+        Dg = D.view(H, W // 2 + 1, N_FRAMES)[:, cols, :].cpu().numpy()
+        max_err = oracle.scaled_error(Dg, D_or, s_q)
+
+    traffic = profiled_traffic()
+    tm_achieved = TEMPORAL_BYTES / (tm_ms / 1e3) / 1e9
+    sp_achieved = SPATIAL_BYTES / (sp_ms / 1e3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": n_gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "N": N_FRAMES, "n_bins": N_BINS,
+                   "frames": "uint16 Brownian Gaussian blobs (3000, sigma 2 px, D0 0.2), mean 2000, Poisson",
+                   "l2": "inputs larger than L2 (frames 537 MB, spectrum 1.08 GB): no flush",
+                   "parallelism": f"replicas x{n_gpus}"},
+        "roofline": {"kernel": "temporal_sf_kernel", "bound": "hbm",
+                     "achieved": tm_achieved, "peak": peak, "unit": "GB/s",
+                     "frac": tm_achieved / peak, "peak_kind": peak_kind,
+                     "traffic": traffic, "algorithmic_bytes": TEMPORAL_BYTES},
+        "stages_ms": {"spatial_fft": sp_ms, "temporal_sf": tm_ms, "azimuthal_average": rd_ms},
+        "step_roofline": {"algorithmic_bytes": STEP_BYTES,
+                          "achieved_gbs": STEP_BYTES / ((sp_ms + tm_ms) / 1e3) / 1e9,
+                          "frac": STEP_BYTES / ((sp_ms + tm_ms) / 1e3) / 1e9 / peak,
+                          "spatial_gbs": sp_achieved, "spatial_frac": sp_achieved / peak},
+        "max_rel_err": max_err,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+    }
+    if e2e:
+        out["e2e"] = e2e
+    if cpu:
+        out["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

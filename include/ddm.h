@@ -1,0 +1,153 @@
+/*
+ * ddm.h -- C ABI of the B300 (sm_103a) DDM structure-function library.
+ *
+ * Computes the image structure function of Differential Dynamic Microscopy,
+ *
+ *     D(q, m) = 1/(N - m) * sum_{t=0}^{N-1-m} |F(q, t+m) - F(q, t)|^2 ,   m = 0 .. N-1,
+ *
+ * (Eq. 1 of Norouzisadeh, Cerchiari, Croccolo, arXiv 2012.05695, read with the lag index
+ * on both frames), where F(q, t) is the unnormalised 2D DFT of frame t (Sec. 2).  The lags
+ * are obtained as in the paper's WITH_FT scheme (Sec. 2, App. B): per wave vector, the
+ * power terms come from running sums of |F|^2 (Eqs. B1, B3) and the cross term from the
+ * autocorrelation obtained by zero-padding the time sequence to N_2 = 2^(ceil(log2 N) + 1)
+ * points (Eq. B4), a transform in time, the squared modulus and an inverse transform.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Frames are row-major [N][H][W] (uint16 or float32).  Wave vectors are stored on the
+ *    real-to-complex half plane: q = ky * (W/2 + 1) + kx with ky = 0..H-1 (DFT order,
+ *    ky >= H/2 means negative) and kx = 0..W/2; n_q = H * (W/2 + 1).  D(-q) = D(q).
+ *  * D is float32 [n_q][N] (lag contiguous), D[q][0] = 0 exactly.
+ *  * All array pointers are DEVICE pointers owned by the caller unless stated otherwise;
+ *    `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  * Calls are asynchronous on `stream`.  Argument errors are returned synchronously and
+ *    nothing is enqueued.  Errors found by a kernel (a non-finite intermediate) are
+ *    recorded in a plan status word readable with ddm_plan_last_device_status() after the
+ *    stream has been synchronised.  No C++ exception crosses this boundary.
+ *  * A plan may be used from one host thread at a time; different plans are independent.
+ */
+#ifndef DDM_B300_H
+#define DDM_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DDM_ABI_VERSION 1
+
+typedef enum ddm_status {
+    DDM_OK = 0,
+    DDM_ERR_INVALID_ARG = 1,   /* bad pointer, size or descriptor field */
+    DDM_ERR_UNSUPPORTED = 2,   /* legal request this build does not implement */
+    DDM_ERR_OOM = 3,           /* device allocation failed or exceeds max_workspace_bytes */
+    DDM_ERR_CUDA = 4,          /* a CUDA runtime call failed (no device, launch error) */
+    DDM_ERR_TIMEOUT = 5,       /* reserved: a bounded device wait gave up */
+    DDM_ERR_NUMERIC = 6,       /* a kernel met a non-finite value */
+    DDM_ERR_NO_WORKSPACE = 7   /* reserved */
+} ddm_status;
+
+typedef enum ddm_dtype { DDM_IN_U16 = 0, DDM_IN_F32 = 1 } ddm_dtype;
+
+/* Arithmetic of the structure-function path.  Both tiers transform in FP32. */
+typedef enum ddm_precision {
+    DDM_PREC_FP32 = 0,   /* FP32 transforms, prefix and suffix sums and combination */
+    DDM_PREC_FP32_FP64FIX = 1 /* as FP32, plus: lags 1..fix_lags recomputed by direct
+                                 differences with FP64 accumulation (cancellation-free) */
+} ddm_precision;
+
+typedef struct ddm_plan_desc {
+    int H, W;          /* frame height and width in pixels (powers of two, 2..1024) */
+    int N;             /* number of frames, 1 .. 1024 */
+    int dtype;         /* ddm_dtype */
+    int precision;     /* ddm_precision */
+    int M;             /* temporal pad length; 0 = N_2 of Eq. B4.  Any M >= 2N-1 gives
+                          the same D (App. B); this build accepts 0 or N_2 and returns
+                          DDM_ERR_INVALID_ARG for M < 2N-1, DDM_ERR_UNSUPPORTED otherwise */
+    int n_bins;        /* radial bins for ddm_azimuthal_average (0 = no radial stage) */
+    int subtract_ref;  /* 1: subtract frame 0 from every frame before the spatial
+                          transform (exact in integers for uint16; D is unchanged by it) */
+    int fix_lags;      /* DDM_PREC_FP32_FP64FIX: number of leading lags recomputed (0 = 8) */
+    size_t max_workspace_bytes; /* 0 = no limit; else plan creation fails with
+                                   DDM_ERR_OOM if the workspace would exceed it */
+} ddm_plan_desc;
+
+typedef struct ddm_plan_s* ddm_plan;
+
+/* Library version of this header's ABI. */
+int ddm_abi_version(void);
+
+/* Static, never NULL. */
+const char* ddm_status_string(ddm_status s);
+
+/* Fill *desc with defaults for an H x W x N stack (uint16, FP32 tier, M = N_2,
+ * n_bins = 0, subtract_ref = 1). */
+ddm_status ddm_plan_desc_init(ddm_plan_desc* desc, int H, int W, int N);
+
+/* Validate *desc and create a plan on the current CUDA device.  The plan owns host
+ * metadata, small device tables (twiddles, radial bin map) and -- unless a workspace is
+ * attached with ddm_plan_set_workspace() before the first call that needs it -- the
+ * spectrum workspace.  *out is NULL on failure. */
+ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc);
+
+/* Release everything the plan owns.  NULL is accepted.  The caller must make sure no
+ * work enqueued with the plan is still running. */
+ddm_status ddm_plan_destroy(ddm_plan p);
+
+/* Bytes of device workspace ddm_structure_function needs (the spectrum store,
+ * n_q * N complex64, 256-byte aligned). */
+ddm_status ddm_plan_workspace_size(ddm_plan p, size_t* bytes);
+
+/* Attach a caller-owned device workspace of at least ddm_plan_workspace_size() bytes,
+ * 256-byte aligned.  Frees a workspace the plan allocated itself.  The caller keeps
+ * ownership and must keep it alive while work is enqueued. */
+ddm_status ddm_plan_set_workspace(ddm_plan p, void* dev_ptr, size_t bytes);
+
+/* n_q = H * (W/2 + 1), the number of stored wave vectors. */
+ddm_status ddm_plan_n_q(ddm_plan p, int64_t* n_q);
+
+/* Kernel-detected status of the last completed call on this plan (DDM_OK or
+ * DDM_ERR_NUMERIC); reading it resets it to DDM_OK.  Synchronise the stream first. */
+ddm_status ddm_plan_last_device_status(ddm_plan p, ddm_status* out);
+
+/* ---- the hot path ---------------------------------------------------------------- */
+
+/* Step one of Sec. 2: the real-to-complex 2D DFT of every frame (after subtracting
+ * frame 0 when desc.subtract_ref is set).
+ *   frames   [N][H][W] uint16 or float32 (desc.dtype), device
+ *   spectrum [N][n_q] complex64 (interleaved re, im), device, written
+ * Unnormalised: F(ky, kx) = sum_{y,x} I(y, x) exp(-2 pi i (ky y / H + kx x / W)). */
+ddm_status ddm_spatial_fft(ddm_plan p, const void* frames, float* spectrum, void* stream);
+
+/* Step two of Sec. 2 with the App. B scheme, on a spectrum laid out as
+ * ddm_spatial_fft writes it:
+ *   spectrum [N][n_q] complex64, device, read only
+ *   D        [n_q][N] float32, device, written
+ * Per wave vector q: remove the time mean of F(q, .) (D is unchanged by any constant),
+ * P1(m) = sum_{t < N-m} |F|^2 and P2(m) = sum_{t >= m} |F|^2 (Eqs. B1, B3), Re C(m) by the
+ * zero-padded transform in time (Eq. B4), D = (P1 + P2 - 2 Re C) / (N - m). */
+ddm_status ddm_temporal_sf(ddm_plan p, const float* spectrum, float* D, void* stream);
+
+/* Both steps: frames [N][H][W] -> D [n_q][N].  Uses the plan's workspace for the
+ * spectrum (allocated on first use if none is attached). */
+ddm_status ddm_structure_function(ddm_plan p, const void* frames, float* D, void* stream);
+
+/* Radial (azimuthal) average over |q| bins -- not in the paper.
+ *   D      [n_q][N] float32, device (as written above)
+ *   Dr     [n_bins][N] float32, device, written: mean of D over the FULL-plane modes of
+ *          each bin (half-plane modes with 0 < kx < W/2 count twice); 0 for empty bins
+ *   counts [n_bins] int32, device, written (may be NULL): full-plane modes per bin
+ * Bins: |q| = 2 pi sqrt((ky'/H)^2 + (kx'/W)^2) rad/px (signed ky', kx'), n_bins uniform
+ * bins over [0, pi sqrt 2], b = min(floor(|q| n_bins / (pi sqrt 2)), n_bins - 1), the floor
+ * evaluated exactly in integers.  Summation order is fixed: results are bitwise
+ * reproducible run to run.  Needs desc.n_bins > 0. */
+ddm_status ddm_azimuthal_average(ddm_plan p, const float* D, float* Dr, int* counts,
+                                 void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDM_B300_H */

@@ -1,0 +1,228 @@
+"""ctypes binding of the C ABI in include/ddm.h (argument marshalling only).
+
+Every entry point keeps its C name.  Arrays are torch CUDA tensors (PyTorch provides the
+device memory and streams); the binding checks shape, dtype, device and contiguity, passes
+raw pointers, and turns a non-OK status into :class:`DDMError`.  There is no fallback: if
+the shared library is missing this module raises on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libddm_b300.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "ddm.h")
+
+DDM_OK = 0
+DDM_ERR_INVALID_ARG = 1
+DDM_ERR_UNSUPPORTED = 2
+DDM_ERR_OOM = 3
+DDM_ERR_CUDA = 4
+DDM_ERR_TIMEOUT = 5
+DDM_ERR_NUMERIC = 6
+DDM_ERR_NO_WORKSPACE = 7
+
+DDM_IN_U16 = 0
+DDM_IN_F32 = 1
+DDM_PREC_FP32 = 0
+DDM_PREC_FP32_FP64FIX = 1
+
+
+class DDMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+class ddm_plan_desc(ctypes.Structure):
+    _fields_ = [
+        ("H", ctypes.c_int), ("W", ctypes.c_int), ("N", ctypes.c_int),
+        ("dtype", ctypes.c_int), ("precision", ctypes.c_int), ("M", ctypes.c_int),
+        ("n_bins", ctypes.c_int), ("subtract_ref", ctypes.c_int), ("fix_lags", ctypes.c_int),
+        ("max_workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libddm_b300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, c_int, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+    sigs = {
+        "ddm_abi_version": (c_int, []),
+        "ddm_status_string": (ctypes.c_char_p, [st]),
+        "ddm_plan_desc_init": (st, [ctypes.POINTER(ddm_plan_desc), c_int, c_int, c_int]),
+        "ddm_plan_create": (st, [ctypes.POINTER(vp), ctypes.POINTER(ddm_plan_desc)]),
+        "ddm_plan_destroy": (st, [vp]),
+        "ddm_plan_workspace_size": (st, [vp, ctypes.POINTER(ctypes.c_size_t)]),
+        "ddm_plan_set_workspace": (st, [vp, vp, ctypes.c_size_t]),
+        "ddm_plan_n_q": (st, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "ddm_plan_last_device_status": (st, [vp, ctypes.POINTER(ctypes.c_int)]),
+        "ddm_spatial_fft": (st, [vp, vp, vp, vp]),
+        "ddm_temporal_sf": (st, [vp, vp, vp, vp]),
+        "ddm_structure_function": (st, [vp, vp, vp, vp]),
+        "ddm_azimuthal_average": (st, [vp, vp, vp, vp, vp]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/ddm.h declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ddm_[a-z0-9_]+)\s*\(", text)))
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().ddm_status_string(int(s)).decode()
+    except Exception:
+        return "status %d" % int(s)
+
+
+def _check(status: int, where: str):
+    if status != DDM_OK:
+        raise DDMError(status, where)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _dev_ptr(t, what, dtype, numel):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{what} must hold {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def spectrum_index_map(H: int, W: int):
+    """(ky, kx) of every stored spectrum slot of one frame, as lists.
+
+    The first H * (W/2) slots are kx < W/2 in [ky][kx] order; the last H slots are the
+    kx = W/2 column in ky order.
+    """
+    Wh = W // 2
+    ky = [s // Wh for s in range(H * Wh)] + list(range(H))
+    kx = [s % Wh for s in range(H * Wh)] + [Wh] * H
+    return ky, kx
+
+
+class Plan:
+    """A ddm_plan with torch-tensor marshalling."""
+
+    def __init__(self, H: int, W: int, N: int, dtype: str = "u16", n_bins: int = 0,
+                 precision: int = DDM_PREC_FP32, subtract_ref: int = 1, M: int = 0,
+                 fix_lags: int = 0, max_workspace_bytes: int = 0):
+        L = lib()
+        d = ddm_plan_desc()
+        _check(L.ddm_plan_desc_init(ctypes.byref(d), H, W, N), "ddm_plan_desc_init")
+        d.dtype = {"u16": DDM_IN_U16, "f32": DDM_IN_F32}[dtype]
+        d.n_bins = n_bins
+        d.precision = precision
+        d.subtract_ref = subtract_ref
+        d.M = M
+        d.fix_lags = fix_lags
+        d.max_workspace_bytes = max_workspace_bytes
+        self.desc = d
+        self.H, self.W, self.N, self.n_bins = H, W, N, n_bins
+        self.dtype = dtype
+        h = ctypes.c_void_p()
+        _check(L.ddm_plan_create(ctypes.byref(h), ctypes.byref(d)), "ddm_plan_create")
+        self._h = h
+        nq = ctypes.c_int64()
+        _check(L.ddm_plan_n_q(h, ctypes.byref(nq)), "ddm_plan_n_q")
+        self.n_q = int(nq.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _frames(self, frames):
+        import torch
+        dt = torch.uint16 if self.dtype == "u16" else torch.float32
+        return _dev_ptr(frames, "frames", dt, self.N * self.H * self.W)
+
+    def workspace_size(self) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().ddm_plan_workspace_size(self._h, ctypes.byref(b)), "ddm_plan_workspace_size")
+        return int(b.value)
+
+    def set_workspace(self, ws):
+        import torch
+        if ws.dtype != torch.uint8 or not ws.is_cuda:
+            raise TypeError("workspace must be a CUDA uint8 tensor")
+        _check(lib().ddm_plan_set_workspace(self._h, ctypes.c_void_p(ws.data_ptr()), ws.numel()),
+               "ddm_plan_set_workspace")
+        self._ws = ws
+
+    def spatial_fft(self, frames, spectrum, stream=None):
+        import torch
+        _check(lib().ddm_spatial_fft(self._h, self._frames(frames),
+                                     _dev_ptr(spectrum, "spectrum", torch.float32, 2 * self.N * self.n_q),
+                                     _stream_ptr(stream)), "ddm_spatial_fft")
+
+    def temporal_sf(self, spectrum, D, stream=None):
+        import torch
+        _check(lib().ddm_temporal_sf(self._h,
+                                     _dev_ptr(spectrum, "spectrum", torch.float32, 2 * self.N * self.n_q),
+                                     _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
+                                     _stream_ptr(stream)), "ddm_temporal_sf")
+
+    def structure_function(self, frames, D, stream=None):
+        import torch
+        _check(lib().ddm_structure_function(self._h, self._frames(frames),
+                                            _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
+                                            _stream_ptr(stream)), "ddm_structure_function")
+
+    def azimuthal_average(self, D, Dr, counts=None, stream=None):
+        import torch
+        cp = ctypes.c_void_p(0) if counts is None else _dev_ptr(counts, "counts", torch.int32, self.n_bins)
+        _check(lib().ddm_azimuthal_average(self._h, _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
+                                           _dev_ptr(Dr, "Dr", torch.float32, self.n_bins * self.N),
+                                           cp, _stream_ptr(stream)), "ddm_azimuthal_average")
+
+    def last_device_status(self) -> int:
+        s = ctypes.c_int()
+        _check(lib().ddm_plan_last_device_status(self._h, ctypes.byref(s)), "ddm_plan_last_device_status")
+        return int(s.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ddm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

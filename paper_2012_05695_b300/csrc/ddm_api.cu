@@ -1,0 +1,313 @@
+// C ABI of the library: plan life cycle, validation, tables, and the entry points of
+// include/ddm.h.  No exception crosses this boundary; every failure is a status code.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "ddm_fft.cuh"
+#include "ddm_internal.h"
+
+namespace ddm {
+
+int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+namespace {
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+constexpr int kMaxSide = 1024;
+constexpr int kMaxFrames = 1024;
+
+// floor(n_bins * |q| / (pi sqrt 2)) with |q| = 2 pi sqrt((ky/H)^2 + (kx/W)^2):
+// the largest b with (b H W)^2 <= 2 n_bins^2 (ky^2 W^2 + kx^2 H^2), in exact integers.
+int radial_bin(int ky_signed, int kx_signed, int H, int W, int n_bins) {
+    typedef unsigned __int128 u128;
+    const u128 ky2 = (u128)((int64_t)ky_signed * ky_signed), kx2 = (u128)((int64_t)kx_signed * kx_signed);
+    const u128 K = ky2 * (u128)W * (u128)W + kx2 * (u128)H * (u128)H;
+    const u128 rhs = (u128)2 * (u128)n_bins * (u128)n_bins * K;
+    const u128 hw2 = (u128)H * W * (u128)H * W;
+    // upper estimate then step down; b <= n_bins * sqrt(2) / 2 * sqrt(2) ~ n_bins
+    int64_t lo = 0, hi = (int64_t)2 * n_bins + 2;
+    while (lo < hi) {          // largest b with b^2 hw2 <= rhs
+        const int64_t mid = (lo + hi + 1) / 2;
+        if ((u128)mid * (u128)mid * hw2 <= rhs) lo = mid; else hi = mid - 1;
+    }
+    return (int)std::min<int64_t>(lo, n_bins - 1);
+}
+
+template <typename T>
+ddm_status upload(T** dst, const std::vector<T>& host) {
+    *dst = nullptr;
+    if (host.empty()) return DDM_OK;
+    if (cudaMalloc((void**)dst, sizeof(T) * host.size()) != cudaSuccess) {
+        cudaGetLastError();
+        *dst = nullptr;
+        return DDM_ERR_OOM;
+    }
+    if (cudaMemcpy(*dst, host.data(), sizeof(T) * host.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return DDM_ERR_CUDA;
+    return DDM_OK;
+}
+
+void free_plan(ddm_plan_s* p) {
+    if (!p) return;
+    cudaFree(p->tw_row);
+    cudaFree(p->tw_col);
+    cudaFree(p->tw_t);
+    cudaFree(p->tw2);
+    cudaFree(p->inv);
+    cudaFree(p->bin_start);
+    cudaFree(p->bin_q);
+    cudaFree(p->bin_count);
+    cudaFree(p->dev_status);
+    if (p->ws_owned) cudaFree(p->workspace);
+    delete p;
+}
+
+std::vector<float2> pass_twiddles(int L) {
+    std::vector<float2> t;
+    if (L >= 64) {
+        t.resize(L);
+        host_pass_twiddles(L, t.data());
+    }
+    return t;
+}
+
+size_t workspace_bytes(const ddm_plan_desc& d) {
+    const size_t nq = (size_t)d.H * (size_t)(d.W / 2 + 1);
+    const size_t b = nq * (size_t)d.N * sizeof(float2);
+    return (b + 255) & ~(size_t)255;
+}
+
+ddm_status validate(const ddm_plan_desc* d) {
+    if (!d) return DDM_ERR_INVALID_ARG;
+    if (!is_pow2(d->H) || !is_pow2(d->W) || d->H < 2 || d->W < 2) return DDM_ERR_INVALID_ARG;
+    if (d->H > kMaxSide || d->W > kMaxSide) return DDM_ERR_UNSUPPORTED;
+    if (d->N < 1) return DDM_ERR_INVALID_ARG;
+    if (d->N > kMaxFrames) return DDM_ERR_UNSUPPORTED;
+    if (d->dtype != DDM_IN_U16 && d->dtype != DDM_IN_F32) return DDM_ERR_INVALID_ARG;
+    if (d->precision != DDM_PREC_FP32 && d->precision != DDM_PREC_FP32_FP64FIX)
+        return DDM_ERR_INVALID_ARG;
+    if (d->precision == DDM_PREC_FP32_FP64FIX) return DDM_ERR_UNSUPPORTED;
+    if (d->subtract_ref != 0 && d->subtract_ref != 1) return DDM_ERR_INVALID_ARG;
+    if (d->n_bins < 0 || d->n_bins > (1 << 20)) return DDM_ERR_INVALID_ARG;
+    if (d->fix_lags < 0) return DDM_ERR_INVALID_ARG;
+    const int L = 1 << ilog2(d->N);
+    if (d->M != 0) {
+        if ((int64_t)d->M < 2 * (int64_t)d->N - 1) return DDM_ERR_INVALID_ARG;
+        if (d->M != 2 * L) return DDM_ERR_UNSUPPORTED;
+    }
+    if (d->max_workspace_bytes != 0 && workspace_bytes(*d) > d->max_workspace_bytes)
+        return DDM_ERR_OOM;
+    return DDM_OK;
+}
+
+bool check_plan(ddm_plan p) { return p != nullptr; }
+
+ddm_status ensure_workspace(ddm_plan_s* p) {
+    if (p->workspace) return DDM_OK;
+    const size_t need = workspace_bytes(p->d);
+    if (cudaMalloc(&p->workspace, need) != cudaSuccess) {
+        cudaGetLastError();
+        p->workspace = nullptr;
+        return DDM_ERR_OOM;
+    }
+    p->ws_bytes = need;
+    p->ws_owned = true;
+    return DDM_OK;
+}
+
+}  // namespace
+}  // namespace ddm
+
+using namespace ddm;
+
+extern "C" {
+
+int ddm_abi_version(void) { return DDM_ABI_VERSION; }
+
+const char* ddm_status_string(ddm_status s) {
+    switch (s) {
+        case DDM_OK: return "ok";
+        case DDM_ERR_INVALID_ARG: return "invalid argument";
+        case DDM_ERR_UNSUPPORTED: return "unsupported by this build";
+        case DDM_ERR_OOM: return "out of device memory or over the workspace limit";
+        case DDM_ERR_CUDA: return "CUDA runtime error";
+        case DDM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case DDM_ERR_NUMERIC: return "non-finite value in a kernel";
+        case DDM_ERR_NO_WORKSPACE: return "no workspace";
+        default: return "unknown status";
+    }
+}
+
+ddm_status ddm_plan_desc_init(ddm_plan_desc* desc, int H, int W, int N) {
+    if (!desc) return DDM_ERR_INVALID_ARG;
+    memset(desc, 0, sizeof(*desc));
+    desc->H = H;
+    desc->W = W;
+    desc->N = N;
+    desc->dtype = DDM_IN_U16;
+    desc->precision = DDM_PREC_FP32;
+    desc->subtract_ref = 1;
+    return DDM_OK;
+}
+
+ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
+    if (!out) return DDM_ERR_INVALID_ARG;
+    *out = nullptr;
+    const ddm_status v = validate(desc);
+    if (v != DDM_OK) return v;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DDM_ERR_CUDA;
+    }
+    ddm_plan_s* p = new (std::nothrow) ddm_plan_s();
+    if (!p) return DDM_ERR_OOM;
+    p->d = *desc;
+    p->device = dev;
+    p->L = 1 << ilog2(desc->N);
+    p->Wh = desc->W / 2;
+    p->n_q = (int64_t)desc->H * (p->Wh + 1);
+    const int KD = std::min(32, p->L / 2);
+    p->kd = std::min(KD, desc->N - 1);
+    p->fix_lags = desc->fix_lags > 0 ? desc->fix_lags : 8;
+    if (cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return DDM_ERR_CUDA;
+    }
+    ddm_status st = DDM_OK;
+    // pass twiddles of the three transform lengths
+    if (st == DDM_OK) st = upload(&p->tw_row, pass_twiddles(desc->W));
+    if (st == DDM_OK) st = upload(&p->tw_col, pass_twiddles(desc->H));
+    if (st == DDM_OK) st = upload(&p->tw_t, pass_twiddles(p->L));
+    // exp(-i pi t / L) and 1/(N - m)
+    if (st == DDM_OK) {
+        std::vector<float2> tw2(p->L);
+        std::vector<float> inv(p->L, 0.f);
+        for (int t = 0; t < p->L; ++t) {
+            const cx_cs cs = cx_cossin_frac(t, (long)2 * p->L);
+            tw2[t] = make_float2((float)cs.c, (float)-cs.s);
+        }
+        for (int m = 1; m < desc->N; ++m) inv[m] = (float)(1.0 / (double)(desc->N - m));
+        st = upload(&p->tw2, tw2);
+        if (st == DDM_OK) st = upload(&p->inv, inv);
+    }
+    // radial bins: CSR of public q per bin (ascending), full-plane counts
+    if (st == DDM_OK && desc->n_bins > 0) {
+        const int H = desc->H, W = desc->W, Wh = p->Wh, nb = desc->n_bins;
+        std::vector<int> bin_of((size_t)p->n_q);
+        std::vector<int> count(nb, 0), start(nb + 1, 0);
+        for (int ky = 0; ky < H; ++ky) {
+            const int ys = ky > H / 2 ? ky - H : ky;
+            for (int kx = 0; kx <= Wh; ++kx) {
+                const int b = radial_bin(ys, kx, H, W, nb);
+                bin_of[(size_t)ky * (Wh + 1) + kx] = b;
+                count[b] += (kx == 0 || kx == Wh) ? 1 : 2;
+                start[b + 1] += 1;
+            }
+        }
+        for (int b = 0; b < nb; ++b) start[b + 1] += start[b];
+        std::vector<int> items((size_t)p->n_q), fill(start.begin(), start.end() - 1);
+        for (int64_t q = 0; q < p->n_q; ++q) items[fill[bin_of[q]]++] = (int)q;
+        st = upload(&p->bin_start, start);
+        if (st == DDM_OK) st = upload(&p->bin_q, items);
+        if (st == DDM_OK) st = upload(&p->bin_count, count);
+    }
+    if (st == DDM_OK) {
+        if (cudaMalloc(&p->dev_status, sizeof(unsigned)) != cudaSuccess ||
+            cudaMemset(p->dev_status, 0, sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            st = DDM_ERR_CUDA;
+        }
+    }
+    if (st != DDM_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return DDM_OK;
+}
+
+ddm_status ddm_plan_destroy(ddm_plan p) {
+    free_plan(p);
+    return DDM_OK;
+}
+
+ddm_status ddm_plan_workspace_size(ddm_plan p, size_t* bytes) {
+    if (!check_plan(p) || !bytes) return DDM_ERR_INVALID_ARG;
+    *bytes = workspace_bytes(p->d);
+    return DDM_OK;
+}
+
+ddm_status ddm_plan_set_workspace(ddm_plan p, void* dev_ptr, size_t bytes) {
+    if (!check_plan(p) || !dev_ptr) return DDM_ERR_INVALID_ARG;
+    if (bytes < workspace_bytes(p->d) || (reinterpret_cast<uintptr_t>(dev_ptr) & 255) != 0)
+        return DDM_ERR_INVALID_ARG;
+    if (p->ws_owned) cudaFree(p->workspace);
+    p->workspace = dev_ptr;
+    p->ws_bytes = bytes;
+    p->ws_owned = false;
+    return DDM_OK;
+}
+
+ddm_status ddm_plan_n_q(ddm_plan p, int64_t* n_q) {
+    if (!check_plan(p) || !n_q) return DDM_ERR_INVALID_ARG;
+    *n_q = p->n_q;
+    return DDM_OK;
+}
+
+ddm_status ddm_plan_last_device_status(ddm_plan p, ddm_status* out) {
+    if (!check_plan(p) || !out) return DDM_ERR_INVALID_ARG;
+    unsigned h = 0;
+    if (cudaMemcpy(&h, p->dev_status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(p->dev_status, 0, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return DDM_ERR_CUDA;
+    }
+    *out = (h & 1u) ? DDM_ERR_NUMERIC : DDM_OK;
+    return DDM_OK;
+}
+
+ddm_status ddm_spatial_fft(ddm_plan p, const void* frames, float* spectrum, void* stream) {
+    if (!check_plan(p) || !frames || !spectrum) return DDM_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(spectrum) & 7) != 0) return DDM_ERR_INVALID_ARG;
+    return launch_spatial(p, frames, reinterpret_cast<float2*>(spectrum), (cudaStream_t)stream);
+}
+
+ddm_status ddm_temporal_sf(ddm_plan p, const float* spectrum, float* D, void* stream) {
+    if (!check_plan(p) || !spectrum || !D) return DDM_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(spectrum) & 7) != 0 || (reinterpret_cast<uintptr_t>(D) & 3) != 0)
+        return DDM_ERR_INVALID_ARG;
+    return launch_temporal(p, reinterpret_cast<const float2*>(spectrum), D, (cudaStream_t)stream);
+}
+
+ddm_status ddm_structure_function(ddm_plan p, const void* frames, float* D, void* stream) {
+    if (!check_plan(p) || !frames || !D) return DDM_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(D) & 3) != 0) return DDM_ERR_INVALID_ARG;
+    ddm_status st = ensure_workspace(p);
+    if (st != DDM_OK) return st;
+    float2* spec = reinterpret_cast<float2*>(p->workspace);
+    st = launch_spatial(p, frames, spec, (cudaStream_t)stream);
+    if (st != DDM_OK) return st;
+    return launch_temporal(p, spec, D, (cudaStream_t)stream);
+}
+
+ddm_status ddm_azimuthal_average(ddm_plan p, const float* D, float* Dr, int* counts,
+                                 void* stream) {
+    if (!check_plan(p) || !D || !Dr) return DDM_ERR_INVALID_ARG;
+    if (p->d.n_bins <= 0) return DDM_ERR_INVALID_ARG;
+    return launch_radial(p, D, Dr, counts, (cudaStream_t)stream);
+}
+
+}  // extern "C"

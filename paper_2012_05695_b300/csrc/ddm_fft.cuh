@@ -1,0 +1,250 @@
+// Batched power-of-two FFT building blocks for sm_103a (CUDA cores, FP32).
+//
+// Every transform of length L is held by T = L / P threads, P points per thread, in the
+// "cyclic" layout: thread i holds x[i + T*u], u = 0..P-1.  A transform is computed in two
+// register passes (four-step factorisation L = P * T, T <= P):
+//   pass 1: P-point DFT over u inside each thread, twiddle w_L^{i*k1};
+//   one exchange through shared memory;
+//   pass 2: T-point DFTs over the threads, P/T of them per thread;
+// and the result comes back in the same cyclic layout: thread i holds X[i + T*u].
+//
+// Shared memory of QT transforms is interleaved ([index][transform]) so that the lanes of
+// a warp, which run consecutive transforms, touch consecutive words (conflict-free).
+//
+// Twiddles inside a thread are compile-time constants evaluated by constexpr code below
+// (Taylor series after exact argument reduction); the pass twiddles come from a table
+// built on the host in double precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <utility>
+
+namespace ddm {
+
+// ------------------------------------------------------------------ constexpr trig
+// cos and sin of 2*pi*a/b for integers, reduced exactly to an angle in [0, pi/4] and
+// evaluated by Taylor series in double precision (|error| < 1e-17 there).
+__host__ __device__ constexpr double cx_taylor_sin(double x) {
+    double term = x, sum = x;
+    for (int n = 1; n < 14; ++n) {
+        term *= -x * x / (double)((2 * n) * (2 * n + 1));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double cx_taylor_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int n = 1; n < 14; ++n) {
+        term *= -x * x / (double)((2 * n - 1) * (2 * n));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// returns {cos, sin} of 2*pi*a/b
+struct cx_cs { double c, s; };
+__host__ __device__ constexpr cx_cs cx_cossin_frac(long a, long b) {
+    // reduce a/b to [0, 1)
+    long r = a % b;
+    if (r < 0) r += b;
+    // octant: angle = 2*pi*r/b, work with eighths: 8r/b
+    const long e8 = 8 * r;                 // angle in units of pi/4 is e8 / b
+    const long oct = e8 / b;               // 0..7
+    const long rem = e8 - oct * b;         // remainder in [0, b)
+    // angle within the octant in radians: (rem / b) * pi/4
+    const double x = (double)rem / (double)b * (kPi / 4.0);
+    const double sx = cx_taylor_sin(x), cxv = cx_taylor_cos(x);
+    const double sy = cx_taylor_sin(kPi / 4.0 - x), cy = cx_taylor_cos(kPi / 4.0 - x);
+    // angle = oct * pi/4 + x
+    switch (oct) {
+        case 0: return {cxv, sx};
+        case 1: return {sy, cy};            // pi/2 - (pi/4 - x)
+        case 2: return {-sx, cxv};          // pi/2 + x
+        case 3: return {-cy, sy};           // pi - (pi/4 - x)
+        case 4: return {-cxv, -sx};         // pi + x
+        case 5: return {-sy, -cy};          // 3pi/2 - (pi/4 - x)
+        case 6: return {sx, -cxv};          // 3pi/2 + x
+        default: return {cy, -sy};          // 2pi - (pi/4 - x)
+    }
+}
+
+// Returns p unchanged but hides its value from the optimiser, so that addresses derived
+// from it are recomputed where they are used instead of being kept live in registers
+// across a transform (32 strided addresses would otherwise pin 64 registers).
+template <typename T>
+__device__ __forceinline__ T* opaque_ptr(T* p) {
+    asm volatile("" : "+l"(p));
+    return p;
+}
+
+// Compiler-only memory fence: shared/global loads may not be hoisted across it.  Used
+// every few elements in unrolled element-wise loops so the scheduler does not pull all
+// of a thread's table loads up front and run out of registers.
+__device__ __forceinline__ void hoist_fence() { asm volatile("" ::: "memory"); }
+
+// ------------------------------------------------------------------ complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+    return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 w) {   // a * conj(w)
+    return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
+}
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// multiply by w_R^K (forward: exp(-2 pi i K / R); inverse: the conjugate), K constant
+template <int R, int K, bool INV>
+__device__ __forceinline__ float2 twiddle_const(float2 o) {
+    constexpr int k = ((K % R) + R) % R;
+    if constexpr (k == 0) {
+        return o;
+    } else if constexpr (4 * k == R) {                 // -i (forward), +i (inverse)
+        return INV ? make_float2(-o.y, o.x) : make_float2(o.y, -o.x);
+    } else if constexpr (2 * k == R) {
+        return make_float2(-o.x, -o.y);
+    } else if constexpr (4 * k == 3 * R) {             // +i (forward), -i (inverse)
+        return INV ? make_float2(o.y, -o.x) : make_float2(-o.y, o.x);
+    } else if constexpr (8 * k == R) {                 // (1 -/+ i)/sqrt2
+        constexpr float h = (float)cx_cossin_frac(1, 8).c;
+        return INV ? make_float2((o.x - o.y) * h, (o.x + o.y) * h)
+                   : make_float2((o.x + o.y) * h, (o.y - o.x) * h);
+    } else if constexpr (8 * k == 3 * R) {             // (-1 -/+ i)/sqrt2
+        constexpr float h = (float)cx_cossin_frac(1, 8).c;
+        return INV ? make_float2(-(o.x + o.y) * h, (o.x - o.y) * h)
+                   : make_float2((o.y - o.x) * h, -(o.x + o.y) * h);
+    } else {
+        constexpr cx_cs cs = cx_cossin_frac(k, R);
+        constexpr float c = (float)cs.c;
+        constexpr float s = INV ? (float)cs.s : (float)-cs.s;
+        return make_float2(fmaf(o.x, c, -o.y * s), fmaf(o.x, s, o.y * c));
+    }
+}
+
+// ------------------------------------------------------------------ in-register DFT
+// Unnormalised DFT of R = 2^n points held in registers, natural order in and out.
+// Radix-2 decimation in time with compile-time twiddles; radix-4 leaves.
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2* v);
+
+template <int R, bool INV, int... K>
+__device__ __forceinline__ void dit_combine(float2* v, const float2* e, const float2* o,
+                                            std::integer_sequence<int, K...>) {
+    ((v[K] = cadd(e[K], twiddle_const<R, K, INV>(o[K])),
+      v[K + R / 2] = csub(e[K], twiddle_const<R, K, INV>(o[K]))), ...);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2* v) {
+    if constexpr (R == 1) {
+        return;
+    } else if constexpr (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        const float2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+        const float2 r = twiddle_const<4, 1, INV>(d13);
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, r);
+        v[3] = csub(d02, r);
+    } else {
+        float2 e[R / 2], o[R / 2];
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            e[k] = v[2 * k];
+            o[k] = v[2 * k + 1];
+        }
+        dft_reg<R / 2, INV>(e);
+        dft_reg<R / 2, INV>(o);
+        dit_combine<R, INV>(v, e, o, std::make_integer_sequence<int, R / 2>{});
+    }
+}
+
+// ------------------------------------------------------------------ two-pass FFT
+template <int L>
+struct FftShape {
+    static_assert((L & (L - 1)) == 0 && L >= 1 && L <= 1024, "L must be a power of two <= 1024");
+    static constexpr int P = L < 32 ? L : 32;   // points per thread
+    static constexpr int T = L / P;              // threads per transform
+    static_assert(T <= P, "two-pass factorisation needs T <= P");
+};
+
+// Host/device twiddle table for the pass between the two register passes of an L-point
+// transform: tw[k1 * T + i] = exp(-2 pi i * i * k1 / L), k1 < P, i < T (L entries).
+inline void host_pass_twiddles(int L, float2* out) {
+    const int P = L < 32 ? L : 32, T = L / P;
+    for (int k1 = 0; k1 < P; ++k1)
+        for (int i = 0; i < T; ++i) {
+            const cx_cs cs = cx_cossin_frac((long)((long)i * k1 % L), L);
+            out[k1 * T + i] = make_float2((float)cs.c, (float)-cs.s);
+        }
+}
+
+// Shared-memory placement of the logical exchange index idx (0..L-1) of one transform.
+// Interleaved: QT transforms side by side, lanes of a warp on consecutive transforms.
+template <int QT>
+struct AddrInterleaved {
+    int ql;
+    __device__ __forceinline__ int operator()(int idx) const { return idx * QT + ql; }
+};
+// Transform-major with one pad element per T: lanes of a warp on consecutive i.
+template <int L>
+struct AddrPadded {
+    int base;   // transform index * stride()
+    static constexpr int T = FftShape<L>::T;
+    static constexpr int stride() { return L + L / T; }
+    __device__ __forceinline__ int operator()(int idx) const { return base + idx + idx / T; }
+};
+
+struct SyncBlock {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct SyncWarp {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+
+// In-place L-point transform of a group of transforms whose threads run in lockstep.
+//   v    thread's P points, cyclic layout in and out
+//   i    thread index within its transform (0..T-1)
+//   xs   shared scratch; element addresses given by addr
+//   tw   pass twiddles in host_pass_twiddles layout (shared or global memory)
+// sync() must make shared-memory writes of every thread of the group visible.
+template <int L, bool INV, typename Addr, typename Sync>
+__device__ __forceinline__ void fft_cyclic(float2 (&v)[FftShape<L>::P], int i, float2* xs,
+                                           Addr addr, const float2* tw, Sync sync) {
+    constexpr int P = FftShape<L>::P;
+    constexpr int T = FftShape<L>::T;
+    dft_reg<P, INV>(v);
+    if constexpr (T > 1) {
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) {
+            float2 a = v[k1];
+            if (k1 > 0) {
+                const float2 w = tw[k1 * T + i];
+                a = INV ? cmul_conj(a, w) : cmul(a, w);
+            }
+            xs[addr(k1 * T + i)] = a;
+            if ((k1 & 7) == 7) hoist_fence();
+        }
+        sync();
+        constexpr int G = P / T;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            float2 w[T];
+#pragma unroll
+            for (int ip = 0; ip < T; ++ip) w[ip] = xs[addr((i + T * g) * T + ip)];
+            dft_reg<T, INV>(w);
+#pragma unroll
+            for (int k2 = 0; k2 < T; ++k2) v[g + G * k2] = w[k2];
+        }
+        sync();
+    }
+}
+
+}  // namespace ddm

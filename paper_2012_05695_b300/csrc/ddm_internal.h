@@ -1,0 +1,48 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ddm.h"
+
+struct ddm_plan_s {
+    ddm_plan_desc d;
+    int L;              // transform length in time: smallest power of two >= N (M = 2L)
+    int Wh;             // W / 2
+    int64_t n_q;        // H * (W/2 + 1)
+    int device;
+    int n_sm;
+    int kd;             // number of trailing lags evaluated by direct differences
+    int fix_lags;       // leading lags recomputed by direct differences (FP64FIX tier)
+    // device tables owned by the plan
+    float2* tw_row;     // pass twiddles of the W-point row transform
+    float2* tw_col;     // pass twiddles of the H-point column transform
+    float2* tw_t;       // pass twiddles of the L-point time transform
+    float2* tw2;        // exp(-i pi t / L), t < L
+    float* inv;         // 1 / (N - m), m < N; 0 at m = 0
+    int* bin_start;     // [n_bins + 1] CSR offsets into bin_q
+    int* bin_q;         // public q indices grouped by bin, ascending inside a bin
+    int* bin_count;     // [n_bins] full-plane modes per bin
+    int max_bin_items;
+    unsigned* dev_status;   // kernel-reported status word
+    void* workspace;
+    size_t ws_bytes;
+    bool ws_owned;
+};
+
+namespace ddm {
+
+// storage index of the spectrum: the first H*Wh entries of a frame are kx < W/2
+// ([ky][kx]); the last H entries are the kx = W/2 column ([ky]).
+size_t spectrum_frame_stride(const ddm_plan_s* p);   // complex elements per frame
+
+ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
+                          cudaStream_t s);
+ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s);
+ddm_status launch_radial(const ddm_plan_s* p, const float* D, float* Dr, int* counts,
+                         cudaStream_t s);
+
+int ilog2(int v);
+
+}  // namespace ddm

@@ -1,0 +1,94 @@
+"""The C-ABI library loads, exports every symbol include/ddm.h declares, and validates
+arguments on the host (no device needed for any of these)."""
+import ctypes
+import subprocess
+
+import pytest
+
+import paper_2012_05695_b300 as ddm
+from paper_2012_05695_b300 import _binding as B
+from conftest import cuda_available
+
+
+def test_library_is_in_tree_and_loads():
+    L = ddm.lib()
+    assert L.ddm_abi_version() == 1
+    assert ddm.LIB_PATH.endswith("paper_2012_05695_b300/_lib/libddm_b300.so")
+
+
+def test_every_header_function_is_exported():
+    names = ddm.header_functions()
+    assert len(names) >= 13
+    L = ddm.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", ddm.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    assert set(names) <= exported
+
+
+def test_status_strings():
+    for s in range(8):
+        assert ddm.status_string(s)
+    assert ddm.status_string(0) == "ok"
+    assert "unknown" in ddm.status_string(99)
+
+
+def _desc(H=8, W=8, N=4):
+    d = B.ddm_plan_desc()
+    assert ddm.lib().ddm_plan_desc_init(ctypes.byref(d), H, W, N) == 0
+    return d
+
+
+def test_desc_init_defaults():
+    d = _desc(16, 32, 10)
+    assert (d.H, d.W, d.N, d.dtype, d.precision, d.M, d.n_bins, d.subtract_ref) == \
+        (16, 32, 10, 0, 0, 0, 0, 1)
+    assert ddm.lib().ddm_plan_desc_init(None, 1, 1, 1) == B.DDM_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("H", 3, B.DDM_ERR_INVALID_ARG),
+    ("W", 0, B.DDM_ERR_INVALID_ARG),
+    ("H", 2048, B.DDM_ERR_UNSUPPORTED),
+    ("N", 0, B.DDM_ERR_INVALID_ARG),
+    ("N", 4096, B.DDM_ERR_UNSUPPORTED),
+    ("dtype", 7, B.DDM_ERR_INVALID_ARG),
+    ("precision", 9, B.DDM_ERR_INVALID_ARG),
+    ("M", 6, B.DDM_ERR_INVALID_ARG),          # M < 2N - 1 wraps around (App. B)
+    ("M", 7, B.DDM_ERR_UNSUPPORTED),          # legal pad length, not the one built
+    ("subtract_ref", 2, B.DDM_ERR_INVALID_ARG),
+    ("n_bins", -1, B.DDM_ERR_INVALID_ARG),
+    ("max_workspace_bytes", 16, B.DDM_ERR_OOM),
+])
+def test_plan_create_validates_before_touching_the_device(field, value, status):
+    d = _desc(8, 8, 4)
+    setattr(d, field, value)
+    h = ctypes.c_void_p(123)
+    assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == status
+    assert not h.value
+
+
+def test_null_arguments():
+    L = ddm.lib()
+    d = _desc()
+    assert L.ddm_plan_create(None, ctypes.byref(d)) == B.DDM_ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    assert L.ddm_plan_create(ctypes.byref(h), None) == B.DDM_ERR_INVALID_ARG
+    assert L.ddm_plan_destroy(None) == 0
+    nul = ctypes.c_void_p(0)
+    assert L.ddm_structure_function(nul, nul, nul, nul) == B.DDM_ERR_INVALID_ARG
+    assert L.ddm_spatial_fft(nul, nul, nul, nul) == B.DDM_ERR_INVALID_ARG
+    assert L.ddm_temporal_sf(nul, nul, nul, nul) == B.DDM_ERR_INVALID_ARG
+    assert L.ddm_azimuthal_average(nul, nul, nul, nul, nul) == B.DDM_ERR_INVALID_ARG
+    sz = ctypes.c_size_t()
+    assert L.ddm_plan_workspace_size(nul, ctypes.byref(sz)) == B.DDM_ERR_INVALID_ARG
+
+
+@pytest.mark.skipif(cuda_available(), reason="checks the no-device path")
+def test_valid_plan_without_device_is_a_cuda_error():
+    d = _desc(8, 8, 4)
+    h = ctypes.c_void_p()
+    assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == B.DDM_ERR_CUDA
+    assert not h.value
