@@ -53,7 +53,18 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--shape", default=None,
+                    help="HxWxN of a smaller blob stack for profiling captures (default 512x512x1024)")
+    args = ap.parse_args()
+    if args.shape:
+        global H, W, N_FRAMES, N_Q, SPATIAL_BYTES, TEMPORAL_BYTES, STEP_BYTES, WORKLOAD
+        H, W, N_FRAMES = (int(x) for x in args.shape.lower().split("x"))
+        N_Q = H * (W // 2 + 1)
+        SPATIAL_BYTES = N_FRAMES * H * W * 2 + N_Q * N_FRAMES * 8
+        TEMPORAL_BYTES = N_Q * N_FRAMES * 8 + N_Q * N_FRAMES * 4
+        STEP_BYTES = SPATIAL_BYTES + TEMPORAL_BYTES
+        WORKLOAD = f"blobs_{H}x{W}x{N_FRAMES}_u16"
+    return args
 
 
 def dist_env():
@@ -178,7 +189,7 @@ def run_reference(args):
     import oracle
     import synth
     oracle.build()
-    frames = synth.blobs_512x512x1024(seed=args.seed)
+    frames = synth.blobs_512x512x1024(seed=args.seed, N=N_FRAMES, H=H, W=W)
     cores = os.cpu_count() or 1
     cols = [1]
     times = []
@@ -219,7 +230,7 @@ def run_ours(args):
     import paper_2012_05695_b300 as ddm
     import synth
 
-    frames_np = synth.blobs_512x512x1024(seed=args.seed + rank)
+    frames_np = synth.blobs_512x512x1024(seed=args.seed + rank, N=N_FRAMES, H=H, W=W)
     plan = ddm.Plan(H, W, N_FRAMES, dtype="u16", n_bins=N_BINS)
     dev = torch.device("cuda", local)
     frames = torch.from_numpy(frames_np).to(dev)
