@@ -146,6 +146,29 @@ ddm_status ddm_structure_function(ddm_plan p, const void* frames, float* D, void
 ddm_status ddm_azimuthal_average(ddm_plan p, const float* D, float* Dr, int* counts,
                                  void* stream);
 
+/* ---- allocation-free variant (the paper has no counterpart) -------------------------- */
+
+/* Size of the library's own device scratch used by ddm_structure_function_static:
+ * 64 MiB, held on every GPU that loads this library until the process exits. */
+#define DDM_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/* Same result as ddm_structure_function, for callers that must not allocate device
+ * memory when they ask for D -- a host whose own pool allocator already owns the device
+ * memory, or a no-allocation hot loop.  The plan is created beforehand (plan creation
+ * does allocate its small tables); this call allocates nothing, needs no workspace and
+ * keeps the spectrum in the library's fixed device scratch instead.
+ *   frames [N][H][W] uint16 or float32 (desc.dtype), device;  D [n_q][N] float32, device.
+ * Limits and behaviour:
+ *   - the spectrum, n_q * N * 8 bytes, must fit DDM_STATIC_SCRATCH_BYTES, else
+ *     DDM_ERR_UNSUPPORTED is returned and nothing is enqueued;
+ *   - the plan's device must be the current device, else DDM_ERR_INVALID_ARG;
+ *   - the first call on a device looks up the scratch's device address (one-time set-up);
+ *     make that first call before capturing any stream;
+ *   - all calls share the one scratch: calls whose work overlaps on the GPU (different
+ *     streams, no ordering between them) race and give wrong results; calls ordered on
+ *     one stream are safe.  Nothing in the scratch needs to start at zero. */
+ddm_status ddm_structure_function_static(ddm_plan p, const void* frames, float* D, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

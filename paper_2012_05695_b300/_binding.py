@@ -71,6 +71,7 @@ def lib():
         "ddm_temporal_sf": (st, [vp, vp, vp, vp]),
         "ddm_structure_function": (st, [vp, vp, vp, vp]),
         "ddm_azimuthal_average": (st, [vp, vp, vp, vp, vp]),
+        "ddm_structure_function_static": (st, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
