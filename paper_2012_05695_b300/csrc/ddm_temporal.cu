@@ -39,7 +39,9 @@ struct TShape {
     static constexpr int NT = (T == 32) ? 512 : 256;      // threads per CTA
     static constexpr int QT = NT / T;                      // wave vectors per tile
     static constexpr int KD = (L / 2 < 32) ? L / 2 : 32;  // max directly evaluated lags
-    static constexpr int DSTRIDE = L + (QT >= 32 ? 1 : 32 / QT);
+    // D staging row stride: conflict-free writes from the cyclic layout, and 16-byte
+    // aligned rows (float4 stores) when QT == 16
+    static constexpr int DSTRIDE = L + (QT >= 32 ? 1 : (QT == 16 ? 4 : 32 / QT));
     static constexpr int RED = (P > 2 * T ? P : 2 * T);
     // shared memory carve-up (bytes)
     static constexpr size_t OFF_TW = 0;
@@ -58,21 +60,20 @@ struct TShape {
 struct TArgs {
     int N;            // frames
     int kd;           // directly evaluated trailing lags (<= KD, < N)
-    int H, Wh;        // for the storage -> public q map
+    int H, Wh, lwh;   // for the storage -> public q map (lwh = log2 Wh)
     int64_t n_q;      // stored wave vectors = spectrum frame stride
     int64_t n_tiles;
+    int vec4;         // D rows 16-byte aligned (N % 4 == 0 and D aligned): float4 stores
     const float2* tw;
     const float2* tw2;
     const float* inv;
     unsigned* status;
 };
 
-__device__ __forceinline__ int64_t public_q(int64_t s, int H, int Wh) {
-    const int64_t main = (int64_t)H * Wh;
-    if (s < main) {
-        const int64_t ky = s / Wh, kx = s - ky * Wh;
-        return ky * (Wh + 1) + kx;
-    }
+// storage index -> public q = ky * (Wh + 1) + kx (Wh = W/2 is a power of two)
+__device__ __forceinline__ int public_q(int s, int H, int Wh, int lwh) {
+    const int main = H << lwh;
+    if (s < main) return (s >> lwh) * (Wh + 1) + (s & (Wh - 1));
     return (s - main) * (Wh + 1) + Wh;
 }
 
@@ -117,6 +118,19 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         const int64_t s = tile * QT + ql;
         const bool valid = s < nq;
         const float2* src = spec + (valid ? s : 0);
+
+        // ---- prefetch the next tile of this CTA into L2: its DRAM fetch overlaps this tile
+        {
+            const int64_t sn = (tile + gridDim.x) * QT + ql;
+            if (sn < nq) {
+                const float2* pn = spec + sn;
+#pragma unroll
+                for (int u = 0; u < P; ++u) {
+                    const int t = i + T * u;
+                    if (t < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(pn + (uint32_t)t * nq32));
+                }
+            }
+        }
 
         // ---- load the time sequence (cyclic layout) and remove its mean
         float2 v[P];
@@ -187,42 +201,46 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         }
         __syncthreads();   // partner reads done: the exchange buffer is free
 
-        // ---- power terms: inclusive prefix sums S(t) of |g|^2 (tile reloaded from L2)
+        // ---- power terms: inclusive prefix sums S(t) of |g|^2.  Thread i owns the rows
+        // r = i + T g of T consecutive t (reloaded from L2; each load instruction still
+        // covers whole 128-byte segments), sums them in registers, and adds the offset of
+        // the rows before it.
         const float2* src3 = opaque_ptr(src);
-#pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int t = i + T * u;
-            float e = 0.f;
-            if (valid && t < N) e = cabs2(csub(__ldg(src3 + (uint32_t)t * nq32), mean));
-            xf[t * QT + ql] = e;
-        }
-        __syncthreads();
-        constexpr int G = P / T;                      // rows of T consecutive t per thread
+        constexpr int G = P / T;
+        float rowv[G][T];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int r = i + T * g;
             float acc = 0.f;
-#pragma unroll 8
+#pragma unroll
             for (int jj = 0; jj < T; ++jj) {
-                const int idx = (r * T + jj) * QT + ql;
-                acc += xf[idx];
-                xf[idx] = acc;
+                const int t = r * T + jj;
+                float e = 0.f;
+                if (valid && t < N) e = cabs2(csub(__ldg(src3 + (uint32_t)t * nq32), mean));
+                acc += e;
+                rowv[g][jj] = acc;
             }
             red[r * QT + ql] = acc;
         }
         __syncthreads();
+        float total = 0.f;
+        float off[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) off[g] = 0.f;
+#pragma unroll
+        for (int rp = 0; rp < P; ++rp) {
+            const float x = red[rp * QT + ql];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (rp < i + T * g) off[g] += x;
+            total += x;
+        }
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int r = i + T * g;
-            float off = 0.f;
-            for (int rp = 0; rp < r; ++rp) off += red[rp * QT + ql];
-            if (r > 0) {
-#pragma unroll 8
-                for (int jj = 0; jj < T; ++jj) xf[(r * T + jj) * QT + ql] += off;
-            }
+#pragma unroll
+            for (int jj = 0; jj < T; ++jj) xf[(r * T + jj) * QT + ql] = rowv[g][jj] + off[g];
         }
-        float total = 0.f;
-        for (int rp = 0; rp < P; ++rp) total += red[rp * QT + ql];
         __syncthreads();
 
         // ---- D(m) = (P1 + P2 - 2 Re C) / (N - m) for m < N - kd
@@ -261,14 +279,28 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
             }
         }
         __syncthreads();
-        for (int r = 0; r < QT; ++r) {
-            const int64_t sr = tile * QT + r;
-            if (sr >= nq) break;
-            float* drow = D + public_q(sr, a.H, a.Wh) * (int64_t)N;
-            for (int m = tid; m < N; m += NT) {
-                const float d = xf[r * DS + m];
-                bad |= !isfinite(d);
-                drow[m] = d;
+        if (QT == 16 && a.vec4) {
+            const int n4 = N >> 2;
+            const int total4 = QT * n4;
+            for (int f = tid; f < total4; f += NT) {
+                const int r = f / n4, j = f - r * n4;
+                const int64_t sr = tile * QT + r;
+                if (sr >= nq) break;
+                const float4 d = *reinterpret_cast<const float4*>(xf + r * DS + 4 * j);
+                bad |= !(isfinite(d.x) && isfinite(d.y) && isfinite(d.z) && isfinite(d.w));
+                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
+                reinterpret_cast<float4*>(drow)[j] = d;
+            }
+        } else {
+            for (int r = 0; r < QT; ++r) {
+                const int64_t sr = tile * QT + r;
+                if (sr >= nq) break;
+                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
+                for (int m = tid; m < N; m += NT) {
+                    const float d = xf[r * DS + m];
+                    bad |= !isfinite(d);
+                    drow[m] = d;
+                }
             }
         }
         __syncthreads();
@@ -284,6 +316,8 @@ ddm_status launch_t(const ddm_plan_s* p, const float2* spec, float* D, cudaStrea
     a.kd = p->kd;
     a.H = p->d.H;
     a.Wh = p->Wh;
+    a.lwh = ilog2(p->Wh);
+    a.vec4 = (p->d.N % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
     a.n_q = p->n_q;
     a.n_tiles = (p->n_q + C::QT - 1) / C::QT;
     a.tw = p->tw_t;
