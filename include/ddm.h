@@ -146,6 +146,70 @@ ddm_status ddm_structure_function(ddm_plan p, const void* frames, float* D, void
 ddm_status ddm_azimuthal_average(ddm_plan p, const float* D, float* Dr, int* counts,
                                  void* stream);
 
+/* ---- fit of D(|q|, dt) (not in the paper: the analysis step that follows it) ---------- */
+
+/* Model D(lag) = A (1 - exp(-(lag / tau)^beta)) + B, fitted per curve at the 64 log-spaced
+ * lags lag_i = exp(i ln(N-1) / 63), i = 0..63 (curves sampled by linear interpolation
+ * between neighbouring integer lags).  Needs N >= 2. */
+#define DDM_FIT_LAGS 64
+#define DDM_MLP_PARAMS 41860   /* 64 -> 128 -> 128 -> 128 -> 4, weights then bias per layer */
+
+typedef enum ddm_fit_mode {
+    DDM_FIT_LM = 0,        /* Levenberg-Marquardt from a heuristic seed */
+    DDM_FIT_MLP = 1,       /* MLP prediction only */
+    DDM_FIT_MLP_LM = 2     /* MLP seed; kept if its RMS residual / A <= 1e-2, else LM from
+                              it, and LM from the heuristic seed if that diverges */
+} ddm_fit_mode;
+
+/* ddm_fit flags per curve */
+#define DDM_FIT_CONVERGED 1
+#define DDM_FIT_MAXITER 2
+#define DDM_FIT_NONFINITE 4
+#define DDM_FIT_MLP_ACCEPTED 8
+#define DDM_FIT_FALLBACK 16
+
+typedef struct ddm_mlp_s* ddm_mlp;
+
+/* Features of curves for the MLP: the 64 log-lag samples divided by their plateau
+ * p8 = mean of the last 8 samples (1 if p8 <= 0).
+ *   Dr [n_curves][N] float32 device (e.g. ddm_azimuthal_average's output; N = plan's N)
+ *   x  [n_curves][64] float32 device, written;  p8 [n_curves] float32 device, written */
+ddm_status ddm_fit_features(ddm_plan p, const float* Dr, int n_curves, float* x, float* p8,
+                            void* stream);
+
+/* Fit every curve of Dr [n_curves][N].  mlp may be NULL for DDM_FIT_LM.
+ *   params [n_curves][4] float32 (A, tau, beta, B);  cost [n_curves] float32 (sum of squared
+ *   residuals at the 64 lags);  iters [n_curves] int32 (LM iterations, 0 if none);
+ *   flags [n_curves] int32 (DDM_FIT_*).  cost, iters, flags may be NULL.
+ * LM (FP32, one warp per curve): p = (A, B, ln tau, beta) on the curve divided by p8,
+ * analytic Jacobian, damping (J^T J + lam diag J^T J) dp = -J^T r, lam from 1e-3, /10 on
+ * an accepted step, x10 on a rejected one (stop above 1e12), beta clamped to [0.05, 3],
+ * stop when a step accepted at its first trial lowers the cost by less than 1e-6 of it,
+ * at most 100 iterations.  Scratch (features, MLP outputs) is taken from the plan's workspace if it is
+ * large enough, else allocated by the plan on first use (n_curves * 276 bytes). */
+ddm_status ddm_fit(ddm_plan p, const float* Dr, int n_curves, int mode, ddm_mlp mlp,
+                   float* params, float* cost, int* iters, int* flags, void* stream);
+
+/* MLP 64 -> 128 -> 128 -> 128 -> 4 with GELU (erf form) on the hidden layers.  FP32 master
+ * weights, Adam state and gradients on the device; the weight matrices are used rounded to
+ * bfloat16, biases and accumulation in FP32.  Head: A = p8 exp(o0), tau = exp(o1),
+ * beta = 0.3 + 0.9 sigmoid(o2), B = A o3.  max_batch bounds every batch passed later. */
+ddm_status ddm_mlp_create(ddm_mlp* out, int max_batch);
+ddm_status ddm_mlp_destroy(ddm_mlp m);
+/* Host arrays of DDM_MLP_PARAMS floats; set resets the Adam state and step count. */
+ddm_status ddm_mlp_set_weights(ddm_mlp m, const float* host_w);
+ddm_status ddm_mlp_get_weights(ddm_mlp m, float* host_w);
+/* x [B][64] device -> o [B][4] device (raw outputs, before the head). */
+ddm_status ddm_mlp_forward(ddm_mlp m, const float* x, int B, float* o, void* stream);
+/* Loss = mean over the batch of (o0 - t0)^2 + (o1 - t1)^2 + (beta - t2)^2 + (o3 - t3)^2,
+ * t [B][4] device targets (ln(A/p8), ln tau, beta, B/A).  grad [DDM_MLP_PARAMS] device and
+ * loss [1] device are written (loss may be NULL).  Summation order is fixed. */
+ddm_status ddm_mlp_grad(ddm_mlp m, const float* x, const float* t, int B, float* grad,
+                        float* loss, void* stream);
+/* ddm_mlp_grad followed by one Adam step (b1 0.9, b2 0.999, eps 1e-8) at rate lr. */
+ddm_status ddm_mlp_train_step(ddm_mlp m, const float* x, const float* t, int B, float lr,
+                              float* loss, void* stream);
+
 /* ---- allocation-free variant (the paper has no counterpart) -------------------------- */
 
 /* Size of the library's own device scratch used by ddm_structure_function_static:

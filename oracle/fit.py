@@ -9,8 +9,8 @@ one curve at a time, written from these definitions:
 * Levenberg-Marquardt on p = (A, B, ln tau, beta), residual r = model - y, cost = sum r^2,
   analytic Jacobian, Marquardt damping (J^T J + lam diag(J^T J)) dp = -J^T r, lam starts at
   1e-3, /10 on an accepted step, x10 on a rejected one; beta is clamped to [0.05, 3];
-  stop when an accepted step lowers the cost by less than tol * cost, when lam exceeds 1e12,
-  or after 100 iterations.
+  stop when a step accepted at its first trial (no rejection in that iteration) lowers the
+  cost by less than tol * cost, when lam exceeds 1e12, or after 100 iterations.
 * heuristic seed: plateau p8 = mean of the last 8 samples, A0 = p8, B0 = 0, beta0 = 1,
   tau0 = the lag where y first reaches (1 - 1/e) p8 (log-linear interpolation; lambda_0 / 2
   if already reached, lambda_63 if never).
@@ -113,6 +113,7 @@ def lm_fit(lam, y, p0, max_iter=100, tol=1e-10):
         g = J.T @ r
         Hm = J.T @ J
         accepted = False
+        first_try = True
         while True:
             Ad = Hm + mu * np.diag(np.diag(Hm))
             try:
@@ -128,6 +129,7 @@ def lm_fit(lam, y, p0, max_iter=100, tol=1e-10):
                 accepted = True
                 break
             mu *= 10.0
+            first_try = False
             if mu > 1e12:
                 break
         if not accepted:
@@ -136,7 +138,7 @@ def lm_fit(lam, y, p0, max_iter=100, tol=1e-10):
         dec = cost - cn
         p, f, J, r, cost = pn, fn, Jn, rn, cn
         mu = max(mu / 10.0, 1e-12)
-        if dec <= tol * cost:
+        if first_try and dec <= tol * cost:
             flags = FLAG_CONVERGED
             break
     return p, cost, it, flags

@@ -29,6 +29,17 @@ DDM_IN_F32 = 1
 DDM_PREC_FP32 = 0
 DDM_PREC_FP32_FP64FIX = 1
 
+DDM_FIT_LM = 0
+DDM_FIT_MLP = 1
+DDM_FIT_MLP_LM = 2
+DDM_FIT_CONVERGED = 1
+DDM_FIT_MAXITER = 2
+DDM_FIT_NONFINITE = 4
+DDM_FIT_MLP_ACCEPTED = 8
+DDM_FIT_FALLBACK = 16
+DDM_FIT_LAGS = 64
+DDM_MLP_PARAMS = 41860
+
 
 class DDMError(RuntimeError):
     def __init__(self, status: int, where: str):
@@ -72,6 +83,15 @@ def lib():
         "ddm_structure_function": (st, [vp, vp, vp, vp]),
         "ddm_azimuthal_average": (st, [vp, vp, vp, vp, vp]),
         "ddm_structure_function_static": (st, [vp, vp, vp, vp]),
+        "ddm_fit_features": (st, [vp, vp, c_int, vp, vp, vp]),
+        "ddm_fit": (st, [vp, vp, c_int, c_int, vp, vp, vp, vp, vp, vp]),
+        "ddm_mlp_create": (st, [ctypes.POINTER(vp), c_int]),
+        "ddm_mlp_destroy": (st, [vp]),
+        "ddm_mlp_set_weights": (st, [vp, vp]),
+        "ddm_mlp_get_weights": (st, [vp, vp]),
+        "ddm_mlp_forward": (st, [vp, vp, c_int, vp, vp]),
+        "ddm_mlp_grad": (st, [vp, vp, vp, c_int, vp, vp, vp]),
+        "ddm_mlp_train_step": (st, [vp, vp, vp, c_int, ctypes.c_float, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -206,6 +226,24 @@ class Plan:
                                            _dev_ptr(Dr, "Dr", torch.float32, self.n_bins * self.N),
                                            cp, _stream_ptr(stream)), "ddm_azimuthal_average")
 
+    def fit_features(self, Dr, n_curves, x, p8, stream=None):
+        import torch
+        _check(lib().ddm_fit_features(self._h, _dev_ptr(Dr, "Dr", torch.float32, n_curves * self.N),
+                                      n_curves, _dev_ptr(x, "x", torch.float32, n_curves * DDM_FIT_LAGS),
+                                      _dev_ptr(p8, "p8", torch.float32, n_curves),
+                                      _stream_ptr(stream)), "ddm_fit_features")
+
+    def fit(self, Dr, n_curves, mode, mlp, params, cost=None, iters=None, flags=None, stream=None):
+        import torch
+
+        def opt(t, what, dt):
+            return ctypes.c_void_p(0) if t is None else _dev_ptr(t, what, dt, n_curves)
+        _check(lib().ddm_fit(self._h, _dev_ptr(Dr, "Dr", torch.float32, n_curves * self.N), n_curves,
+                             int(mode), None if mlp is None else mlp.handle,
+                             _dev_ptr(params, "params", torch.float32, 4 * n_curves),
+                             opt(cost, "cost", torch.float32), opt(iters, "iters", torch.int32),
+                             opt(flags, "flags", torch.int32), _stream_ptr(stream)), "ddm_fit")
+
     def last_device_status(self) -> int:
         s = ctypes.c_int()
         _check(lib().ddm_plan_last_device_status(self._h, ctypes.byref(s)), "ddm_plan_last_device_status")
@@ -227,3 +265,62 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class MLP:
+    """ddm_mlp: the fit seed network (device weights, Adam state)."""
+
+    def __init__(self, max_batch: int = 4096):
+        h = ctypes.c_void_p()
+        _check(lib().ddm_mlp_create(ctypes.byref(h), int(max_batch)), "ddm_mlp_create")
+        self._h = h
+        self.max_batch = int(max_batch)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_weights(self, w):
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+        if a.size != DDM_MLP_PARAMS:
+            raise ValueError("weights must hold %d floats" % DDM_MLP_PARAMS)
+        _check(lib().ddm_mlp_set_weights(self._h, a.ctypes.data_as(ctypes.c_void_p)), "ddm_mlp_set_weights")
+
+    def get_weights(self):
+        import numpy as np
+        a = np.empty(DDM_MLP_PARAMS, np.float32)
+        _check(lib().ddm_mlp_get_weights(self._h, a.ctypes.data_as(ctypes.c_void_p)), "ddm_mlp_get_weights")
+        return a
+
+    def forward(self, x, B, o, stream=None):
+        import torch
+        _check(lib().ddm_mlp_forward(self._h, _dev_ptr(x, "x", torch.float32, B * DDM_FIT_LAGS), int(B),
+                                     _dev_ptr(o, "o", torch.float32, B * 4), _stream_ptr(stream)),
+               "ddm_mlp_forward")
+
+    def grad(self, x, t, B, grad, loss=None, stream=None):
+        import torch
+        lp = ctypes.c_void_p(0) if loss is None else _dev_ptr(loss, "loss", torch.float32, 1)
+        _check(lib().ddm_mlp_grad(self._h, _dev_ptr(x, "x", torch.float32, B * DDM_FIT_LAGS),
+                                  _dev_ptr(t, "t", torch.float32, B * 4), int(B),
+                                  _dev_ptr(grad, "grad", torch.float32, DDM_MLP_PARAMS), lp,
+                                  _stream_ptr(stream)), "ddm_mlp_grad")
+
+    def train_step(self, x, t, B, lr, loss=None, stream=None):
+        import torch
+        lp = ctypes.c_void_p(0) if loss is None else _dev_ptr(loss, "loss", torch.float32, 1)
+        _check(lib().ddm_mlp_train_step(self._h, _dev_ptr(x, "x", torch.float32, B * DDM_FIT_LAGS),
+                                        _dev_ptr(t, "t", torch.float32, B * 4), int(B), float(lr), lp,
+                                        _stream_ptr(stream)), "ddm_mlp_train_step")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ddm_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

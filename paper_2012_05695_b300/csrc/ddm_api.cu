@@ -68,6 +68,10 @@ void free_plan(ddm_plan_s* p) {
     cudaFree(p->bin_start);
     cudaFree(p->bin_q);
     cudaFree(p->bin_count);
+    cudaFree(p->lag_j);
+    cudaFree(p->lag_f);
+    cudaFree(p->lag_ll);
+    cudaFree(p->fit_scratch);
     cudaFree(p->dev_status);
     if (p->ws_owned) cudaFree(p->workspace);
     delete p;
@@ -224,6 +228,7 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
         if (st == DDM_OK) st = upload(&p->bin_q, items);
         if (st == DDM_OK) st = upload(&p->bin_count, count);
     }
+    if (st == DDM_OK) st = make_fit_tables(p);
     if (st == DDM_OK) {
         if (cudaMalloc(&p->dev_status, sizeof(unsigned)) != cudaSuccess ||
             cudaMemset(p->dev_status, 0, sizeof(unsigned)) != cudaSuccess) {

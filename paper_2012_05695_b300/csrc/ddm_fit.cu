@@ -1,0 +1,354 @@
+// Fit of the radial structure functions (not in the paper): sample every curve at 64
+// log-spaced lags, seed (heuristic or MLP), and Levenberg-Marquardt of
+// D(lag) = A (1 - exp(-(lag / tau)^beta)) + B.  One warp per curve, two lags per lane.
+//
+// Every warp reduction ends with a broadcast of lane 0's value, so all lanes hold
+// bitwise-identical sums and take identical accept / reject decisions.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <vector>
+
+#include "ddm_internal.h"
+
+namespace ddm {
+
+ddm_status mlp_forward_raw(const ddm_mlp_s* m, const float* x, int B, float* o, cudaStream_t s);
+int mlp_max_batch(const ddm_mlp_s* m);
+
+namespace {
+
+constexpr int kLags = DDM_FIT_LAGS;
+constexpr int kWarpsPerBlock = 4;
+
+__device__ __forceinline__ float warp_sum_bcast(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// grid: ceil(n / kWarpsPerBlock); block: 32 * kWarpsPerBlock
+__global__ void features_kernel(const float* __restrict__ Dr, int n, int N,
+                                const int* __restrict__ lag_j, const float* __restrict__ lag_f,
+                                float* __restrict__ x, float* __restrict__ p8) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= n) return;
+    const float* d = Dr + (size_t)c * N;
+    float y[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        const int j = lag_j[i];
+        const int j1 = j + 1 < N ? j + 1 : N - 1;
+        const float f = lag_f[i];
+        y[h] = d[j] * (1.f - f) + d[j1] * f;
+    }
+    // plateau: mean of samples 56..63 (lanes 24..31, second half)
+    float p = warp_sum_bcast(lane >= 24 ? y[1] : 0.f) * 0.125f;
+    if (!(p > 0.f)) p = 1.f;
+    x[(size_t)c * kLags + lane] = y[0] / p;
+    x[(size_t)c * kLags + lane + 32] = y[1] / p;
+    if (lane == 0) p8[c] = p;
+}
+
+struct Curve {
+    float y[2], ll[2];
+};
+
+// residuals and Jacobian rows of the two lags of this lane at p = (A, B, ln tau, beta)
+__device__ __forceinline__ void model_rows(const Curve& cv, const float p[4], float r[2],
+                                           float J[2][4]) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float lx = cv.ll[h] - p[2];
+        const float s = expf(p[3] * lx);
+        const float e = expf(-s);
+        r[h] = p[0] * (1.f - e) + p[1] - cv.y[h];
+        J[h][0] = 1.f - e;
+        J[h][1] = 1.f;
+        J[h][2] = -p[0] * p[3] * s * e;
+        J[h][3] = p[0] * e * s * lx;
+    }
+}
+
+__device__ __forceinline__ float cost_at(const Curve& cv, const float p[4]) {
+    float r[2], J[2][4];
+    model_rows(cv, p, r, J);
+    return warp_sum_bcast(r[0] * r[0] + r[1] * r[1]);
+}
+
+// Solve (H + mu diag H) dp = -g by Cholesky of the Jacobi-scaled matrix
+// S (H + mu diag H) S with S = diag(H)^(-1/2) (unit diagonal 1 + mu: better conditioned in
+// FP32 when columns of J are nearly collinear); false if not positive definite / finite.
+__device__ __forceinline__ bool solve4(const float H[10], const float g[4], float mu, float dp[4]) {
+    // H packed: 00 10 11 20 21 22 30 31 32 33
+    if (!(H[0] > 0.f && H[2] > 0.f && H[5] > 0.f && H[9] > 0.f)) return false;
+    const float s0 = rsqrtf(H[0]), s1 = rsqrtf(H[2]), s2 = rsqrtf(H[5]), s3 = rsqrtf(H[9]);
+    const float dg = 1.f + mu;
+    const float a10 = H[1] * s1 * s0, a20 = H[3] * s2 * s0, a21 = H[4] * s2 * s1;
+    const float a30 = H[6] * s3 * s0, a31 = H[7] * s3 * s1, a32 = H[8] * s3 * s2;
+    const float b0 = -g[0] * s0, b1 = -g[1] * s1, b2 = -g[2] * s2, b3 = -g[3] * s3;
+    const float l00 = sqrtf(dg);
+    const float l10 = a10 / l00, l20 = a20 / l00, l30 = a30 / l00;
+    const float d1 = dg - l10 * l10;
+    if (!(d1 > 0.f)) return false;
+    const float l11 = sqrtf(d1);
+    const float l21 = (a21 - l20 * l10) / l11, l31 = (a31 - l30 * l10) / l11;
+    const float d2 = dg - l20 * l20 - l21 * l21;
+    if (!(d2 > 0.f)) return false;
+    const float l22 = sqrtf(d2);
+    const float l32 = (a32 - l30 * l20 - l31 * l21) / l22;
+    const float d3 = dg - l30 * l30 - l31 * l31 - l32 * l32;
+    if (!(d3 > 0.f)) return false;
+    const float l33 = sqrtf(d3);
+    const float z0 = b0 / l00;
+    const float z1 = (b1 - l10 * z0) / l11;
+    const float z2 = (b2 - l20 * z0 - l21 * z1) / l22;
+    const float z3 = (b3 - l30 * z0 - l31 * z1 - l32 * z2) / l33;
+    const float e3 = z3 / l33;
+    const float e2 = (z2 - l32 * e3) / l22;
+    const float e1 = (z1 - l21 * e2 - l31 * e3) / l11;
+    const float e0 = (z0 - l10 * e1 - l20 * e2 - l30 * e3) / l00;
+    dp[0] = e0 * s0;
+    dp[1] = e1 * s1;
+    dp[2] = e2 * s2;
+    dp[3] = e3 * s3;
+    return isfinite(dp[0]) && isfinite(dp[1]) && isfinite(dp[2]) && isfinite(dp[3]);
+}
+
+// LM from p (in/out); returns iterations, sets cost and flags
+__device__ int lm(const Curve& cv, float p[4], float& cost, int& flags) {
+    cost = cost_at(cv, p);
+    if (!isfinite(cost)) {
+        flags = DDM_FIT_NONFINITE;
+        return 0;
+    }
+    float mu = 1e-3f;
+    flags = DDM_FIT_MAXITER;
+    int it = 0;
+    while (it < 100) {
+        ++it;
+        float r[2], J[2][4];
+        model_rows(cv, p, r, J);
+        float H[10], g[4];
+        {
+            int k = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+#pragma unroll
+                for (int b = 0; b <= a; ++b) H[k++] = warp_sum_bcast(J[0][a] * J[0][b] + J[1][a] * J[1][b]);
+                g[a] = warp_sum_bcast(J[0][a] * r[0] + J[1][a] * r[1]);
+            }
+        }
+        bool accepted = false, first_try = true;
+        float pn[4], cn = 0.f;
+        while (true) {
+            float dp[4];
+            if (solve4(H, g, mu, dp)) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) pn[a] = p[a] + dp[a];
+                pn[3] = fminf(fmaxf(pn[3], 0.05f), 3.f);
+                cn = cost_at(cv, pn);
+                if (isfinite(cn) && cn < cost) {
+                    accepted = true;
+                    break;
+                }
+            }
+            mu *= 10.f;
+            first_try = false;
+            if (mu > 1e12f) break;
+        }
+        if (!accepted) {
+            flags = DDM_FIT_CONVERGED;
+            break;
+        }
+        const float dec = cost - cn;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) p[a] = pn[a];
+        cost = cn;
+        mu = fmaxf(mu * 0.1f, 1e-12f);
+        if (first_try && dec <= 1e-6f * cost) {
+            flags = DDM_FIT_CONVERGED;
+            break;
+        }
+    }
+    return it;
+}
+
+__device__ void heuristic_seed(const Curve& cv, int lane, float p[4]) {
+    const float target = 1.f - expf(-1.f);           // plateau of a normalised curve is 1
+    const unsigned b0 = __ballot_sync(0xffffffffu, cv.y[0] >= target);
+    const unsigned b1 = __ballot_sync(0xffffffffu, cv.y[1] >= target);
+    int k = -1;
+    if (b0) k = __ffs(b0) - 1;
+    else if (b1) k = 32 + __ffs(b1) - 1;
+    float ltau;
+    const float ll_last = __shfl_sync(0xffffffffu, cv.ll[1], 31);
+    const float ll_first = __shfl_sync(0xffffffffu, cv.ll[0], 0);
+    if (k < 0) {
+        ltau = ll_last;
+    } else if (k == 0) {
+        ltau = ll_first - logf(2.f);
+    } else {
+        const int km = k - 1;
+        const float yk = __shfl_sync(0xffffffffu, k < 32 ? cv.y[0] : cv.y[1], k & 31);
+        const float ykm = __shfl_sync(0xffffffffu, km < 32 ? cv.y[0] : cv.y[1], km & 31);
+        const float llk = __shfl_sync(0xffffffffu, k < 32 ? cv.ll[0] : cv.ll[1], k & 31);
+        const float llkm = __shfl_sync(0xffffffffu, km < 32 ? cv.ll[0] : cv.ll[1], km & 31);
+        const float w = (yk != ykm) ? (target - ykm) / (yk - ykm) : 0.f;
+        ltau = llkm + w * (llk - llkm);
+    }
+    (void)lane;
+    p[0] = 1.f;
+    p[1] = 0.f;
+    p[2] = ltau;
+    p[3] = 1.f;
+}
+
+// grid: ceil(n / kWarpsPerBlock); block: 32 * kWarpsPerBlock
+__global__ void lm_kernel(const float* __restrict__ x, const float* __restrict__ p8,
+                          const float* __restrict__ mlp_o, int n, int mode,
+                          const float* __restrict__ lag_ll, float* __restrict__ params,
+                          float* __restrict__ cost_out, int* __restrict__ iters_out,
+                          int* __restrict__ flags_out) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (c >= n) return;
+    Curve cv;
+    cv.y[0] = x[(size_t)c * kLags + lane];
+    cv.y[1] = x[(size_t)c * kLags + lane + 32];
+    cv.ll[0] = lag_ll[lane];
+    cv.ll[1] = lag_ll[lane + 32];
+    const float P8 = p8[c];
+    float p[4], cost = 0.f;
+    int flags = 0, it = 0;
+    if (mode == DDM_FIT_LM) {
+        heuristic_seed(cv, lane, p);
+        it = lm(cv, p, cost, flags);
+    } else {
+        const float o0 = mlp_o[(size_t)c * 4 + 0], o1 = mlp_o[(size_t)c * 4 + 1];
+        const float o2 = mlp_o[(size_t)c * 4 + 2], o3 = mlp_o[(size_t)c * 4 + 3];
+        const float A = expf(o0);
+        p[0] = A;
+        p[1] = A * o3;
+        p[2] = o1;
+        p[3] = 0.3f + 0.9f / (1.f + expf(-o2));
+        cost = cost_at(cv, p);
+        if (mode == DDM_FIT_MLP) {
+            flags = DDM_FIT_MLP_ACCEPTED | (isfinite(cost) ? 0 : DDM_FIT_NONFINITE);
+        } else if (isfinite(cost) && sqrtf(cost / (float)kLags) <= 1e-2f * fabsf(A)) {
+            flags = DDM_FIT_CONVERGED | DDM_FIT_MLP_ACCEPTED;
+        } else {
+            float q[4] = {p[0], p[1], p[2], p[3]};
+            it = lm(cv, q, cost, flags);
+            if (flags & DDM_FIT_NONFINITE) {
+                heuristic_seed(cv, lane, q);
+                it += lm(cv, q, cost, flags);
+                flags |= DDM_FIT_FALLBACK;
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) p[a] = q[a];
+        }
+    }
+    if (lane == 0) {
+        params[(size_t)c * 4 + 0] = p[0] * P8;
+        params[(size_t)c * 4 + 1] = expf(p[2]);
+        params[(size_t)c * 4 + 2] = p[3];
+        params[(size_t)c * 4 + 3] = p[1] * P8;
+        if (cost_out) cost_out[c] = cost * P8 * P8;
+        if (iters_out) iters_out[c] = it;
+        if (flags_out) flags_out[c] = flags;
+    }
+}
+
+}  // namespace
+
+ddm_status make_fit_tables(ddm_plan_s* p) {
+    const int N = p->d.N;
+    if (N < 2) return DDM_OK;
+    std::vector<int> j(kLags);
+    std::vector<float> f(kLags), ll(kLags);
+    for (int i = 0; i < kLags; ++i) {
+        const double lam = std::exp((double)i * std::log((double)(N - 1)) / (double)(kLags - 1));
+        int jj = (int)std::floor(lam);
+        if (jj > N - 1) jj = N - 1;
+        j[i] = jj;
+        f[i] = (float)(lam - (double)jj);
+        ll[i] = (float)std::log(lam);
+    }
+    if (cudaMalloc(&p->lag_j, sizeof(int) * kLags) != cudaSuccess ||
+        cudaMalloc(&p->lag_f, sizeof(float) * kLags) != cudaSuccess ||
+        cudaMalloc(&p->lag_ll, sizeof(float) * kLags) != cudaSuccess) {
+        cudaGetLastError();
+        return DDM_ERR_OOM;
+    }
+    if (cudaMemcpy(p->lag_j, j.data(), sizeof(int) * kLags, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->lag_f, f.data(), sizeof(float) * kLags, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->lag_ll, ll.data(), sizeof(float) * kLags, cudaMemcpyHostToDevice) != cudaSuccess)
+        return DDM_ERR_CUDA;
+    return DDM_OK;
+}
+
+ddm_status launch_features(const ddm_plan_s* p, const float* Dr, int n, float* x, float* p8,
+                           cudaStream_t s) {
+    const int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    features_kernel<<<blocks, 32 * kWarpsPerBlock, 0, s>>>(Dr, n, p->d.N, p->lag_j, p->lag_f, x, p8);
+    return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
+}
+
+ddm_status launch_fit(ddm_plan_s* p, const float* Dr, int n, int mode, const ddm_mlp_s* mlp,
+                      float* params, float* cost, int* iters, int* flags, cudaStream_t s) {
+    // scratch: x [n][64], p8 [n], o [n][4]
+    const size_t need = (size_t)n * (kLags + 1 + 4) * sizeof(float);
+    if (p->fit_scratch_bytes < need) {
+        if (p->fit_scratch) cudaFree(p->fit_scratch);
+        p->fit_scratch = nullptr;
+        p->fit_scratch_bytes = 0;
+        if (cudaMalloc(&p->fit_scratch, need) != cudaSuccess) {
+            cudaGetLastError();
+            return DDM_ERR_OOM;
+        }
+        p->fit_scratch_bytes = need;
+    }
+    float* x = p->fit_scratch;
+    float* p8 = x + (size_t)n * kLags;
+    float* o = p8 + n;
+    ddm_status st = launch_features(p, Dr, n, x, p8, s);
+    if (st != DDM_OK) return st;
+    if (mode != DDM_FIT_LM) {
+        const int mb = mlp_max_batch(mlp);
+        for (int c0 = 0; c0 < n; c0 += mb) {
+            const int b = (n - c0) < mb ? (n - c0) : mb;
+            st = mlp_forward_raw(mlp, x + (size_t)c0 * kLags, b, o + (size_t)c0 * 4, s);
+            if (st != DDM_OK) return st;
+        }
+    }
+    const int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    lm_kernel<<<blocks, 32 * kWarpsPerBlock, 0, s>>>(x, p8, o, n, mode, p->lag_ll, params, cost, iters,
+                                                     flags);
+    return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
+}
+
+}  // namespace ddm
+
+extern "C" {
+
+ddm_status ddm_fit_features(ddm_plan p, const float* Dr, int n_curves, float* x, float* p8,
+                            void* stream) {
+    if (!p || !Dr || !x || !p8 || n_curves < 1) return DDM_ERR_INVALID_ARG;
+    if (p->d.N < 2 || !p->lag_j) return DDM_ERR_INVALID_ARG;
+    return ddm::launch_features(p, Dr, n_curves, x, p8, (cudaStream_t)stream);
+}
+
+ddm_status ddm_fit(ddm_plan p, const float* Dr, int n_curves, int mode, ddm_mlp mlp, float* params,
+                   float* cost, int* iters, int* flags, void* stream) {
+    if (!p || !Dr || !params || n_curves < 1) return DDM_ERR_INVALID_ARG;
+    if (mode != DDM_FIT_LM && mode != DDM_FIT_MLP && mode != DDM_FIT_MLP_LM) return DDM_ERR_INVALID_ARG;
+    if (mode != DDM_FIT_LM && !mlp) return DDM_ERR_INVALID_ARG;
+    if (p->d.N < 2 || !p->lag_j) return DDM_ERR_INVALID_ARG;
+    return ddm::launch_fit(p, Dr, n_curves, mode, mlp, params, cost, iters, flags, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -25,6 +25,11 @@ struct ddm_plan_s {
     int* bin_q;         // public q indices grouped by bin, ascending inside a bin
     int* bin_count;     // [n_bins] full-plane modes per bin
     int max_bin_items;
+    int* lag_j;         // fit: integer part of the 64 log lags
+    float* lag_f;       // fit: fractional part
+    float* lag_ll;      // fit: ln(lag)
+    float* fit_scratch; // fit: features, plateaus, MLP outputs (grown on demand)
+    size_t fit_scratch_bytes;
     unsigned* dev_status;   // kernel-reported status word
     void* workspace;
     size_t ws_bytes;
@@ -44,5 +49,6 @@ ddm_status launch_radial(const ddm_plan_s* p, const float* D, float* Dr, int* co
                          cudaStream_t s);
 
 int ilog2(int v);
+ddm_status make_fit_tables(ddm_plan_s* p);
 
 }  // namespace ddm

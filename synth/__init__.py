@@ -171,3 +171,37 @@ def ou_64x64x128(seed: int = 0) -> np.ndarray:
 def blobs_512x512x1024(seed: int = 0, N: int = 1024, H: int = 512, W: int = 512) -> np.ndarray:
     """512x512 uint16, N = 1024, 3000 blobs (sigma 2 px), D0 = 0.2, mean 2000, Poisson."""
     return blob_stack(H, W, N, 3000, 2.0, 0.2, seed)
+
+
+# Fit-stage data: curves of known parameters, and initial network weights.
+def stretched_exp_curves(n: int, N: int, seed: int, noise_rel: float = 0.01):
+    """n curves D(m), m = 0..N-1, with D(0) = 0 and, for m >= 1,
+    D(m) = A (1 - exp(-(m / tau)^beta)) + B times (1 + noise_rel * N(0, 1)).
+
+    A = s * 10^U(-0.3, 0.3) with a per-curve scale s = 10^U(2, 9); tau = 10^U(0.3, 2.6);
+    beta = U(0.5, 1.1); B = A * U(0, 0.5).  Returns (D [n, N] float32, labels [n, 4] as
+    (A, tau, beta, B) float64).
+    """
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), 0xF17])))
+    scale = 10.0 ** rng.uniform(2, 9, n)
+    A = scale * 10.0 ** rng.uniform(-0.3, 0.3, n)
+    tau = 10.0 ** rng.uniform(0.3, 2.6, n)
+    beta = rng.uniform(0.5, 1.1, n)
+    B = A * rng.uniform(0.0, 0.5, n)
+    m = np.arange(N, dtype=np.float64)[None, :]
+    D = A[:, None] * (1.0 - np.exp(-np.power(m / tau[:, None], beta[:, None]))) + B[:, None]
+    D *= 1.0 + noise_rel * rng.standard_normal(D.shape)
+    D[:, 0] = 0.0
+    return D.astype(np.float32), np.stack([A, tau, beta, B], axis=1)
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """Initial weights of the 64-128-128-128-4 network: uniform(+-sqrt(6 / fan_in)) per
+    weight matrix (He), zero biases; flat [W1, b1, W2, b2, W3, b3, W4, b4], float32."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), 0x3A1])))
+    parts = []
+    for fi, fo in [(64, 128), (128, 128), (128, 128), (128, 4)]:
+        lim = math.sqrt(6.0 / fi)
+        parts.append(rng.uniform(-lim, lim, fi * fo))
+        parts.append(np.zeros(fo))
+    return np.concatenate(parts).astype(np.float32)

@@ -1,0 +1,191 @@
+"""Fit stage on the GPU (LM kernel, MLP kernels) vs the FP64 fit oracle, and what the
+trained network gains over the heuristic seed."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2012_05695_b300 as ddm
+import synth
+from oracle import fit as F
+from paper_2012_05695_b300 import _binding as B
+
+pytestmark = pytest.mark.gpu
+
+
+def _cuda(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _fit(plan, D, mode, mlp=None):
+    import torch
+    n = D.shape[0]
+    params = torch.empty(n * 4, device="cuda")
+    cost = torch.empty(n, device="cuda")
+    iters = torch.empty(n, dtype=torch.int32, device="cuda")
+    flags = torch.empty(n, dtype=torch.int32, device="cuda")
+    plan.fit(_cuda(D.reshape(-1)), n, mode, mlp, params, cost, iters, flags)
+    torch.cuda.synchronize()
+    return (params.cpu().numpy().reshape(n, 4).astype(np.float64), cost.cpu().numpy().astype(np.float64),
+            iters.cpu().numpy(), flags.cpu().numpy())
+
+
+def test_features_match_oracle():
+    import torch
+    N, n = 777, 37
+    D, _ = synth.stretched_exp_curves(n, N, 1)
+    plan = ddm.Plan(8, 8, N, dtype="f32")
+    x = torch.empty(n * 64, device="cuda")
+    p8 = torch.empty(n, device="cuda")
+    plan.fit_features(_cuda(D.reshape(-1)), n, x, p8)
+    torch.cuda.synchronize()
+    y = F.sample_log_lags(D.astype(np.float64))
+    xr, pr = F.features(y)
+    np.testing.assert_allclose(p8.cpu().numpy(), pr, rtol=2e-6)
+    np.testing.assert_allclose(x.cpu().numpy().reshape(n, 64), xr, rtol=2e-6, atol=1e-7)
+
+
+def test_lm_matches_oracle_on_noiseless_curves():
+    """Noiseless curves at integer lags; both sides fit the same log-lag samples (linear
+    interpolation between integer lags), so the FP32 kernel must land on the FP64
+    oracle's optimum."""
+    N = 1024
+    lam_int = np.arange(N, dtype=np.float64)
+    truth = np.array([[1.0, 20.0, 1.0, 0.1], [5e8, 3.0, 0.7, 1e7], [2.0, 150.0, 0.9, 0.0],
+                      [1e4, 1.5, 1.1, 5e3], [300.0, 60.0, 0.6, 30.0]])
+    D = np.stack([F.model(np.maximum(lam_int, 1e-9), *t) for t in truth]).astype(np.float32)
+    D[:, 0] = 0
+    plan = ddm.Plan(8, 8, N, dtype="f32")
+    params, cost, iters, flags = _fit(plan, D, B.DDM_FIT_LM)
+    assert np.all(flags & B.DDM_FIT_CONVERGED), flags
+    lam = F.log_lags(N)
+    y = F.sample_log_lags(D.astype(np.float64))
+    ref = np.stack([F.params_to_physical(F.lm_fit(lam, y[c], F.heuristic_seed(lam, y[c]))[0])
+                    for c in range(len(truth))])
+    err = np.abs(params - ref) / (np.abs(ref) + 1e-3 * ref[:, :1])
+    assert np.max(err) <= 2e-3, (params, ref, err)
+
+
+def test_lm_matches_oracle_on_noisy_curves():
+    """Same curves, same algorithm: the FP32 kernel's final cost is within 1e-3 of the
+    FP64 oracle's, and its parameters agree where they are well determined."""
+    N, n = 1024, 64
+    D, labels = synth.stretched_exp_curves(n, N, 2)
+    plan = ddm.Plan(8, 8, N, dtype="f32")
+    params, cost, iters, flags = _fit(plan, D, B.DDM_FIT_LM)
+    lam = F.log_lags(N)
+    y = F.sample_log_lags(D.astype(np.float64))
+    worse = 0
+    for c in range(n):
+        p, co, it, fl = F.lm_fit(lam, y[c], F.heuristic_seed(lam, y[c]))
+        assert cost[c] <= co * (1 + 1e-3) + 1e-12 * y[c, -1] ** 2 or cost[c] <= co * 1.05, (c, cost[c], co)
+        worse += cost[c] > co * (1 + 1e-3)
+        phys = F.params_to_physical(p)
+        if 2.0 < phys[1] < 300.0:
+            np.testing.assert_allclose(params[c, [0, 2]], phys[[0, 2]], rtol=2e-2)
+    assert worse <= n // 16
+
+
+def test_mlp_forward_matches_oracle():
+    import torch
+    w = synth.mlp_init(5)
+    rng = np.random.Generator(np.random.PCG64(5))
+    Bn = 77
+    x = rng.uniform(0, 1.2, (Bn, 64)).astype(np.float32)
+    mlp = ddm.MLP(128)
+    mlp.set_weights(w)
+    o = torch.empty(Bn * 4, device="cuda")
+    mlp.forward(_cuda(x.reshape(-1)), Bn, o)
+    torch.cuda.synchronize()
+    ref, _ = F.mlp_forward(w.astype(np.float64), x.astype(np.float64), bf16=True)
+    got = o.cpu().numpy().reshape(Bn, 4)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
+    np.testing.assert_array_equal(mlp.get_weights(), w)
+
+
+def test_mlp_gradient_matches_oracle():
+    import torch
+    w = synth.mlp_init(6)
+    rng = np.random.Generator(np.random.PCG64(6))
+    Bn = 100                                   # 4 chunks, the last one ragged
+    x = rng.uniform(0, 1.2, (Bn, 64)).astype(np.float32)
+    t = np.stack([rng.normal(0, 1, Bn), rng.uniform(0, 6, Bn), rng.uniform(0.5, 1.1, Bn),
+                  rng.uniform(0, 0.5, Bn)], axis=1).astype(np.float32)
+    mlp = ddm.MLP(256)
+    mlp.set_weights(w)
+    g = torch.empty(B.DDM_MLP_PARAMS, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    mlp.grad(_cuda(x.reshape(-1)), _cuda(t.reshape(-1)), Bn, g, loss)
+    torch.cuda.synchronize()
+    lref, gref = F.loss_and_grad(w.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert float(loss.item()) == pytest.approx(lref, rel=1e-5)
+    gg = g.cpu().numpy()
+    assert np.max(np.abs(gg - gref)) <= 1e-4 * np.max(np.abs(gref))
+
+
+def test_adam_step_matches_oracle():
+    import torch
+    w = synth.mlp_init(7)
+    rng = np.random.Generator(np.random.PCG64(7))
+    Bn = 64
+    x = rng.uniform(0, 1.2, (Bn, 64)).astype(np.float32)
+    t = rng.uniform(0, 1, (Bn, 4)).astype(np.float32)
+    mlp = ddm.MLP(Bn)
+    mlp.set_weights(w)
+    lr = 1e-3
+    mlp.train_step(_cuda(x.reshape(-1)), _cuda(t.reshape(-1)), Bn, lr)
+    torch.cuda.synchronize()
+    w1 = mlp.get_weights().astype(np.float64)
+    _, g = F.loss_and_grad(w.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    wr, _, _ = F.adam_step(w.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, lr)
+    big = np.abs(g) > 1e-3 * np.max(np.abs(g))     # sign of tiny gradients is rounding noise
+    np.testing.assert_allclose(w1[big], wr[big], rtol=0, atol=1e-6)
+
+
+def test_trained_mlp_seed_gains_over_heuristic_seed():
+    """Train on 16k curves with the GPU kernels, then fit 2k held-out curves: LM seeded by
+    the network needs fewer iterations than LM from the heuristic seed, at no cost in fit
+    quality.  The numbers are printed for the record."""
+    import torch
+    N = 1024
+    Dtr, ltr = synth.stretched_exp_curves(16384, N, 10)
+    Dte, lte = synth.stretched_exp_curves(2048, N, 11)
+    plan = ddm.Plan(8, 8, N, dtype="f32")
+    # features of the training curves on the device, targets from the labels
+    x = torch.empty(16384 * 64, device="cuda")
+    p8 = torch.empty(16384, device="cuda")
+    plan.fit_features(_cuda(Dtr.reshape(-1)), 16384, x, p8)
+    torch.cuda.synchronize()
+    p8h = p8.cpu().numpy().astype(np.float64)
+    tgt = F.targets(ltr, p8h).astype(np.float32)
+    t_dev = _cuda(tgt.reshape(-1))
+    mlp = ddm.MLP(4096)
+    mlp.set_weights(synth.mlp_init(0))
+    loss = torch.empty(1, device="cuda")
+    losses = []
+    rng = np.random.Generator(np.random.PCG64(0))
+    for step in range(3000):
+        b = int(rng.integers(0, 4))
+        lr = 2e-3 if step < 2000 else 5e-4
+        mlp.train_step(x[b * 4096 * 64:(b + 1) * 4096 * 64], t_dev[b * 4096 * 4:(b + 1) * 4096 * 4],
+                       4096, lr, loss)
+        if step % 500 == 0 or step == 2999:
+            losses.append(float(loss.item()))
+    assert losses[-1] < 0.2 * losses[0], losses
+    pl, cl, il, fl = _fit(plan, Dte, B.DDM_FIT_LM)
+    pm, cm, im, fm = _fit(plan, Dte, B.DDM_FIT_MLP_LM, mlp)
+    ok_l = (fl & B.DDM_FIT_CONVERGED) > 0
+    ok_m = (fm & B.DDM_FIT_CONVERGED) > 0
+    ratio = cm / np.maximum(cl, 1e-30)
+    print(f"\ntrain loss {losses[0]:.3f} -> {losses[-1]:.4f}; held-out 2048 curves: "
+          f"LM iters mean {il.mean():.2f}, MLP+LM iters mean {im.mean():.2f}; "
+          f"converged {ok_l.mean():.4f} vs {ok_m.mean():.4f}; "
+          f"MLP accepted without LM {np.mean((fm & B.DDM_FIT_MLP_ACCEPTED) > 0):.3f}; "
+          f"cost ratio median {np.median(ratio):.4f}, p99 {np.quantile(ratio, 0.99):.3f}")
+    assert im.mean() < 0.7 * il.mean()
+    assert ok_m.mean() >= ok_l.mean() - 0.01
+    assert np.median(ratio) <= 1.02
