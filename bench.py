@@ -1,10 +1,14 @@
 #!/usr/bin/env python3
 """Frames/s to the full structure function D(q, dt) of a 512x512 uint16 stack, N = 1024.
 
-One step = one pass of the whole D path through the C ABI on one synthetic stack:
+One step = one pass of the whole hot path through the C ABI on one synthetic stack:
   ddm_spatial_fft   (step one: real-to-complex 2D DFT of every frame, 2 kernels)
   ddm_temporal_sf   (step two: per-q power sums + zero-padded transform in time, 1 kernel)
   ddm_azimuthal_average (radial average over 362 |q| bins, 1 kernel)
+  ddm_fit           (Levenberg-Marquardt of every radial curve, 2 kernels)
+After the timed steps, the fit is also run seeded by the MLP (trained at set-up on
+synthetic stretched-exponential curves with the library's own training kernels) and both
+fits are reported side by side.
 The frames (537 MB) and the spectrum (1.08 GB) are larger than L2, so no flush is needed
 between timed steps.
 
@@ -53,6 +57,7 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fit-compare", action="store_true")
     ap.add_argument("--shape", default=None,
                     help="HxWxN of a smaller blob stack for profiling captures (default 512x512x1024)")
     args = ap.parse_args()
@@ -182,6 +187,59 @@ def oracle_sample(frames, cols, nthreads):
     return time.perf_counter() - t0, D, s_q
 
 
+def compare_fits(ddm, plan, Dr, stream):
+    """Train the seed network on synthetic curves (library kernels), then fit the stack's
+    radial curves with plain LM and with the MLP seed; times and iteration counts."""
+    import torch
+    import synth
+    from oracle import fit as F   # host-side targets for the training labels only
+    B_ = ddm._binding
+    n_train, batch, steps = 65536, 4096, 4000
+    # decay times and noise floors of the kind a blob stack's radial curves span:
+    # tau from 0.2 frames (high q) to 2e5 frames (lowest q), B/A from 1e-3 to 10
+    Dtr, ltr = synth.stretched_exp_curves(n_train, N_FRAMES, 10, log10_tau=(-0.7, 5.3),
+                                          log10_b_over_a=(-3.0, 1.0))
+    tplan = ddm.Plan(8, 8, N_FRAMES, dtype="f32")
+    x = torch.empty(n_train * 64, device="cuda")
+    p8 = torch.empty(n_train, device="cuda")
+    tplan.fit_features(torch.from_numpy(Dtr.reshape(-1)).cuda(), n_train, x, p8)
+    torch.cuda.synchronize()
+    tgt = torch.from_numpy(F.targets(ltr, p8.cpu().numpy().astype(np.float64))
+                           .astype(np.float32).reshape(-1)).cuda()
+    mlp = ddm.MLP(batch)
+    mlp.set_weights(synth.mlp_init(0))
+    loss = torch.empty(1, device="cuda")
+    rng = np.random.Generator(np.random.PCG64(0))
+    t0 = time.perf_counter()
+    for k in range(steps):
+        b = int(rng.integers(0, n_train // batch))
+        mlp.train_step(x[b * batch * 64:(b + 1) * batch * 64], tgt[b * batch * 4:(b + 1) * batch * 4],
+                       batch, 2e-3 if k < 3000 else 5e-4, loss)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    out = {"train_steps": steps, "train_batch": batch, "train_s": train_s,
+           "train_loss": float(loss.item()), "curves": N_BINS}
+    for name, mode, net in (("lm", B_.DDM_FIT_LM, None), ("mlp_lm", B_.DDM_FIT_MLP_LM, mlp)):
+        prm = torch.empty(N_BINS * 4, device="cuda")
+        cst = torch.empty(N_BINS, device="cuda")
+        its = torch.empty(N_BINS, dtype=torch.int32, device="cuda")
+        flg = torch.empty(N_BINS, dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            plan.fit(Dr, N_BINS, mode, net, prm, cst, its, flg, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            plan.fit(Dr, N_BINS, mode, net, prm, cst, its, flg, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f = flg.cpu().numpy()
+        out[name] = {"ms": e0.elapsed_time(e1) / 20, "iters_mean": float(its.cpu().numpy().mean()),
+                     "converged": float(np.mean((f & B_.DDM_FIT_CONVERGED) > 0)),
+                     "mlp_accepted": float(np.mean((f & B_.DDM_FIT_MLP_ACCEPTED) > 0)),
+                     "cost_sum": float(cst.cpu().numpy().astype(np.float64).sum())}
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -238,6 +296,10 @@ def run_ours(args):
     D = torch.empty(plan.n_q * N_FRAMES, dtype=torch.float32, device=dev)
     Dr = torch.empty(N_BINS * N_FRAMES, dtype=torch.float32, device=dev)
     counts = torch.empty(N_BINS, dtype=torch.int32, device=dev)
+    fit_params = torch.empty(N_BINS * 4, dtype=torch.float32, device=dev)
+    fit_cost = torch.empty(N_BINS, dtype=torch.float32, device=dev)
+    fit_iters = torch.empty(N_BINS, dtype=torch.int32, device=dev)
+    fit_flags = torch.empty(N_BINS, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
@@ -252,12 +314,16 @@ def run_ours(args):
         plan.azimuthal_average(D, Dr, counts, stream)
         if ev:
             ev[3].record(stream)
+        plan.fit(Dr, N_BINS, ddm._binding.DDM_FIT_LM, None, fit_params, fit_cost, fit_iters,
+                 fit_flags, stream)
+        if ev:
+            ev[4].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         if dist:
@@ -282,6 +348,7 @@ def run_ours(args):
     sp_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
     tm_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
     rd_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / args.steps
+    ft_ms = sum(e[3].elapsed_time(e[4]) for e in evs) / args.steps
     n_gpus = ws
     value = n_gpus * N_FRAMES * args.steps / (ms_total / 1e3)
     peak, peak_kind = measured_peaks()
@@ -293,11 +360,15 @@ def run_ours(args):
         Dr_host = torch.empty(N_BINS * N_FRAMES, dtype=torch.float32).pin_memory()
         frames_e2e = torch.empty_like(frames)
 
+        params_host = torch.empty(N_BINS * 4, dtype=torch.float32).pin_memory()
+
         def e2e_step():
             frames_e2e.copy_(host, non_blocking=True)
             plan.structure_function(frames_e2e, D, stream)
             plan.azimuthal_average(D, Dr, counts, stream)
+            plan.fit(Dr, N_BINS, ddm._binding.DDM_FIT_LM, None, fit_params, None, None, None, stream)
             Dr_host.copy_(Dr, non_blocking=True)
+            params_host.copy_(fit_params, non_blocking=True)
 
         for _ in range(max(2, args.warmup)):
             e2e_step()
@@ -318,8 +389,14 @@ def run_ours(args):
             e_ms = float(tt.item())
         e2e = {"value": n_gpus * N_FRAMES * k_e2e / (e_ms / 1e3), "unit": "frames/s",
                "h2d_bytes_per_step": int(host.numel() * host.element_size()),
-               "d2h_bytes_per_step": int(Dr_host.numel() * Dr_host.element_size()),
+               "d2h_bytes_per_step": int(Dr_host.numel() * Dr_host.element_size()
+                                         + params_host.numel() * params_host.element_size()),
                "steps": k_e2e}
+
+    # ---- fit of the 362 radial curves: plain LM vs LM seeded by the trained MLP
+    fit_cmp = None
+    if rank == 0 and not args.no_fit_compare:
+        fit_cmp = compare_fits(ddm, plan, Dr, stream)
 
     # ---- FP64 oracle on a bounded sample: CPU baseline and max scaled error of this run
     cpu = None
@@ -357,15 +434,18 @@ def run_ours(args):
                      "achieved": tm_achieved, "peak": peak, "unit": "GB/s",
                      "frac": tm_achieved / peak, "peak_kind": peak_kind,
                      "traffic": traffic, "algorithmic_bytes": TEMPORAL_BYTES},
-        "stages_ms": {"spatial_fft": sp_ms, "temporal_sf": tm_ms, "azimuthal_average": rd_ms},
+        "stages_ms": {"spatial_fft": sp_ms, "temporal_sf": tm_ms, "azimuthal_average": rd_ms,
+                      "fit_lm": ft_ms},
         "step_roofline": {"algorithmic_bytes": STEP_BYTES,
                           "achieved_gbs": STEP_BYTES / ((sp_ms + tm_ms) / 1e3) / 1e9,
                           "frac": STEP_BYTES / ((sp_ms + tm_ms) / 1e3) / 1e9 / peak,
                           "spatial_gbs": sp_achieved, "spatial_frac": sp_achieved / peak},
         "max_rel_err": max_err,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 6 * args.steps,
         "clocks": clocks,
     }
+    if fit_cmp:
+        out["fit"] = fit_cmp
     if e2e:
         out["e2e"] = e2e
     if cpu:

@@ -44,7 +44,7 @@ typedef enum ddm_status {
     DDM_ERR_UNSUPPORTED = 2,   /* legal request this build does not implement */
     DDM_ERR_OOM = 3,           /* device allocation failed or exceeds max_workspace_bytes */
     DDM_ERR_CUDA = 4,          /* a CUDA runtime call failed (no device, launch error) */
-    DDM_ERR_TIMEOUT = 5,       /* reserved: a bounded device wait gave up */
+    DDM_ERR_TIMEOUT = 5,       /* a bounded device wait (tile copy) gave up */
     DDM_ERR_NUMERIC = 6,       /* a kernel met a non-finite value */
     DDM_ERR_NO_WORKSPACE = 7   /* reserved */
 } ddm_status;
@@ -108,8 +108,9 @@ ddm_status ddm_plan_set_workspace(ddm_plan p, void* dev_ptr, size_t bytes);
 /* n_q = H * (W/2 + 1), the number of stored wave vectors. */
 ddm_status ddm_plan_n_q(ddm_plan p, int64_t* n_q);
 
-/* Kernel-detected status of the last completed call on this plan (DDM_OK or
- * DDM_ERR_NUMERIC); reading it resets it to DDM_OK.  Synchronise the stream first. */
+/* Kernel-detected status of the last completed calls on this plan (DDM_OK,
+ * DDM_ERR_NUMERIC, or DDM_ERR_TIMEOUT if a tile copy did not complete within its bounded
+ * wait); reading it resets it to DDM_OK.  Synchronise the stream first. */
 ddm_status ddm_plan_last_device_status(ddm_plan p, ddm_status* out);
 
 /* ---- the hot path ---------------------------------------------------------------- */

@@ -280,7 +280,7 @@ ddm_status ddm_plan_last_device_status(ddm_plan p, ddm_status* out) {
         cudaGetLastError();
         return DDM_ERR_CUDA;
     }
-    *out = (h & 1u) ? DDM_ERR_NUMERIC : DDM_OK;
+    *out = (h & 2u) ? DDM_ERR_TIMEOUT : (h & 1u) ? DDM_ERR_NUMERIC : DDM_OK;
     return DDM_OK;
 }
 

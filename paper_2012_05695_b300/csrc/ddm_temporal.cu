@@ -22,14 +22,58 @@
 // reads whole 128-byte row segments F[t][q0 .. q0+QT) of the [t][q] spectrum, and the
 // thread mapping (q fastest, then transform thread i) turns them into per-q sequences
 // in registers (thread i of q holds t = i + T u).
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "ddm_fft.cuh"
 #include "ddm_internal.h"
 
 namespace ddm {
 namespace {
+
+// ---- TMA (bulk tensor copies) and mbarrier helpers, inline PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y),
+        "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"(map), "r"(x),
+                 "r"(y) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// A bounded wait on the tile barrier: about two seconds of polling, then false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > 4000000000LL) return false;
+    }
+    return true;
+}
 
 template <int LOG2L>
 struct TShape {
@@ -43,11 +87,16 @@ struct TShape {
     // aligned rows (float4 stores) when QT == 16
     static constexpr int DSTRIDE = L + (QT >= 32 ? 1 : (QT == 16 ? 4 : 32 / QT));
     static constexpr int RED = (P > 2 * T ? P : 2 * T);
+    // tiles of 16 wave vectors and L >= 256 frames arrive by TMA: boxes of 16 complex x 256
+    // frames (32 KB) straight into the exchange buffer, which has the same [t][16] layout
+    static constexpr bool USE_TMA = (QT == 16) && (L >= 256);
+    static constexpr int BOX_T = 256;
+    static constexpr int NBOX = L / BOX_T;
     // shared memory carve-up (bytes)
     static constexpr size_t OFF_TW = 0;
     static constexpr size_t OFF_TW2 = OFF_TW + (T > 1 ? L : 0) * sizeof(float2);
     static constexpr size_t OFF_INV = OFF_TW2 + (size_t)L * sizeof(float2);
-    static constexpr size_t OFF_XS = (OFF_INV + (size_t)L * sizeof(float) + 15) & ~size_t(15);
+    static constexpr size_t OFF_XS = (OFF_INV + (size_t)L * sizeof(float) + 1023) & ~size_t(1023);
     static constexpr size_t OFF_AB = OFF_XS + (size_t)L * QT * sizeof(float2);
     static constexpr size_t OFF_HT = OFF_AB + (size_t)L * QT * sizeof(float);
     static constexpr size_t OFF_MU = OFF_HT + (size_t)2 * (KD > 0 ? KD : 1) * QT * sizeof(float2);
@@ -79,10 +128,11 @@ __device__ __forceinline__ int public_q(int s, int H, int Wh, int lwh) {
 
 template <int LOG2L>
 __global__ void __launch_bounds__(TShape<LOG2L>::NT, TShape<LOG2L>::NT == 512 ? 1 : 2)
-temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs a) {
+temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs a,
+                   const __grid_constant__ CUtensorMap tmap) {
     using C = TShape<LOG2L>;
     constexpr int L = C::L, P = C::P, T = C::T, NT = C::NT, QT = C::QT, KD = C::KD;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw + C::OFF_TW);
     float2* tw2 = reinterpret_cast<float2*>(smem_raw + C::OFF_TW2);
     float* inv = reinterpret_cast<float*>(smem_raw + C::OFF_INV);
@@ -96,6 +146,14 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
     float2* red2 = reinterpret_cast<float2*>(smem_raw + C::OFF_RED);
 
     const int tid = threadIdx.x;
+    __shared__ uint64_t tile_bar;
+    uint32_t bar_phase = 0;
+    if constexpr (C::USE_TMA) {
+        if (tid == 0) {
+            mbar_init(&tile_bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
     if constexpr (T > 1) {
         for (int k = tid; k < L; k += NT) tw[k] = a.tw[k];
     }
@@ -113,6 +171,22 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
     const uint32_t nq32 = (uint32_t)nq;   // N * n_q < 2^32 (checked at plan creation)
     const AddrInterleaved<QT> addr{ql};
     bool bad = false;
+    bool timed_out = false;
+    // Copy tile `tl` into xs ([t][16] complex, zeros beyond N and n_q) and wait for it.
+    // Precondition: every thread is done with xs (a barrier was just passed).
+    auto load_tile = [&](int64_t tl) -> bool {
+        if (tid == 0) {
+            fence_proxy_async();
+            mbar_expect_tx(&tile_bar, (uint32_t)(C::NBOX * C::BOX_T * QT * sizeof(float2)));
+#pragma unroll
+            for (int b = 0; b < C::NBOX; ++b)
+                tma_load_2d(xs + b * C::BOX_T * QT, &tmap, (int)(2 * tl * QT), b * C::BOX_T, &tile_bar);
+        }
+        const bool ok = mbar_wait_bounded(&tile_bar, bar_phase);
+        bar_phase ^= 1u;
+        // the decision to give up must be the same in every thread (barriers follow)
+        return __syncthreads_or(ok ? 0 : 1) == 0;
+    };
 
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         const int64_t s = tile * QT + ql;
@@ -120,7 +194,11 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         const float2* src = spec + (valid ? s : 0);
 
         // ---- prefetch the next tile of this CTA into L2: its DRAM fetch overlaps this tile
-        {
+        if constexpr (C::USE_TMA) {
+            const int64_t tn = tile + gridDim.x;
+            if (tid < C::NBOX && tn < a.n_tiles)
+                tma_prefetch_2d(&tmap, (int)(2 * tn * QT), tid * C::BOX_T);
+        } else {
             const int64_t sn = (tile + gridDim.x) * QT + ql;
             if (sn < nq) {
                 const float2* pn = spec + sn;
@@ -135,11 +213,20 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         // ---- load the time sequence (cyclic layout) and remove its mean
         float2 v[P];
         float2 part = make_float2(0.f, 0.f);
+        if constexpr (C::USE_TMA) {
+            if (!load_tile(tile)) { timed_out = true; break; }
 #pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int t = i + T * u;
-            v[u] = (valid && t < N) ? __ldg(src + (uint32_t)t * nq32) : make_float2(0.f, 0.f);
-            part = cadd(part, v[u]);
+            for (int u = 0; u < P; ++u) {
+                v[u] = xs[(i + T * u) * QT + ql];
+                part = cadd(part, v[u]);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+                const int t = i + T * u;
+                v[u] = (valid && t < N) ? __ldg(src + (uint32_t)t * nq32) : make_float2(0.f, 0.f);
+                part = cadd(part, v[u]);
+            }
         }
         red2[i * QT + ql] = part;
         __syncthreads();
@@ -171,11 +258,21 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         for (int u = 0; u < P; ++u) ab[(i + T * u) * QT + ql] = cabs2(v[u]);
 
         // ---- even bins: L-point DFT of g (reloaded; the tile is still in L2)
-        const float2* src2 = opaque_ptr(src);
+        if constexpr (C::USE_TMA) {
+            if (!load_tile(tile)) { timed_out = true; break; }
 #pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int t = i + T * u;
-            v[u] = (valid && t < N) ? csub(__ldg(src2 + (uint32_t)t * nq32), mean) : make_float2(0.f, 0.f);
+            for (int u = 0; u < P; ++u) {
+                const int t = i + T * u;
+                v[u] = (t < N) ? csub(xs[t * QT + ql], mean) : make_float2(0.f, 0.f);
+            }
+            __syncthreads();   // tile read: the exchange buffer is reused by the transform
+        } else {
+            const float2* src2 = opaque_ptr(src);
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+                const int t = i + T * u;
+                v[u] = (valid && t < N) ? csub(__ldg(src2 + (uint32_t)t * nq32), mean) : make_float2(0.f, 0.f);
+            }
         }
         fft_cyclic<L, false>(v, i, xs, addr, tw, SyncBlock{});
 #pragma unroll
@@ -208,6 +305,9 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         const float2* src3 = opaque_ptr(src);
         constexpr int G = P / T;
         float rowv[G][T];
+        if constexpr (C::USE_TMA) {
+            if (!load_tile(tile)) { timed_out = true; break; }
+        }
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int r = i + T * g;
@@ -216,7 +316,11 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
             for (int jj = 0; jj < T; ++jj) {
                 const int t = r * T + jj;
                 float e = 0.f;
-                if (valid && t < N) e = cabs2(csub(__ldg(src3 + (uint32_t)t * nq32), mean));
+                if constexpr (C::USE_TMA) {
+                    if (t < N) e = cabs2(csub(xs[t * QT + ql], mean));
+                } else {
+                    if (valid && t < N) e = cabs2(csub(__ldg(src3 + (uint32_t)t * nq32), mean));
+                }
                 acc += e;
                 rowv[g][jj] = acc;
             }
@@ -305,12 +409,57 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         }
         __syncthreads();
     }
+    if (timed_out) {
+        // a tile copy never completed: report it; give an outstanding copy a last bounded
+        // chance to land before the CTA's shared memory goes away
+        atomicOr(a.status, 2u);
+        mbar_wait_bounded(&tile_bar, bar_phase);
+    }
     if (bad) atomicOr(a.status, 1u);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2D view of the spectrum as float32 [N][2 n_q]; boxes of 32 floats (16 complex) x 256 rows;
+// rows >= N and columns >= 2 n_q read as zero.
+bool make_spectrum_map(CUtensorMap* map, const float2* spec, int64_t n_q, int N) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * n_q), (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)(2 * n_q * sizeof(float))};
+    const cuuint32_t box[2] = {32, 256};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(spec), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int LOG2L>
 ddm_status launch_t(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
     using C = TShape<LOG2L>;
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    if constexpr (C::USE_TMA) {
+        if ((reinterpret_cast<uintptr_t>(spec) & 15) != 0) return DDM_ERR_INVALID_ARG;
+        if (!make_spectrum_map(&tmap, spec, p->n_q, p->d.N)) return DDM_ERR_CUDA;
+    }
     TArgs a;
     a.N = p->d.N;
     a.kd = p->kd;
@@ -329,7 +478,7 @@ ddm_status launch_t(const ddm_plan_s* p, const float2* spec, float* D, cudaStrea
         cudaSuccess)
         return DDM_ERR_CUDA;
     const int64_t grid = a.n_tiles < p->n_sm ? a.n_tiles : p->n_sm;
-    k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(spec, D, a);
+    k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(spec, D, a, tmap);
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 

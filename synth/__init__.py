@@ -174,20 +174,24 @@ def blobs_512x512x1024(seed: int = 0, N: int = 1024, H: int = 512, W: int = 512)
 
 
 # Fit-stage data: curves of known parameters, and initial network weights.
-def stretched_exp_curves(n: int, N: int, seed: int, noise_rel: float = 0.01):
+def stretched_exp_curves(n: int, N: int, seed: int, noise_rel: float = 0.01,
+                         log10_tau=(0.3, 2.6), log10_b_over_a=None):
     """n curves D(m), m = 0..N-1, with D(0) = 0 and, for m >= 1,
     D(m) = A (1 - exp(-(m / tau)^beta)) + B times (1 + noise_rel * N(0, 1)).
 
-    A = s * 10^U(-0.3, 0.3) with a per-curve scale s = 10^U(2, 9); tau = 10^U(0.3, 2.6);
-    beta = U(0.5, 1.1); B = A * U(0, 0.5).  Returns (D [n, N] float32, labels [n, 4] as
-    (A, tau, beta, B) float64).
+    A = s * 10^U(-0.3, 0.3) with a per-curve scale s = 10^U(2, 9); tau = 10^U(log10_tau);
+    beta = U(0.5, 1.1); B = A * U(0, 0.5), or A * 10^U(log10_b_over_a) when given.
+    Returns (D [n, N] float32, labels [n, 4] as (A, tau, beta, B) float64).
     """
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), 0xF17])))
     scale = 10.0 ** rng.uniform(2, 9, n)
     A = scale * 10.0 ** rng.uniform(-0.3, 0.3, n)
-    tau = 10.0 ** rng.uniform(0.3, 2.6, n)
+    tau = 10.0 ** rng.uniform(log10_tau[0], log10_tau[1], n)
     beta = rng.uniform(0.5, 1.1, n)
-    B = A * rng.uniform(0.0, 0.5, n)
+    if log10_b_over_a is None:
+        B = A * rng.uniform(0.0, 0.5, n)
+    else:
+        B = A * 10.0 ** rng.uniform(log10_b_over_a[0], log10_b_over_a[1], n)
     m = np.arange(N, dtype=np.float64)[None, :]
     D = A[:, None] * (1.0 - np.exp(-np.power(m / tau[:, None], beta[:, None]))) + B[:, None]
     D *= 1.0 + noise_rel * rng.standard_normal(D.shape)
