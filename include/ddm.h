@@ -58,6 +58,15 @@ typedef enum ddm_precision {
                                  differences with FP64 accumulation (cancellation-free) */
 } ddm_precision;
 
+/* Kernels of step one.  Both give the same spectrum (to FP32 rounding). */
+typedef enum ddm_spatial_path {
+    DDM_SPATIAL_TWO_PASS = 0,  /* row pass (rows staged by bulk copies) then column pass;
+                                  the spectrum makes one extra round trip through HBM */
+    DDM_SPATIAL_FUSED = 1      /* square frames 64..512: one frame per thread-block cluster,
+                                  rows exchanged through distributed shared memory; other
+                                  shapes fall back to the two-pass kernels */
+} ddm_spatial_path;
+
 typedef struct ddm_plan_desc {
     int H, W;          /* frame height and width in pixels (powers of two, 2..1024) */
     int N;             /* number of frames, 1 .. 1024 */
@@ -72,6 +81,7 @@ typedef struct ddm_plan_desc {
     int fix_lags;      /* DDM_PREC_FP32_FP64FIX: number of leading lags recomputed (0 = 8) */
     size_t max_workspace_bytes; /* 0 = no limit; else plan creation fails with
                                    DDM_ERR_OOM if the workspace would exceed it */
+    int spatial_path;  /* ddm_spatial_path: which step-one kernels run */
 } ddm_plan_desc;
 
 typedef struct ddm_plan_s* ddm_plan;

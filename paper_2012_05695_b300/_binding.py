@@ -29,6 +29,9 @@ DDM_IN_F32 = 1
 DDM_PREC_FP32 = 0
 DDM_PREC_FP32_FP64FIX = 1
 
+DDM_SPATIAL_TWO_PASS = 0
+DDM_SPATIAL_FUSED = 1
+
 DDM_FIT_LM = 0
 DDM_FIT_MLP = 1
 DDM_FIT_MLP_LM = 2
@@ -53,6 +56,7 @@ class ddm_plan_desc(ctypes.Structure):
         ("dtype", ctypes.c_int), ("precision", ctypes.c_int), ("M", ctypes.c_int),
         ("n_bins", ctypes.c_int), ("subtract_ref", ctypes.c_int), ("fix_lags", ctypes.c_int),
         ("max_workspace_bytes", ctypes.c_size_t),
+        ("spatial_path", ctypes.c_int),
     ]
 
 
@@ -157,7 +161,7 @@ class Plan:
 
     def __init__(self, H: int, W: int, N: int, dtype: str = "u16", n_bins: int = 0,
                  precision: int = DDM_PREC_FP32, subtract_ref: int = 1, M: int = 0,
-                 fix_lags: int = 0, max_workspace_bytes: int = 0):
+                 fix_lags: int = 0, max_workspace_bytes: int = 0, spatial_path: int = 0):
         L = lib()
         d = ddm_plan_desc()
         _check(L.ddm_plan_desc_init(ctypes.byref(d), H, W, N), "ddm_plan_desc_init")
@@ -168,6 +172,7 @@ class Plan:
         d.M = M
         d.fix_lags = fix_lags
         d.max_workspace_bytes = max_workspace_bytes
+        d.spatial_path = spatial_path
         self.desc = d
         self.H, self.W, self.N, self.n_bins = H, W, N, n_bins
         self.dtype = dtype

@@ -105,6 +105,8 @@ ddm_status validate(const ddm_plan_desc* d) {
     if (d->subtract_ref != 0 && d->subtract_ref != 1) return DDM_ERR_INVALID_ARG;
     if (d->n_bins < 0 || d->n_bins > (1 << 20)) return DDM_ERR_INVALID_ARG;
     if (d->fix_lags < 0) return DDM_ERR_INVALID_ARG;
+    if (d->spatial_path != DDM_SPATIAL_TWO_PASS && d->spatial_path != DDM_SPATIAL_FUSED)
+        return DDM_ERR_INVALID_ARG;
     const int L = 1 << ilog2(d->N);
     if (d->M != 0) {
         if ((int64_t)d->M < 2 * (int64_t)d->N - 1) return DDM_ERR_INVALID_ARG;

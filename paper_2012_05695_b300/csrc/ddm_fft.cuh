@@ -202,6 +202,18 @@ struct AddrPadded {
     __device__ __forceinline__ int operator()(int idx) const { return base + idx + idx / T; }
 };
 
+// Transform-major without padding: the index is XOR-swizzled with its own block number,
+// idx ^ ((idx / T) mod T), so that both exchange access patterns (consecutive idx in
+// pass 1, stride-T idx in pass 2) spread over all banks.  L * (#transforms) elements.
+template <int L>
+struct AddrSwizzled {
+    int base;   // transform index * L
+    static constexpr int T = FftShape<L>::T;
+    __device__ __forceinline__ int operator()(int idx) const {
+        return base + (idx ^ ((idx / T) & (T - 1)));
+    }
+};
+
 struct SyncBlock {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };

@@ -234,11 +234,444 @@ cudaError_t dispatch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
 
 size_t spectrum_frame_stride(const ddm_plan_s* p) { return (size_t)p->n_q; }
 
+bool fused_spatial_supported(const ddm_plan_s* p);
+ddm_status launch_spatial_fused(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
+bool rows_bulk_supported(const ddm_plan_s* p, const void* frames);
+cudaError_t launch_rows_bulk(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
+
+// Path: DDM_SPATIAL_FUSED (cluster kernel) where supported and asked for; otherwise the
+// row pass (bulk-staged where rows allow it) followed by the column pass.
 ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
-    cudaError_t e = (p->d.dtype == DDM_IN_U16) ? dispatch_rows<uint16_t>(p, frames, spec, s)
-                                               : dispatch_rows<float>(p, frames, spec, s);
+    if (p->d.spatial_path == DDM_SPATIAL_FUSED && fused_spatial_supported(p) &&
+        (reinterpret_cast<uintptr_t>(frames) & 15) == 0)
+        return launch_spatial_fused(p, frames, spec, s);
+    cudaError_t e;
+    if (rows_bulk_supported(p, frames))
+        e = launch_rows_bulk(p, frames, spec, s);
+    else
+        e = (p->d.dtype == DDM_IN_U16) ? dispatch_rows<uint16_t>(p, frames, spec, s)
+                                       : dispatch_rows<float>(p, frames, spec, s);
     if (e != cudaSuccess) return DDM_ERR_CUDA;
     e = dispatch_cols(p, spec, s);
+    return e == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
+}
+
+}  // namespace ddm
+
+// =====================================================================================
+// Fused one-pass step one for square frames (side S <= 512): a cluster of CL CTAs owns
+// one frame at a time (persistent over frames).  CTAs of 256 threads and ~68 KB of shared
+// memory, so that two or three share an SM and hide each other's waits (512 x 512: a
+// 16-CTA cluster, which needs the non-portable cluster size).  CTA r of the cluster
+//   1. bulk-copies its S/CL consecutive rows of frame t into shared memory (one 1-D
+//      cp.async.bulk per 16 KB, mbarrier with a bounded wait) and subtracts frame 0
+//      (read through L2, where it stays: every cluster uses it);
+//   2. transforms its rows (two real rows per complex FFT) and splits them;
+//   3. writes every output value straight into the shared memory of the CTA that owns
+//      its column block (distributed shared memory, st.shared::cluster), cluster barrier;
+//   4. transforms its S/2/CL columns (column 0 of CTA 0 holds the packed DC / Nyquist
+//      pair and is unpacked) and stores 256-byte row segments of the [t][q] spectrum.
+// No intermediate spectrum ever goes through HBM.
+// =====================================================================================
+namespace ddm {
+namespace {
+
+__device__ __forceinline__ uint32_t cvta_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void st_cluster_f2(uint32_t local_addr, uint32_t rank, float2 v) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(remote), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void mbar_init_s(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cvta_smem(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_s(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok) : "r"(cvta_smem(bar)), "r"(parity) : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > 4000000000LL) return false;
+    }
+}
+
+template <int S, int CL>
+struct FusedShape {
+    static constexpr int T = FftShape<S>::T, P = FftShape<S>::P;
+    static constexpr int RH = S / CL;            // rows per CTA
+    static constexpr int PAIRS = RH / 2;         // row pairs per CTA
+    static constexpr int CW = S / 2 / CL;        // stored columns per CTA
+    static constexpr int NT = PAIRS * T;         // threads
+    static_assert(CW * T == NT, "row and column phases use the same threads");
+    static constexpr int XELEMS = PAIRS * S;     // complex elements of the shared region
+    static_assert(XELEMS == CW * S, "region holds the CTA's rows and its columns");
+    static constexpr size_t BYTES = sizeof(float2) * (size_t)XELEMS + (T > 1 ? sizeof(float2) * S : 0);
+};
+
+template <int S, int CL, typename In>
+__global__ void __launch_bounds__(FusedShape<S, CL>::NT, FusedShape<S, CL>::NT <= 256 ? 2 : 1)
+fused_r2c_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int N, int subtract_ref,
+                 const float2* __restrict__ tw_g, int n_clusters, unsigned* status) {
+    using C = FusedShape<S, CL>;
+    constexpr int T = C::T, P = C::P, NT = C::NT, PAIRS = C::PAIRS, CW = C::CW, RH = C::RH;
+    constexpr int Wh = S / 2;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float2* X = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = X + C::XELEMS;
+    __shared__ uint64_t bar;
+    const int tid = threadIdx.x;
+    const uint32_t rank = (CL > 1) ? cluster_rank() : 0u;
+    const int cluster = blockIdx.x / CL;
+    if (tid == 0) {
+        mbar_init_s(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if constexpr (T > 1) {
+        for (int k = tid; k < S; k += NT) tw[k] = tw_g[k];
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    bool timeout = false;
+    // row phase mapping: transform j (row pair), thread i; column phase: column c, thread ic
+    const int i = tid % T, j = tid / T;
+    const int c = tid % CW, ic = tid / CW;
+    constexpr uint32_t kRowBytes = S * sizeof(In);
+    constexpr uint32_t kBytes = RH * kRowBytes;
+    constexpr uint32_t kChunk = kBytes < 16384u ? kBytes : 16384u;
+
+    for (int t = cluster; t < N; t += n_clusters) {
+        const In* rows = frames + ((size_t)t * S + (size_t)rank * RH) * S;
+        // ---- 1. rows of frame t -> shared memory (bulk copies), frame 0 via L2
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cvta_smem(&bar)),
+                         "r"(kBytes) : "memory");
+            for (uint32_t off = 0; off < kBytes; off += kChunk)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                    ::"r"(cvta_smem(reinterpret_cast<unsigned char*>(X) + off)),
+                    "l"(reinterpret_cast<const unsigned char*>(rows) + off), "r"(kChunk),
+                    "r"(cvta_smem(&bar)) : "memory");
+        }
+        if (t + n_clusters < N && tid == 0) {
+            const In* nxt = frames + ((size_t)(t + n_clusters) * S + (size_t)rank * RH) * S;
+            for (uint32_t off = 0; off < kBytes; off += kChunk)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                                 reinterpret_cast<const unsigned char*>(nxt) + off), "r"(kChunk) : "memory");
+        }
+        if (!mbar_wait_s(&bar, phase)) timeout = true;   // keep going: every barrier must match
+        phase ^= 1u;
+        const In* stage = reinterpret_cast<const In*>(X);
+        const In* ref = frames + (size_t)rank * RH * S;
+        float2 v[P];
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int x = i + T * u;
+            const int ra = (2 * j) * S + x, rb = ra + S;
+            float a, b;
+            if constexpr (sizeof(In) == 2) {
+                a = (float)((int)stage[ra] - (subtract_ref ? (int)__ldg(ref + ra) : 0));
+                b = (float)((int)stage[rb] - (subtract_ref ? (int)__ldg(ref + rb) : 0));
+            } else {
+                a = subtract_ref ? (float)stage[ra] - (float)__ldg(ref + ra) : (float)stage[ra];
+                b = subtract_ref ? (float)stage[rb] - (float)__ldg(ref + rb) : (float)stage[rb];
+            }
+            v[u] = make_float2(a, b);
+        }
+        __syncthreads();   // staging read: the region becomes the row exchange buffer
+
+        // ---- 2. row transforms (z = row a + i row b), then split into the two rows
+        const AddrSwizzled<S> raddr{j * S};
+        fft_cyclic<S, false>(v, i, X, raddr, tw, SyncBlock{});
+#pragma unroll
+        for (int u = 0; u < P; ++u) X[raddr(i + T * u)] = v[u];
+        __syncthreads();
+        float2 outa[P / 2], outb[P / 2];
+#pragma unroll
+        for (int u = 0; u < P / 2; ++u) {
+            const int k = i + T * u;                      // k < S/2
+            const float2 z = X[raddr(k)];
+            if (k == 0) {
+                const float2 zn = X[raddr(S / 2)];
+                outa[u] = make_float2(z.x, zn.x);         // A[0], A[S/2] (both real)
+                outb[u] = make_float2(z.y, zn.y);
+            } else {
+                const float2 zr = X[raddr(S - k)];
+                outa[u] = make_float2(0.5f * (z.x + zr.x), 0.5f * (z.y - zr.y));
+                outb[u] = make_float2(0.5f * (z.y + zr.y), 0.5f * (zr.x - z.x));
+            }
+        }
+        // ---- 3. every CTA is done with its region; scatter (row y, kx) to kx's owner
+        if constexpr (CL > 1) cluster_sync_all(); else __syncthreads();
+        const int ya = rank * RH + 2 * j, yb = ya + 1;
+#pragma unroll
+        for (int u = 0; u < P / 2; ++u) {
+            const int k = i + T * u;
+            const uint32_t dst = (uint32_t)(k / CW);
+            const int col = k - (int)dst * CW;
+            if constexpr (CL > 1) {
+                st_cluster_f2(cvta_smem(X + ya * CW + col), dst, outa[u]);
+                st_cluster_f2(cvta_smem(X + yb * CW + col), dst, outb[u]);
+            } else {
+                X[ya * CW + col] = outa[u];
+                X[yb * CW + col] = outb[u];
+            }
+        }
+        if constexpr (CL > 1) cluster_sync_all(); else __syncthreads();
+
+        // ---- 4. column transforms of this CTA's CW stored columns
+        float2 w[P];
+#pragma unroll
+        for (int u = 0; u < P; ++u) w[u] = X[(ic + T * u) * CW + c];
+        __syncthreads();
+        const AddrInterleaved<CW> caddr{c};
+        fft_cyclic<S, false>(w, ic, X, caddr, tw, SyncBlock{});
+        const int kx = rank * CW + c;
+        float2* fr = spec + (size_t)t * (size_t)(S * (Wh + 1));
+        if (rank == 0) {
+            // column 0 holds the packed DC / Nyquist pair: needs C[-ky]
+#pragma unroll
+            for (int u = 0; u < P; ++u)
+                if (c == 0) X[ic + T * u] = w[u];
+            __syncthreads();
+        }
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int ky = ic + T * u;
+            if (rank == 0 && c == 0) {
+                const float2 cc = w[u];
+                const float2 cr = X[(S - ky) & (S - 1)];
+                fr[(size_t)ky * Wh] = make_float2(0.5f * (cc.x + cr.x), 0.5f * (cc.y - cr.y));
+                fr[(size_t)S * Wh + ky] = make_float2(0.5f * (cc.y + cr.y), 0.5f * (cr.x - cc.x));
+            } else {
+                fr[(size_t)ky * Wh + kx] = w[u];
+            }
+        }
+        __syncthreads();   // the region is rewritten by the next frame's copy
+    }
+    if (timeout && tid == 0) atomicOr(status, 2u);
+    if constexpr (CL > 1) cluster_sync_all();   // no CTA leaves while a peer may still write
+}
+
+template <int S, int CL, typename In>
+cudaError_t launch_fused(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+    using C = FusedShape<S, CL>;
+    auto k = fused_r2c_kernel<S, CL, In>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
+    if (e != cudaSuccess) return e;
+    if (CL > 8) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(C::NT);
+    cfg.dynamicSmemBytes = C::BYTES;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int max_clusters = 0;
+    cfg.gridDim = dim3(CL * 1024);
+    e = cudaOccupancyMaxActiveClusters(&max_clusters, (void*)k, &cfg);
+    if (e != cudaSuccess || max_clusters < 1) {
+        cudaGetLastError();
+        max_clusters = p->n_sm / CL;
+    }
+    const int n_clusters = max_clusters < p->d.N ? max_clusters : p->d.N;
+    cfg.gridDim = dim3(CL * n_clusters);
+    return cudaLaunchKernelEx(&cfg, k, (const In*)frames, spec, p->d.N, p->d.subtract_ref,
+                              (const float2*)p->tw_col, n_clusters, p->dev_status);
+}
+
+template <typename In>
+cudaError_t dispatch_fused(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+    switch (p->d.H) {
+        case 64: return launch_fused<64, 1, In>(p, frames, spec, s);
+        case 128: return launch_fused<128, 2, In>(p, frames, spec, s);
+        case 256: return launch_fused<256, 4, In>(p, frames, spec, s);
+        case 512: return launch_fused<512, 16, In>(p, frames, spec, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+namespace {
+
+// ---- row pass with bulk-staged input -------------------------------------------------
+// A CTA owns PAIRS consecutive row pairs of one frame.  Those rows, and the same rows of
+// frame 0, are contiguous in memory: two cp.async.bulk copies bring them into shared
+// memory (mbarrier with a bounded wait) instead of 2-byte scattered loads, and the region
+// then serves as the transform's exchange buffer (XOR-swizzled, no padding).  ~64 KB per
+// CTA, so three CTAs share an SM.
+template <int W, typename In>
+struct RowBulkShape {
+    static constexpr int T = FftShape<W>::T, P = FftShape<W>::P;
+    static constexpr int BYTES_ROW = W * (int)sizeof(In);
+    static constexpr int P1 = 256 / T;
+    static constexpr int P2 = 16384 / BYTES_ROW > 0 ? 16384 / BYTES_ROW : 1;
+    static constexpr int PAIRS = (P1 < P2 ? P1 : P2) < 1 ? 1 : (P1 < P2 ? P1 : P2);
+    static constexpr int NT = PAIRS * T;
+    static constexpr size_t STAGE = (size_t)2 * 2 * PAIRS * BYTES_ROW;   // frame rows + frame-0 rows
+    static constexpr size_t XCH = (size_t)PAIRS * W * sizeof(float2);
+    static constexpr size_t XBYTES = STAGE > XCH ? STAGE : XCH;
+    static constexpr size_t BYTES = XBYTES + (T > 1 ? W * sizeof(float2) : 0);
+};
+
+template <int W, typename In>
+__global__ void __launch_bounds__(RowBulkShape<W, In>::NT)
+row_bulk_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H, size_t frame_stride,
+                int subtract_ref, const float2* __restrict__ tw_g, unsigned* status) {
+    using C = RowBulkShape<W, In>;
+    constexpr int T = C::T, P = C::P, PAIRS = C::PAIRS, NT = C::NT;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float2* X = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = reinterpret_cast<float2*>(smem_raw + C::XBYTES);
+    __shared__ uint64_t bar;
+    const int tid = threadIdx.x;
+    const int t = blockIdx.y;
+    const int pair0 = blockIdx.x * PAIRS;
+    const int npairs = min(PAIRS, H / 2 - pair0);
+    const uint32_t bytes = (uint32_t)(2 * npairs) * C::BYTES_ROW;
+    const In* src = frames + ((size_t)t * H + 2 * pair0) * W;
+    const In* ref = frames + (size_t)(2 * pair0) * W;
+    unsigned char* stage_f = smem_raw;
+    unsigned char* stage_r = smem_raw + (size_t)2 * PAIRS * C::BYTES_ROW;
+    if (tid == 0) {
+        mbar_init_s(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cvta_smem(&bar)),
+                     "r"(subtract_ref ? 2 * bytes : bytes) : "memory");
+        for (uint32_t off = 0; off < bytes; off += 16384u) {
+            const uint32_t n = bytes - off < 16384u ? bytes - off : 16384u;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                ::"r"(cvta_smem(stage_f + off)), "l"(reinterpret_cast<const unsigned char*>(src) + off),
+                "r"(n), "r"(cvta_smem(&bar)) : "memory");
+            if (subtract_ref)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                    ::"r"(cvta_smem(stage_r + off)), "l"(reinterpret_cast<const unsigned char*>(ref) + off),
+                    "r"(n), "r"(cvta_smem(&bar)) : "memory");
+        }
+    }
+    if constexpr (T > 1) {
+        for (int k = tid; k < W; k += NT) tw[k] = tw_g[k];
+    }
+    __syncthreads();                                   // barrier initialised, twiddles in place
+    const bool ok = mbar_wait_s(&bar, 0);
+    const int i = tid % T, j = tid / T;
+    const bool active = j < npairs;
+    const In* fa = reinterpret_cast<const In*>(stage_f) + (size_t)(2 * j) * W;
+    const In* ra = reinterpret_cast<const In*>(stage_r) + (size_t)(2 * j) * W;
+    float2 v[P];
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+        const int x = i + T * u;
+        float a = 0.f, b = 0.f;
+        if (active) {
+            if constexpr (sizeof(In) == 2) {
+                a = (float)((int)fa[x] - (subtract_ref ? (int)ra[x] : 0));
+                b = (float)((int)fa[W + x] - (subtract_ref ? (int)ra[W + x] : 0));
+            } else {
+                a = subtract_ref ? (float)fa[x] - (float)ra[x] : (float)fa[x];
+                b = subtract_ref ? (float)fa[W + x] - (float)ra[W + x] : (float)fa[W + x];
+            }
+        }
+        v[u] = make_float2(a, b);
+    }
+    __syncthreads();                                   // staging read: region becomes the exchange
+    const AddrSwizzled<W> addr{j * W};
+    fft_cyclic<W, false>(v, i, X, addr, tw, SyncBlock{});
+#pragma unroll
+    for (int u = 0; u < P; ++u) X[addr(i + T * u)] = v[u];
+    __syncthreads();
+    if (active) {
+        float2* outa = spec + (size_t)t * frame_stride + (size_t)(2 * (pair0 + j)) * (W / 2);
+        float2* outb = outa + W / 2;
+#pragma unroll
+        for (int u = 0; u < (P + 1) / 2; ++u) {
+            const int k = i + T * u;
+            if (k >= W / 2) break;
+            const float2 z = X[addr(k)];
+            if (k == 0) {
+                const float2 zn = X[addr(W / 2)];
+                outa[0] = make_float2(z.x, zn.x);
+                outb[0] = make_float2(z.y, zn.y);
+            } else {
+                const float2 zr = X[addr(W - k)];
+                outa[k] = make_float2(0.5f * (z.x + zr.x), 0.5f * (z.y - zr.y));
+                outb[k] = make_float2(0.5f * (z.y + zr.y), 0.5f * (zr.x - z.x));
+            }
+        }
+    }
+    if (!ok && tid == 0) atomicOr(status, 2u);
+}
+
+template <int W, typename In>
+cudaError_t launch_rows_bulk_t(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+    using C = RowBulkShape<W, In>;
+    auto k = row_bulk_kernel<W, In>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p->d.H / 2 + C::PAIRS - 1) / C::PAIRS, p->d.N);
+    k<<<grid, C::NT, C::BYTES, s>>>((const In*)frames, spec, p->d.H, (size_t)p->n_q, p->d.subtract_ref,
+                                     p->tw_row, p->dev_status);
+    return cudaGetLastError();
+}
+
+template <typename In>
+cudaError_t dispatch_rows_bulk(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+    switch (p->d.W) {
+        case 4: return launch_rows_bulk_t<4, In>(p, frames, spec, s);
+        case 8: return launch_rows_bulk_t<8, In>(p, frames, spec, s);
+        case 16: return launch_rows_bulk_t<16, In>(p, frames, spec, s);
+        case 32: return launch_rows_bulk_t<32, In>(p, frames, spec, s);
+        case 64: return launch_rows_bulk_t<64, In>(p, frames, spec, s);
+        case 128: return launch_rows_bulk_t<128, In>(p, frames, spec, s);
+        case 256: return launch_rows_bulk_t<256, In>(p, frames, spec, s);
+        case 512: return launch_rows_bulk_t<512, In>(p, frames, spec, s);
+        case 1024: return launch_rows_bulk_t<1024, In>(p, frames, spec, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+// rows of W * sizeof(In) >= 16 bytes, frames 16-byte aligned: bulk-staged row pass
+bool rows_bulk_supported(const ddm_plan_s* p, const void* frames) {
+    const int esize = p->d.dtype == DDM_IN_U16 ? 2 : 4;
+    return p->d.W * esize >= 16 && (reinterpret_cast<uintptr_t>(frames) & 15) == 0;
+}
+
+cudaError_t launch_rows_bulk(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+    return p->d.dtype == DDM_IN_U16 ? dispatch_rows_bulk<uint16_t>(p, frames, spec, s)
+                                    : dispatch_rows_bulk<float>(p, frames, spec, s);
+}
+
+bool fused_spatial_supported(const ddm_plan_s* p) {
+    return p->d.H == p->d.W && (p->d.H == 64 || p->d.H == 128 || p->d.H == 256 || p->d.H == 512);
+}
+
+ddm_status launch_spatial_fused(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+    cudaError_t e = (p->d.dtype == DDM_IN_U16) ? dispatch_fused<uint16_t>(p, frames, spec, s)
+                                               : dispatch_fused<float>(p, frames, spec, s);
     return e == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 

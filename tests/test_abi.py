@@ -61,6 +61,7 @@ def test_desc_init_defaults():
     ("subtract_ref", 2, B.DDM_ERR_INVALID_ARG),
     ("n_bins", -1, B.DDM_ERR_INVALID_ARG),
     ("max_workspace_bytes", 16, B.DDM_ERR_OOM),
+    ("spatial_path", 7, B.DDM_ERR_INVALID_ARG),
 ])
 def test_plan_create_validates_before_touching_the_device(field, value, status):
     d = _desc(8, 8, 4)

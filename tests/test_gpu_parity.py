@@ -49,6 +49,25 @@ def test_spatial_fft_matches_oracle_dft(H, W, N, dtype):
     assert np.all(F[0] == 0)         # frame 0 minus itself
 
 
+@pytest.mark.parametrize("S,N,dtype", [(64, 5, "f32"), (128, 3, "u16"), (256, 4, "f32"),
+                                       (512, 3, "u16"), (512, 40, "u16")])
+def test_spatial_fft_fused_cluster_path_matches_oracle(S, N, dtype):
+    """The cluster kernel (rows exchanged through distributed shared memory)."""
+    import torch
+    frames = _frames(N, S, S, dtype, seed=S + N)
+    plan = ddm.Plan(S, S, N, dtype=dtype, spatial_path=ddm._binding.DDM_SPATIAL_FUSED)
+    spec = torch.empty(2 * N * plan.n_q, dtype=torch.float32, device="cuda")
+    plan.spatial_fft(to_device(frames), spec)
+    torch.cuda.synchronize()
+    F = storage_to_plane(spec.cpu().numpy().view(np.complex64).reshape(N, plan.n_q).astype(np.complex128), S, S)
+    diff = frames.astype(np.float64) - frames[0].astype(np.float64)[None]
+    ref = oracle.dft2(diff, oracle.half_plane_columns(S))
+    for t in range(N):
+        scale = max(np.max(np.abs(ref[t])), 1e-30)
+        assert np.max(np.abs(F[t] - ref[t])) / scale <= 1e-5, t
+    assert plan.last_device_status() == 0
+
+
 def test_spatial_fft_without_reference_subtraction():
     import torch
     H, W, N = 64, 32, 3
