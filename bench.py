@@ -412,6 +412,23 @@ def run_ours(args):
                                          + params_host.numel() * params_host.element_size()),
                "steps": k_e2e}
 
+    # ---- precision tiers on the same stack: the FP32+FP64-fixup temporal stage
+    tiers = {"fp32": {"temporal_ms": tm_ms}}
+    D_fix = None
+    if rank == 0:
+        plan_fix = ddm.Plan(H, W, N_FRAMES, dtype="u16", precision=ddm.DDM_PREC_FP32_FP64FIX)
+        D_fix = torch.empty_like(D)
+        plan.spatial_fft(frames, spec, stream)
+        for _ in range(3):
+            plan_fix.temporal_sf(spec, D_fix, stream)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(10):
+            plan_fix.temporal_sf(spec, D_fix, stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        tiers["fp32_fp64fix"] = {"temporal_ms": f0.elapsed_time(f1) / 10, "fix_lags": 8}
+
     # ---- fit of the 362 radial curves: plain LM vs LM seeded by the trained MLP
     fit_cmp = None
     if rank == 0 and not args.no_fit_compare:
@@ -436,6 +453,13 @@ def run_ours(args):
         torch.cuda.synchronize()
         Dg = D.view(H, W // 2 + 1, N_FRAMES)[:, cols, :].cpu().numpy()
         max_err = oracle.scaled_error(Dg, D_or, s_q)
+        ref = D_or[..., 1:9]
+        tiers["fp32"]["max_rel_err"] = max_err
+        tiers["fp32"]["small_lag_err_rel_D"] = float(np.max(np.abs(Dg[..., 1:9] - ref) / ref))
+        if D_fix is not None:
+            Df = D_fix.view(H, W // 2 + 1, N_FRAMES)[:, cols, :].cpu().numpy()
+            tiers["fp32_fp64fix"]["max_rel_err"] = oracle.scaled_error(Df, D_or, s_q)
+            tiers["fp32_fp64fix"]["small_lag_err_rel_D"] = float(np.max(np.abs(Df[..., 1:9] - ref) / ref))
 
     traffic = profiled_traffic()
     tm_achieved = TEMPORAL_BYTES / (tm_ms / 1e3) / 1e9
@@ -463,6 +487,7 @@ def run_ours(args):
         "gpu_launches": 6 * args.steps,
         "clocks": clocks,
     }
+    out["precision_tiers"] = tiers
     if fit_cmp:
         out["fit"] = fit_cmp
     if e2e:

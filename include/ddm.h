@@ -55,7 +55,9 @@ typedef enum ddm_dtype { DDM_IN_U16 = 0, DDM_IN_F32 = 1 } ddm_dtype;
 typedef enum ddm_precision {
     DDM_PREC_FP32 = 0,   /* FP32 transforms, prefix and suffix sums and combination */
     DDM_PREC_FP32_FP64FIX = 1 /* as FP32, plus: lags 1..fix_lags recomputed by direct
-                                 differences with FP64 accumulation (cancellation-free) */
+                                 differences (Eq. 1), FP32 over each thread's 32 frames and
+                                 FP64 across threads: no cancellation against the power
+                                 sums.  This build: 257 <= N <= 1024, fix_lags <= 8 */
 } ddm_precision;
 
 /* Kernels of step one.  Both give the same spectrum (to FP32 rounding). */
@@ -78,7 +80,8 @@ typedef struct ddm_plan_desc {
     int n_bins;        /* radial bins for ddm_azimuthal_average (0 = no radial stage) */
     int subtract_ref;  /* 1: subtract frame 0 from every frame before the spatial
                           transform (exact in integers for uint16; D is unchanged by it) */
-    int fix_lags;      /* DDM_PREC_FP32_FP64FIX: number of leading lags recomputed (0 = 8) */
+    int fix_lags;      /* DDM_PREC_FP32_FP64FIX: number of leading lags recomputed (0 = 8,
+                          at most 8) */
     size_t max_workspace_bytes; /* 0 = no limit; else plan creation fails with
                                    DDM_ERR_OOM if the workspace would exceed it */
     int spatial_path;  /* ddm_spatial_path: which step-one kernels run */

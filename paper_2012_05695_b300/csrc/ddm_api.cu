@@ -101,7 +101,12 @@ ddm_status validate(const ddm_plan_desc* d) {
     if (d->dtype != DDM_IN_U16 && d->dtype != DDM_IN_F32) return DDM_ERR_INVALID_ARG;
     if (d->precision != DDM_PREC_FP32 && d->precision != DDM_PREC_FP32_FP64FIX)
         return DDM_ERR_INVALID_ARG;
-    if (d->precision == DDM_PREC_FP32_FP64FIX) return DDM_ERR_UNSUPPORTED;
+    if (d->precision == DDM_PREC_FP32_FP64FIX) {
+        // built for the time transforms whose tiles arrive whole in shared memory
+        const int Lf = 1 << ilog2(d->N);
+        if (Lf != 512 && Lf != 1024) return DDM_ERR_UNSUPPORTED;
+        if (d->fix_lags > 8) return DDM_ERR_UNSUPPORTED;
+    }
     if (d->subtract_ref != 0 && d->subtract_ref != 1) return DDM_ERR_INVALID_ARG;
     if (d->n_bins < 0 || d->n_bins > (1 << 20)) return DDM_ERR_INVALID_ARG;
     if (d->fix_lags < 0) return DDM_ERR_INVALID_ARG;

@@ -92,6 +92,7 @@ struct TShape {
     static constexpr bool USE_TMA = (QT == 16) && (L >= 256);
     static constexpr int BOX_T = 256;
     static constexpr int NBOX = L / BOX_T;
+    static constexpr int FIX_MAX = 8;             // most leading lags the FP64 fixup redoes
     // shared memory carve-up (bytes)
     static constexpr size_t OFF_TW = 0;
     static constexpr size_t OFF_TW2 = OFF_TW + (T > 1 ? L : 0) * sizeof(float2);
@@ -113,6 +114,7 @@ struct TArgs {
     int64_t n_q;      // stored wave vectors = spectrum frame stride
     int64_t n_tiles;
     int vec4;         // D rows 16-byte aligned (N % 4 == 0 and D aligned): float4 stores
+    int fix;          // FP64-fixup tier: lags 1..fix by direct differences (0 = off)
     const float2* tw;
     const float2* tw2;
     const float* inv;
@@ -126,7 +128,7 @@ __device__ __forceinline__ int public_q(int s, int H, int Wh, int lwh) {
     return (s - main) * (Wh + 1) + Wh;
 }
 
-template <int LOG2L>
+template <int LOG2L, bool FIXUP>
 __global__ void __launch_bounds__(TShape<LOG2L>::NT, TShape<LOG2L>::NT == 512 ? 1 : 2)
 temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs a,
                    const __grid_constant__ CUtensorMap tmap) {
@@ -308,15 +310,45 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         if constexpr (C::USE_TMA) {
             if (!load_tile(tile)) { timed_out = true; break; }
         }
+        // FP64-fixup tier (tile in shared memory): over its rows each thread also sums
+        // |F(t+m) - F(t)|^2 for m = 1..fix, the direct, cancellation-free form of Eq. 1,
+        // keeping F(t .. t+FIX_MAX) in a sliding register window
+        constexpr int FM = C::FIX_MAX;
+        const int fix = (FIXUP && C::USE_TMA) ? a.fix : 0;
+        float fixp[FM];
+#pragma unroll
+        for (int k = 0; k < FM; ++k) fixp[k] = 0.f;
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int r = i + T * g;
             float acc = 0.f;
+            float2 win[FM + 1];
+            if constexpr (FIXUP && C::USE_TMA) {
+                if (fix > 0) {
+#pragma unroll
+                    for (int k = 0; k < FM; ++k) {
+                        const int tk = r * T + k;
+                        win[k] = tk < N ? xs[tk * QT + ql] : make_float2(0.f, 0.f);
+                    }
+                }
+            }
 #pragma unroll
             for (int jj = 0; jj < T; ++jj) {
                 const int t = r * T + jj;
                 float e = 0.f;
-                if constexpr (C::USE_TMA) {
+                if constexpr (FIXUP && C::USE_TMA) {
+                    if (fix > 0) {
+                        win[FM] = (t + FM < N) ? xs[(t + FM) * QT + ql] : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int m = 1; m <= FM; ++m)
+                            if (m <= fix && t + m < N) fixp[m - 1] += cabs2(csub(win[m], win[0]));
+                        if (t < N) e = cabs2(csub(win[0], mean));
+#pragma unroll
+                        for (int k = 0; k < FM; ++k) win[k] = win[k + 1];
+                    } else {
+                        if (t < N) e = cabs2(csub(xs[t * QT + ql], mean));
+                    }
+                } else if constexpr (C::USE_TMA) {
                     if (t < N) e = cabs2(csub(xs[t * QT + ql], mean));
                 } else {
                     if (valid && t < N) e = cabs2(csub(__ldg(src3 + (uint32_t)t * nq32), mean));
@@ -327,6 +359,13 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
             red[r * QT + ql] = acc;
         }
         __syncthreads();
+        // the tile has been read: the upper half of the exchange buffer takes the fixup partials
+        float* fixpart = xf + (size_t)L * QT;                  // [m][i][ql]
+        if (FIXUP && fix > 0) {
+#pragma unroll
+            for (int k = 0; k < FM; ++k)
+                if (k < fix) fixpart[(k * T + i) * QT + ql] = fixp[k];
+        }
         float total = 0.f;
         float off[G];
 #pragma unroll
@@ -344,6 +383,14 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
             const int r = i + T * g;
 #pragma unroll
             for (int jj = 0; jj < T; ++jj) xf[(r * T + jj) * QT + ql] = rowv[g][jj] + off[g];
+        }
+        __syncthreads();
+        // partials of lag m = i + 1 summed in FP64 over the T threads of each sequence;
+        // D(m) parked in the row-total buffer (free now) until the D rows are staged
+        if (FIXUP && fix > 0 && i < fix && i + 1 < N) {
+            double sum = 0.0;
+            for (int ip = 0; ip < T; ++ip) sum += (double)fixpart[(i * T + ip) * QT + ql];
+            red[i * QT + ql] = (float)(sum / (double)(N - 1 - i));
         }
         __syncthreads();
 
@@ -382,6 +429,7 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
                 xf[ql * DS + m] = acc * inv[m];
             }
         }
+        if (FIXUP && fix > 0 && i < fix && i + 1 < N - kd) xf[ql * DS + i + 1] = red[i * QT + ql];
         __syncthreads();
         if (QT == 16 && a.vec4) {
             const int n4 = N >> 2;
@@ -451,7 +499,7 @@ bool make_spectrum_map(CUtensorMap* map, const float2* spec, int64_t n_q, int N)
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int LOG2L>
+template <int LOG2L, bool FIXUP>
 ddm_status launch_t(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
     using C = TShape<LOG2L>;
     CUtensorMap tmap;
@@ -467,13 +515,14 @@ ddm_status launch_t(const ddm_plan_s* p, const float2* spec, float* D, cudaStrea
     a.Wh = p->Wh;
     a.lwh = ilog2(p->Wh);
     a.vec4 = (p->d.N % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
+    a.fix = (p->d.precision == DDM_PREC_FP32_FP64FIX) ? p->fix_lags : 0;
     a.n_q = p->n_q;
     a.n_tiles = (p->n_q + C::QT - 1) / C::QT;
     a.tw = p->tw_t;
     a.tw2 = p->tw2;
     a.inv = p->inv;
     a.status = p->dev_status;
-    auto k = temporal_sf_kernel<LOG2L>;
+    auto k = temporal_sf_kernel<LOG2L, FIXUP>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
         cudaSuccess)
         return DDM_ERR_CUDA;
@@ -485,18 +534,19 @@ ddm_status launch_t(const ddm_plan_s* p, const float2* spec, float* D, cudaStrea
 }  // namespace
 
 ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
+    const bool fix = p->d.precision == DDM_PREC_FP32_FP64FIX;
     switch (ilog2(p->L)) {
-        case 0: return launch_t<0>(p, spec, D, s);
-        case 1: return launch_t<1>(p, spec, D, s);
-        case 2: return launch_t<2>(p, spec, D, s);
-        case 3: return launch_t<3>(p, spec, D, s);
-        case 4: return launch_t<4>(p, spec, D, s);
-        case 5: return launch_t<5>(p, spec, D, s);
-        case 6: return launch_t<6>(p, spec, D, s);
-        case 7: return launch_t<7>(p, spec, D, s);
-        case 8: return launch_t<8>(p, spec, D, s);
-        case 9: return launch_t<9>(p, spec, D, s);
-        case 10: return launch_t<10>(p, spec, D, s);
+        case 0: return launch_t<0, false>(p, spec, D, s);
+        case 1: return launch_t<1, false>(p, spec, D, s);
+        case 2: return launch_t<2, false>(p, spec, D, s);
+        case 3: return launch_t<3, false>(p, spec, D, s);
+        case 4: return launch_t<4, false>(p, spec, D, s);
+        case 5: return launch_t<5, false>(p, spec, D, s);
+        case 6: return launch_t<6, false>(p, spec, D, s);
+        case 7: return launch_t<7, false>(p, spec, D, s);
+        case 8: return launch_t<8, false>(p, spec, D, s);
+        case 9: return fix ? launch_t<9, true>(p, spec, D, s) : launch_t<9, false>(p, spec, D, s);
+        case 10: return fix ? launch_t<10, true>(p, spec, D, s) : launch_t<10, false>(p, spec, D, s);
         default: return DDM_ERR_UNSUPPORTED;
     }
 }

@@ -268,3 +268,39 @@ def test_side_stream():
     s.synchronize()
     D_ref, s_q = oracle.structure_function(frames)
     assert oracle.scaled_error(D.cpu().numpy().reshape(H, W // 2 + 1, N), D_ref, s_q) <= TOL
+
+
+# ------------------------------------------------------------------ FP64-fixup tier
+@pytest.mark.parametrize("N", [300, 1024])
+def test_fp64_fixup_tier_small_lags_relative_to_D(N):
+    """Slow dynamics: D(1) is ~1e-5 of the plateau, so P1 + P2 - 2 Re C cancels most of
+    its FP32 digits.  The fixup tier recomputes lags 1..8 by direct differences (FP64
+    across threads) and must match the FP64 oracle relative to D itself; the whole D
+    stays within the usual plateau-relative tolerance."""
+    import torch
+    H = W = 16
+    frames = synth.ou_stack(H, W, N, 1e-4, synth.gaussian_spectrum(0.5), 1e-3, seed=N,
+                            dtype=np.float32) + np.float32(5.0)
+    D_ref, s_q = oracle.structure_function(frames)
+    errs = {}
+    for prec in (ddm.DDM_PREC_FP32, ddm.DDM_PREC_FP32_FP64FIX):
+        D, plan, _ = gpu_structure_function(frames, precision=prec)
+        assert oracle.scaled_error(D, D_ref, s_q) <= TOL
+        ref = D_ref[..., 1:9]
+        big = ref > 1e-9 * np.max(ref)
+        errs[prec] = float(np.max(np.abs(D[..., 1:9] - ref)[big] / ref[big]))
+    assert errs[ddm.DDM_PREC_FP32_FP64FIX] <= 2e-5, errs
+    assert errs[ddm.DDM_PREC_FP32_FP64FIX] < errs[ddm.DDM_PREC_FP32], errs
+    print(f"\nsmall-lag error relative to D, N={N}: FP32 {errs[ddm.DDM_PREC_FP32]:.2e}, "
+          f"FP32+FP64 fixup {errs[ddm.DDM_PREC_FP32_FP64FIX]:.2e}")
+
+
+def test_fp64_fixup_tier_blobs_512x512x1024_sampled():
+    frames = synth.blobs_512x512x1024(seed=3)
+    D, _, _ = gpu_structure_function(frames, precision=ddm.DDM_PREC_FP32_FP64FIX)
+    cols = [1, 100, 256]
+    D_ref, s_q = oracle.structure_function(frames, kx_sel=cols)
+    assert oracle.scaled_error(D[:, cols, :], D_ref, s_q) <= TOL
+    ref = D_ref[..., 1:9]
+    err = np.max(np.abs(D[:, cols, 1:9] - ref) / ref)
+    assert err <= 2e-5, err
