@@ -124,6 +124,39 @@ __device__ __forceinline__ float2 twiddle_const(float2 o) {
     }
 }
 
+// e + w o and e - w o for the constant twiddle w = w_R^K.  A general twiddle is applied in
+// factored form, w o = c (o.x - t o.y, o.y + t o.x) with t = s / c (or the same with s
+// factored out when |s| > |c|, so that |t| <= 1): two FMAs build the bracket and four
+// more finish both outputs, six FMA-pipe instructions instead of eight.
+__host__ __device__ constexpr double cx_absd(double x) { return x < 0 ? -x : x; }
+
+template <int R, int K, bool INV>
+__device__ __forceinline__ void bfly_const(float2 e, float2 o, float2& lo, float2& hi) {
+    constexpr int k = ((K % R) + R) % R;
+    if constexpr (k == 0 || 4 * k == R || 2 * k == R || 4 * k == 3 * R) {
+        const float2 t = twiddle_const<R, K, INV>(o);
+        lo = cadd(e, t);
+        hi = csub(e, t);
+    } else {
+        constexpr cx_cs cs = cx_cossin_frac(k, R);
+        constexpr double c = cs.c;
+        constexpr double s = INV ? cs.s : -cs.s;
+        if constexpr (cx_absd(c) >= cx_absd(s)) {
+            constexpr float cf = (float)c;
+            constexpr float tf = (float)(s / c);
+            const float ux = fmaf(-tf, o.y, o.x), uy = fmaf(tf, o.x, o.y);
+            lo = make_float2(fmaf(cf, ux, e.x), fmaf(cf, uy, e.y));
+            hi = make_float2(fmaf(-cf, ux, e.x), fmaf(-cf, uy, e.y));
+        } else {
+            constexpr float sf = (float)s;
+            constexpr float tf = (float)(c / s);
+            const float ux = fmaf(tf, o.x, -o.y), uy = fmaf(tf, o.y, o.x);
+            lo = make_float2(fmaf(sf, ux, e.x), fmaf(sf, uy, e.y));
+            hi = make_float2(fmaf(-sf, ux, e.x), fmaf(-sf, uy, e.y));
+        }
+    }
+}
+
 // ------------------------------------------------------------------ in-register DFT
 // Unnormalised DFT of R = 2^n points held in registers, natural order in and out.
 // Radix-2 decimation in time with compile-time twiddles; radix-4 leaves.
@@ -133,8 +166,7 @@ __device__ __forceinline__ void dft_reg(float2* v);
 template <int R, bool INV, int... K>
 __device__ __forceinline__ void dit_combine(float2* v, const float2* e, const float2* o,
                                             std::integer_sequence<int, K...>) {
-    ((v[K] = cadd(e[K], twiddle_const<R, K, INV>(o[K])),
-      v[K + R / 2] = csub(e[K], twiddle_const<R, K, INV>(o[K]))), ...);
+    (bfly_const<R, K, INV>(e[K], o[K], v[K], v[K + R / 2]), ...);
 }
 
 template <int R, bool INV>
@@ -192,6 +224,8 @@ template <int QT>
 struct AddrInterleaved {
     int ql;
     __device__ __forceinline__ int operator()(int idx) const { return idx * QT + ql; }
+    template <int T>
+    __device__ __forceinline__ int at(int hi, int lo) const { return (hi * T + lo) * QT + ql; }
 };
 // Transform-major with one pad element per T: lanes of a warp on consecutive i.
 template <int L>
@@ -200,6 +234,8 @@ struct AddrPadded {
     static constexpr int T = FftShape<L>::T;
     static constexpr int stride() { return L + L / T; }
     __device__ __forceinline__ int operator()(int idx) const { return base + idx + idx / T; }
+    template <int T_>
+    __device__ __forceinline__ int at(int hi, int lo) const { return base + hi * (T + 1) + lo; }
 };
 
 // Transform-major without padding: the index is XOR-swizzled with its own block number,
@@ -212,6 +248,19 @@ struct AddrSwizzled {
     __device__ __forceinline__ int operator()(int idx) const {
         return base + (idx ^ ((idx / T) & (T - 1)));
     }
+    template <int T_>
+    __device__ __forceinline__ int at(int hi, int lo) const { return base + hi * T + (lo ^ (hi & (T - 1))); }
+};
+
+// QT transforms interleaved, each with one pad element per T (index hi*T + lo sits at
+// hi*(T+1) + lo): the stride-T reads of pass 2 fall on different banks even when only a
+// few transforms share a warp.  (L + L/T) * QT elements.
+template <int QT, int T>
+struct AddrPaddedInterleaved {
+    int ql;
+    __device__ __forceinline__ int operator()(int idx) const { return (idx + idx / T) * QT + ql; }
+    template <int T_>
+    __device__ __forceinline__ int at(int hi, int lo) const { return (hi * (T + 1) + lo) * QT + ql; }
 };
 
 struct SyncBlock {
@@ -219,6 +268,13 @@ struct SyncBlock {
 };
 struct SyncWarp {
     __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+// named barrier `id` over the 128 threads of one group of four warps
+struct SyncGroup128 {
+    int id;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
+    }
 };
 
 // In-place L-point transform of a group of transforms whose threads run in lockstep.
@@ -241,7 +297,7 @@ __device__ __forceinline__ void fft_cyclic(float2 (&v)[FftShape<L>::P], int i, f
                 const float2 w = tw[k1 * T + i];
                 a = INV ? cmul_conj(a, w) : cmul(a, w);
             }
-            xs[addr(k1 * T + i)] = a;
+            xs[addr.template at<T>(k1, i)] = a;
             if ((k1 & 7) == 7) hoist_fence();
         }
         sync();
@@ -250,7 +306,7 @@ __device__ __forceinline__ void fft_cyclic(float2 (&v)[FftShape<L>::P], int i, f
         for (int g = 0; g < G; ++g) {
             float2 w[T];
 #pragma unroll
-            for (int ip = 0; ip < T; ++ip) w[ip] = xs[addr((i + T * g) * T + ip)];
+            for (int ip = 0; ip < T; ++ip) w[ip] = xs[addr.template at<T>(i + T * g, ip)];
             dft_reg<T, INV>(w);
 #pragma unroll
             for (int k2 = 0; k2 < T; ++k2) v[g + G * k2] = w[k2];

@@ -18,10 +18,18 @@
 // The last kd lags (N - m <= kd pairs) are taken directly from Eq. 1 by differences
 // instead: few terms, and no cancellation against the much larger power sums.
 //
-// Corner turn: a CTA owns QT consecutive stored wave vectors; each warp load instruction
-// reads whole 128-byte row segments F[t][q0 .. q0+QT) of the [t][q] spectrum, and the
-// thread mapping (q fastest, then transform thread i) turns them into per-q sequences
-// in registers (thread i of q holds t = i + T u).
+// Two kernels share this arithmetic:
+//  * L >= 512 (the production sizes): 512-thread CTAs split into four independent groups of
+//    128 threads.  A group owns QG = 128/T consecutive stored wave vectors at a time; their
+//    tile ([L frames][QG] complex) arrives by TMA bulk tensor copies, the group's threads
+//    synchronise on a named barrier of their own, so the four groups drift apart and one
+//    group's copy wait hides behind the others' transforms.  The next tile's copy is issued
+//    before the D rows are staged, and the D rows leave shared memory by bulk async copies.
+//    Each tile is copied three times (the odd-bin, even-bin and power-sum passes each need
+//    g and there is no room to keep it): once from DRAM, twice from L2.
+//  * L <= 256: one group per CTA, each thread loads its own samples (every warp load
+//    instruction covers whole 128-byte row segments F[t][q0 .. q0+QT) of the [t][q]
+//    spectrum).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -33,7 +41,7 @@
 namespace ddm {
 namespace {
 
-// ---- TMA (bulk tensor copies) and mbarrier helpers, inline PTX
+// ---- TMA (bulk tensor copies), bulk copies and mbarrier helpers, inline PTX
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -59,14 +67,22 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y),
         "r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"(map), "r"(x),
-                 "r"(y) : "memory");
-}
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// A bounded wait on the tile barrier: about two seconds of polling, then false.
+// shared -> global bulk copy (size and both addresses multiples of 16 bytes)
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(smem_u32(ssrc)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// this thread's bulk copies have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// this thread's bulk copies are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// A bounded wait on a tile barrier: about two seconds of polling, then false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
@@ -74,46 +90,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
     return true;
 }
-
-template <int LOG2L>
-struct TShape {
-    static constexpr int L = 1 << LOG2L;
-    using S = FftShape<L>;
-    static constexpr int P = S::P, T = S::T;
-    static constexpr int NT = (T == 32) ? 512 : 256;      // threads per CTA
-    static constexpr int QT = NT / T;                      // wave vectors per tile
-    static constexpr int KD = (L / 2 < 32) ? L / 2 : 32;  // max directly evaluated lags
-    // D staging row stride: conflict-free writes from the cyclic layout, and 16-byte
-    // aligned rows (float4 stores) when QT == 16
-    static constexpr int DSTRIDE = L + (QT >= 32 ? 1 : (QT == 16 ? 4 : 32 / QT));
-    static constexpr int RED = (P > 2 * T ? P : 2 * T);
-    // tiles of 16 wave vectors and L >= 256 frames arrive by TMA: boxes of 16 complex x 256
-    // frames (32 KB) straight into the exchange buffer, which has the same [t][16] layout
-    static constexpr bool USE_TMA = (QT == 16) && (L >= 256);
-    static constexpr int BOX_T = 256;
-    static constexpr int NBOX = L / BOX_T;
-    static constexpr int FIX_MAX = 8;             // most leading lags the FP64 fixup redoes
-    // shared memory carve-up (bytes)
-    static constexpr size_t OFF_TW = 0;
-    static constexpr size_t OFF_TW2 = OFF_TW + (T > 1 ? L : 0) * sizeof(float2);
-    static constexpr size_t OFF_INV = OFF_TW2 + (size_t)L * sizeof(float2);
-    static constexpr size_t OFF_XS = (OFF_INV + (size_t)L * sizeof(float) + 1023) & ~size_t(1023);
-    static constexpr size_t OFF_AB = OFF_XS + (size_t)L * QT * sizeof(float2);
-    static constexpr size_t OFF_HT = OFF_AB + (size_t)L * QT * sizeof(float);
-    static constexpr size_t OFF_MU = OFF_HT + (size_t)2 * (KD > 0 ? KD : 1) * QT * sizeof(float2);
-    static constexpr size_t OFF_RED = OFF_MU + (size_t)QT * sizeof(float2);
-    static constexpr size_t BYTES = OFF_RED + (size_t)RED * QT * sizeof(float);
-    static_assert(BYTES <= 232448, "temporal kernel shared memory exceeds 227 KB");
-    static_assert((size_t)QT * DSTRIDE <= (size_t)2 * L * QT, "D staging must fit the exchange buffer");
-};
+// true in every thread of the 128-thread group on named barrier `id` if pred holds in any
+__device__ __forceinline__ bool group_any(bool pred, int id) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n"
+        " selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r) : "r"((uint32_t)pred), "r"(id) : "memory");
+    return r != 0;
+}
 
 struct TArgs {
     int N;            // frames
-    int kd;           // directly evaluated trailing lags (<= KD, < N)
+    int kd;           // directly evaluated trailing lags (<= 32, < N)
     int H, Wh, lwh;   // for the storage -> public q map (lwh = log2 Wh)
     int64_t n_q;      // stored wave vectors = spectrum frame stride
-    int64_t n_tiles;
-    int vec4;         // D rows 16-byte aligned (N % 4 == 0 and D aligned): float4 stores
+    int64_t n_tiles;  // tiles (of one group, L >= 512; of one CTA, L <= 256)
+    int vec4;         // D rows 16-byte aligned (N % 4 == 0 and D aligned)
     int fix;          // FP64-fixup tier: lags 1..fix by direct differences (0 = off)
     const float2* tw;
     const float2* tw2;
@@ -128,10 +121,399 @@ __device__ __forceinline__ int public_q(int s, int H, int Wh, int lwh) {
     return (s - main) * (Wh + 1) + Wh;
 }
 
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+
+// =====================================================================================
+// L >= 512: four independent 128-thread groups per CTA, tiles by TMA
+// =====================================================================================
+template <int LOG2L>
+struct GShape {
+    static constexpr int L = 1 << LOG2L;
+    using S = FftShape<L>;
+    static constexpr int P = S::P, T = S::T;
+    static constexpr int NG = 4;              // groups per CTA
+    static constexpr int GT = 128;            // threads per group
+    static constexpr int NT = NG * GT;
+    static constexpr int QG = GT / T;         // wave vectors per group tile
+    static constexpr int IW = 32 / QG;        // threads of one wave vector in a warp
+    static constexpr int NWG = GT / 32;       // warps per group
+    static constexpr int KD = 32;             // most trailing lags taken by differences
+    static constexpr int KT = (KD + T - 1) / T;   // trailing lags per thread
+    static constexpr int G = P / T;           // rows of T frames per thread in the prefix sums
+    static constexpr int DS = L + IW;         // D staging row stride (floats): conflict-free
+    static constexpr int BOX_T = 256, NBOX = L / BOX_T;
+    static constexpr int FIX_MAX = 8;
+    // per-group buffers (bytes)
+    //   xs:  the tile [t][QG] (TMA layout), the padded transform exchange, the padded
+    //        |g|^2 / prefix-sum rows (floats)
+    //   ab:  |X_odd|^2, then Re C ([m][QG] floats), then the D rows [QG][DS]
+    //   red: row totals of the prefix sums; the mean's warp partials
+    //   fix: warp partials of the FP64-fixup lags
+    static constexpr size_t G_XS = (size_t)(L + L / T) * QG * sizeof(float2);
+    static constexpr size_t G_AB = cmax((size_t)L * QG * sizeof(float), (size_t)QG * DS * sizeof(float));
+    static constexpr size_t G_RED = (size_t)P * QG * sizeof(float);
+    static constexpr size_t G_FIX = (size_t)FIX_MAX * NWG * QG * sizeof(float);
+    static constexpr size_t OFF_TW = 0;
+    static constexpr size_t OFF_TW2 = OFF_TW + (size_t)L * sizeof(float2);
+    static constexpr size_t OFF_INV = OFF_TW2 + (size_t)L * sizeof(float2);
+    static constexpr size_t OFF_XS = (OFF_INV + (size_t)L * sizeof(float) + 1023) & ~size_t(1023);
+    static constexpr size_t OFF_AB = OFF_XS + NG * G_XS;
+    static constexpr size_t OFF_RED = OFF_AB + NG * G_AB;
+    static constexpr size_t OFF_FIX = OFF_RED + NG * G_RED;
+    static constexpr size_t BYTES = OFF_FIX + NG * G_FIX;
+    static_assert(L >= 512 && T >= 16 && QG * T == GT, "grouped kernel: L >= 512");
+    static_assert(BYTES + 64 <= 232448, "temporal kernel shared memory exceeds 227 KB");
+    static_assert(G_XS % 1024 == 0, "TMA destinations stay 1024-byte aligned");
+    static_assert((DS % 4) == 0 && (G_AB % 16) == 0, "D rows must be 16-byte aligned for bulk copies");
+    static_assert((size_t)NWG * QG * sizeof(float2) <= G_RED, "mean partials must fit");
+    static_assert((size_t)2 * L * QG * sizeof(float) >= (size_t)(L + L / T) * QG * sizeof(float),
+                  "padded prefix rows must fit the tile buffer");
+};
+
 template <int LOG2L, bool FIXUP>
-__global__ void __launch_bounds__(TShape<LOG2L>::NT, TShape<LOG2L>::NT == 512 ? 1 : 2)
-temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs a,
-                   const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(GShape<LOG2L>::NT, 1)
+temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUtensorMap tmap) {
+    using C = GShape<LOG2L>;
+    constexpr int L = C::L, P = C::P, T = C::T, QG = C::QG, NG = C::NG, GT = C::GT;
+    constexpr int NWG = C::NWG, G = C::G, KT = C::KT, DS = C::DS, FM = C::FIX_MAX;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint64_t tile_bar[NG];
+
+    const int tid = threadIdx.x;
+    const int grp = tid / GT, tg = tid % GT;
+    const int bar_id = 1 + grp;          // named barrier of this group (0 is __syncthreads)
+    float2* tw = reinterpret_cast<float2*>(smem_raw + C::OFF_TW);
+    float2* tw2 = reinterpret_cast<float2*>(smem_raw + C::OFF_TW2);
+    float* inv = reinterpret_cast<float*>(smem_raw + C::OFF_INV);
+    float2* xs = reinterpret_cast<float2*>(smem_raw + C::OFF_XS + grp * C::G_XS);
+    float* xf = reinterpret_cast<float*>(xs);
+    float* ab = reinterpret_cast<float*>(smem_raw + C::OFF_AB + grp * C::G_AB);
+    float* red = reinterpret_cast<float*>(smem_raw + C::OFF_RED + grp * C::G_RED);
+    float2* red2 = reinterpret_cast<float2*>(red);
+    float* fixw = reinterpret_cast<float*>(smem_raw + C::OFF_FIX + grp * C::G_FIX);
+    uint64_t* bar = &tile_bar[grp];
+
+    if (tg == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int k = tid; k < L; k += C::NT) {
+        tw[k] = a.tw[k];
+        tw2[k] = a.tw2[k];
+        inv[k] = a.inv[k];
+    }
+    __syncthreads();   // the only CTA-wide barrier: from here on the groups run on their own
+
+    const int ql = tg % QG;
+    const int i = tg / QG;
+    const int lane = tid & 31, wg = tg >> 5;
+    const SyncGroup128 sync{bar_id};
+    const AddrPaddedInterleaved<QG, T> xaddr{ql};
+    const int N = a.N;
+    const int kd = a.kd;
+    const int64_t nq = a.n_q;
+    const int64_t gstride = (int64_t)gridDim.x * NG;
+    bool timed_out = false;
+    float chk = 0.f;                      // becomes NaN if any D value is not finite
+    uint32_t phase = 0;
+
+    // Copy group tile `t` ([t][QG] complex, zeros beyond N and n_q) into xs.
+    // Precondition: every thread of the group is done with xs (a group barrier was passed).
+    auto issue = [&](int64_t t) {
+        if (tg == 0) {
+            fence_proxy_async();
+            mbar_expect_tx(bar, (uint32_t)(C::NBOX * C::BOX_T * QG * sizeof(float2)));
+#pragma unroll
+            for (int b = 0; b < C::NBOX; ++b)
+                tma_load_2d(xs + b * C::BOX_T * QG, &tmap, (int)(2 * t * QG), b * C::BOX_T, bar);
+        }
+    };
+    // Wait for the copy in flight; the decision to give up is the same in the whole group.
+    auto wait = [&]() -> bool {
+        const bool ok = mbar_wait_bounded(bar, phase);
+        if (group_any(!ok, bar_id)) return false;
+        phase ^= 1u;
+        return true;
+    };
+
+    // trailing lags of this thread: m = m0 + k T in [N - kd, N)
+    const int m_lo = N - kd;
+    const int m0 = m_lo + ((i - m_lo) % T + T) % T;
+    // S(m - 1) and S(N - 1 - m) for m = i + T u sit at these padded positions + / - u (T + 1)
+    const int base1 = i >= 1 ? i - 1 : -2;
+    const int base2 = (N - 1 - i) + (N - 1 - i) / T;
+
+    int64_t gt = (int64_t)blockIdx.x * NG + grp;
+    if (gt < a.n_tiles) issue(gt);
+    for (; gt < a.n_tiles; gt += gstride) {
+        // (no L2 prefetch of later tiles: with four groups per SM their copies already
+        // overlap the other groups' work, and prefetched lines measurably crowd the
+        // current tiles' reloads out of L2 at 512x512x1024: 1.45 ms with, 1.15 ms without)
+        if (!wait()) { timed_out = true; break; }
+
+        // ---- the time sequence in the cyclic layout, and its mean
+        float2 v[P];
+        float2 part = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            v[u] = xs[(i + T * u) * QG + ql];
+            part = cadd(part, v[u]);
+        }
+#pragma unroll
+        for (int o = QG; o < 32; o <<= 1) {
+            part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
+            part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
+        }
+        if (lane < QG) red2[wg * QG + ql] = part;
+        sync();
+        float2 mean = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < NWG; ++w) mean = cadd(mean, red2[w * QG + ql]);
+        {
+            const float rn = 1.0f / (float)N;
+            mean = make_float2(mean.x * rn, mean.y * rn);
+        }
+#pragma unroll
+        for (int u = 0; u < P; ++u)
+            if (i + T * u < N) v[u] = csub(v[u], mean);
+        // the previous tile's D copies must have left ab before it is written again
+        if (tg < QG) bulk_wait_read_all();
+
+        // ---- odd bins: L-point DFT of g(t) e^{-i pi t / L}; |.|^2 parked in ab
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            v[u] = cmul(v[u], tw2[i + T * u]);
+            if ((u & 7) == 7) hoist_fence();
+        }
+        fft_cyclic<L, false>(v, i, xs, xaddr, tw, sync);
+#pragma unroll
+        for (int u = 0; u < P; ++u) ab[(i + T * u) * QG + ql] = cabs2(v[u]);
+
+        // ---- even bins: L-point DFT of g (the tile again, from L2)
+        issue(gt);
+        if (!wait()) { timed_out = true; break; }
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int t = i + T * u;
+            v[u] = (t < N) ? csub(xs[t * QG + ql], mean) : make_float2(0.f, 0.f);
+        }
+        sync();   // tile read: the exchange overwrites it
+        fft_cyclic<L, false>(v, i, xs, xaddr, tw, sync);
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            v[u] = make_float2(cabs2(v[u]), ab[(i + T * u) * QG + ql]);
+            if ((u & 7) == 7) hoist_fence();
+        }
+
+        // ---- inverse transform of Z = |X_even|^2 + i |X_odd|^2, then Re C(m) into ab
+        fft_cyclic<L, true>(v, i, xs, xaddr, tw, sync);
+#pragma unroll
+        for (int u = 0; u < P; ++u) xs[(i + T * u) * QG + ql] = v[u];
+        sync();
+        {
+            const float scale = 0.25f / (float)L;
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+                const int m = i + T * u;
+                const float2 z = v[u];
+                const float2 zr = xs[((L - m) & (L - 1)) * QG + ql];
+                const float2 w = tw2[m];                   // (cos(pi m/L), -sin(pi m/L))
+                ab[m * QG + ql] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
+                if ((u & 7) == 7) hoist_fence();
+            }
+        }
+        sync();   // partner reads done: xs is free
+
+        // ---- the tile a third time: |g - mean|^2, the trailing lags by differences (Eq. 1)
+        // and, in the FP64-fixup tier, the leading lags by differences
+        issue(gt);
+        if (!wait()) { timed_out = true; break; }
+        float e[P];
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int t = i + T * u;
+            e[u] = (t < N) ? cabs2(csub(xs[t * QG + ql], mean)) : 0.f;
+        }
+        float tl[KT];
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const int m = m0 + k * T;
+            float acc = 0.f;
+            if (m < N) {
+                for (int t = 0; t < N - m; ++t)
+                    acc += cabs2(csub(xs[(t + m) * QG + ql], xs[t * QG + ql]));
+                acc *= inv[m];
+                chk = fmaf(acc, 0.f, chk);
+            }
+            tl[k] = acc;
+        }
+        if constexpr (FIXUP) {
+            const int fix = a.fix;
+            float fp[FM];
+#pragma unroll
+            for (int k = 0; k < FM; ++k) fp[k] = 0.f;
+#pragma unroll 4
+            for (int u = 0; u < P; ++u) {
+                const int t = i + T * u;
+                if (t < N) {
+                    const float2 g0 = xs[t * QG + ql];
+#pragma unroll
+                    for (int k = 0; k < FM; ++k)
+                        if (k < fix && t + k + 1 < N) fp[k] += cabs2(csub(xs[(t + k + 1) * QG + ql], g0));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < FM; ++k) {
+#pragma unroll
+                for (int o = QG; o < 32; o <<= 1) fp[k] += __shfl_xor_sync(0xffffffffu, fp[k], o);
+                if (lane < QG) fixw[(k * NWG + wg) * QG + ql] = fp[k];
+            }
+        }
+        sync();   // tile fully read
+
+        // |g - mean|^2 into padded rows (frame t at t + t / T): both the cyclic writes here
+        // and the row-wise reads below are conflict-free
+#pragma unroll
+        for (int u = 0; u < P; ++u) xf[(i + u * (T + 1)) * QG + ql] = e[u];
+        sync();
+        // ---- inclusive prefix sums S(t): thread i owns the rows r = i + T g of T frames
+        float rowv[G][T];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int r = i + T * g;
+            float acc = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < T; ++jj) {
+                acc += xf[(r * (T + 1) + jj) * QG + ql];
+                rowv[g][jj] = acc;
+            }
+            red[r * QG + ql] = acc;
+        }
+        sync();
+        float total = 0.f;
+        float off[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) off[g] = 0.f;
+#pragma unroll
+        for (int rp = 0; rp < P; ++rp) {
+            const float x = red[rp * QG + ql];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (rp < i + T * g) off[g] += x;
+            total += x;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int r = i + T * g;
+#pragma unroll
+            for (int jj = 0; jj < T; ++jj) xf[(r * (T + 1) + jj) * QG + ql] = rowv[g][jj] + off[g];
+        }
+        sync();
+        // FP64-fixup tier: lag m = i (1 <= i <= fix) summed over the group's warps in FP64
+        float fixd = 0.f;
+        const bool has_fix = FIXUP && a.fix > 0 && i >= 1 && i <= a.fix && i < N - kd;
+        if (has_fix) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < NWG; ++w) s += (double)fixw[((i - 1) * NWG + w) * QG + ql];
+            fixd = (float)(s / (double)(N - i));
+            chk = fmaf(fixd, 0.f, chk);
+        }
+
+        // ---- D(m) = (P1 + P2 - 2 Re C) / (N - m) for 0 < m < N - kd
+        float dv[P];
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int m = i + T * u;
+            float d = 0.f;
+            if (m > 0 && m < N - kd) {
+                const float p1 = xf[(base2 - u * (T + 1)) * QG + ql];
+                const float p2 = total - xf[(base1 + u * (T + 1)) * QG + ql];
+                d = (p1 + p2 - 2.f * ab[m * QG + ql]) * inv[m];
+                chk = fmaf(d, 0.f, chk);
+            }
+            dv[u] = d;
+            if ((u & 7) == 7) hoist_fence();
+        }
+        sync();   // reads of S and Re C done: xs and ab are free
+
+        // ---- the next tile's copy overlaps the staging and the stores of this one
+        if (gt + gstride < a.n_tiles) issue(gt + gstride);
+
+        // ---- D rows [q][m] staged in ab, then copied out
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int m = i + T * u;
+            if (m < N) ab[ql * DS + m] = dv[u];
+        }
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const int m = m0 + k * T;
+            if (m < N) ab[ql * DS + m] = tl[k];
+        }
+        if (has_fix) ab[ql * DS + i] = fixd;
+        if (a.vec4) fence_proxy_async();   // generic writes -> the bulk copies' reads
+        sync();
+        if (a.vec4) {
+            if (tg < QG) {
+                const int64_t sr = gt * QG + tg;
+                if (sr < nq) {
+                    float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
+                    bulk_store(drow, ab + tg * DS, (uint32_t)N * (uint32_t)sizeof(float));
+                }
+                bulk_commit();
+            }
+        } else {
+#pragma unroll 1
+            for (int r = 0; r < QG; ++r) {
+                const int64_t sr = gt * QG + r;
+                if (sr >= nq) break;
+                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
+                for (int m = tg; m < N; m += GT) drow[m] = ab[r * DS + m];
+            }
+        }
+    }
+    if (timed_out) {
+        // a tile copy never completed: report it; give the outstanding copy a last bounded
+        // chance to land before the CTA's shared memory goes away
+        atomicOr(a.status, 2u);
+        mbar_wait_bounded(bar, phase);
+    }
+    if (tg < QG) bulk_wait_all();
+    if (chk != chk) atomicOr(a.status, 1u);
+}
+
+// =====================================================================================
+// L <= 256: one group per CTA, per-thread loads
+// =====================================================================================
+template <int LOG2L>
+struct TShape {
+    static constexpr int L = 1 << LOG2L;
+    using S = FftShape<L>;
+    static constexpr int P = S::P, T = S::T;
+    static constexpr int NT = 256;                         // threads per CTA
+    static constexpr int QT = NT / T;                      // wave vectors per tile (>= 32)
+    static constexpr int KD = (L / 2 < 32) ? L / 2 : 32;  // max directly evaluated lags
+    static constexpr int DSTRIDE = L + 1;                  // D staging row stride
+    static constexpr int RED = (P > 2 * T ? P : 2 * T);
+    static constexpr size_t OFF_TW = 0;
+    static constexpr size_t OFF_TW2 = OFF_TW + (T > 1 ? L : 0) * sizeof(float2);
+    static constexpr size_t OFF_INV = OFF_TW2 + (size_t)L * sizeof(float2);
+    static constexpr size_t OFF_XS = (OFF_INV + (size_t)L * sizeof(float) + 1023) & ~size_t(1023);
+    static constexpr size_t OFF_AB = OFF_XS + (size_t)L * QT * sizeof(float2);
+    static constexpr size_t OFF_HT = OFF_AB + (size_t)L * QT * sizeof(float);
+    static constexpr size_t OFF_MU = OFF_HT + (size_t)2 * (KD > 0 ? KD : 1) * QT * sizeof(float2);
+    static constexpr size_t OFF_RED = OFF_MU + (size_t)QT * sizeof(float2);
+    static constexpr size_t BYTES = OFF_RED + (size_t)RED * QT * sizeof(float);
+    static_assert(L <= 256 && QT >= 32, "per-thread-load kernel: L <= 256");
+    static_assert(BYTES <= 232448, "temporal kernel shared memory exceeds 227 KB");
+    static_assert((size_t)QT * DSTRIDE <= (size_t)2 * L * QT, "D staging must fit the exchange buffer");
+};
+
+// (shared memory allows one CTA per SM at every L: the register file is all this CTA's)
+template <int LOG2L>
+__global__ void __launch_bounds__(TShape<LOG2L>::NT, 1)
+temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs a) {
     using C = TShape<LOG2L>;
     constexpr int L = C::L, P = C::P, T = C::T, NT = C::NT, QT = C::QT, KD = C::KD;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -148,14 +530,6 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
     float2* red2 = reinterpret_cast<float2*>(smem_raw + C::OFF_RED);
 
     const int tid = threadIdx.x;
-    __shared__ uint64_t tile_bar;
-    uint32_t bar_phase = 0;
-    if constexpr (C::USE_TMA) {
-        if (tid == 0) {
-            mbar_init(&tile_bar, 1);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-    }
     if constexpr (T > 1) {
         for (int k = tid; k < L; k += NT) tw[k] = a.tw[k];
     }
@@ -173,22 +547,6 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
     const uint32_t nq32 = (uint32_t)nq;   // N * n_q < 2^32 (checked at plan creation)
     const AddrInterleaved<QT> addr{ql};
     bool bad = false;
-    bool timed_out = false;
-    // Copy tile `tl` into xs ([t][16] complex, zeros beyond N and n_q) and wait for it.
-    // Precondition: every thread is done with xs (a barrier was just passed).
-    auto load_tile = [&](int64_t tl) -> bool {
-        if (tid == 0) {
-            fence_proxy_async();
-            mbar_expect_tx(&tile_bar, (uint32_t)(C::NBOX * C::BOX_T * QT * sizeof(float2)));
-#pragma unroll
-            for (int b = 0; b < C::NBOX; ++b)
-                tma_load_2d(xs + b * C::BOX_T * QT, &tmap, (int)(2 * tl * QT), b * C::BOX_T, &tile_bar);
-        }
-        const bool ok = mbar_wait_bounded(&tile_bar, bar_phase);
-        bar_phase ^= 1u;
-        // the decision to give up must be the same in every thread (barriers follow)
-        return __syncthreads_or(ok ? 0 : 1) == 0;
-    };
 
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         const int64_t s = tile * QT + ql;
@@ -196,11 +554,7 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         const float2* src = spec + (valid ? s : 0);
 
         // ---- prefetch the next tile of this CTA into L2: its DRAM fetch overlaps this tile
-        if constexpr (C::USE_TMA) {
-            const int64_t tn = tile + gridDim.x;
-            if (tid < C::NBOX && tn < a.n_tiles)
-                tma_prefetch_2d(&tmap, (int)(2 * tn * QT), tid * C::BOX_T);
-        } else {
+        {
             const int64_t sn = (tile + gridDim.x) * QT + ql;
             if (sn < nq) {
                 const float2* pn = spec + sn;
@@ -215,20 +569,11 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         // ---- load the time sequence (cyclic layout) and remove its mean
         float2 v[P];
         float2 part = make_float2(0.f, 0.f);
-        if constexpr (C::USE_TMA) {
-            if (!load_tile(tile)) { timed_out = true; break; }
 #pragma unroll
-            for (int u = 0; u < P; ++u) {
-                v[u] = xs[(i + T * u) * QT + ql];
-                part = cadd(part, v[u]);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < P; ++u) {
-                const int t = i + T * u;
-                v[u] = (valid && t < N) ? __ldg(src + (uint32_t)t * nq32) : make_float2(0.f, 0.f);
-                part = cadd(part, v[u]);
-            }
+        for (int u = 0; u < P; ++u) {
+            const int t = i + T * u;
+            v[u] = (valid && t < N) ? __ldg(src + (uint32_t)t * nq32) : make_float2(0.f, 0.f);
+            part = cadd(part, v[u]);
         }
         red2[i * QT + ql] = part;
         __syncthreads();
@@ -260,15 +605,7 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         for (int u = 0; u < P; ++u) ab[(i + T * u) * QT + ql] = cabs2(v[u]);
 
         // ---- even bins: L-point DFT of g (reloaded; the tile is still in L2)
-        if constexpr (C::USE_TMA) {
-            if (!load_tile(tile)) { timed_out = true; break; }
-#pragma unroll
-            for (int u = 0; u < P; ++u) {
-                const int t = i + T * u;
-                v[u] = (t < N) ? csub(xs[t * QT + ql], mean) : make_float2(0.f, 0.f);
-            }
-            __syncthreads();   // tile read: the exchange buffer is reused by the transform
-        } else {
+        {
             const float2* src2 = opaque_ptr(src);
 #pragma unroll
             for (int u = 0; u < P; ++u) {
@@ -301,71 +638,24 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
         __syncthreads();   // partner reads done: the exchange buffer is free
 
         // ---- power terms: inclusive prefix sums S(t) of |g|^2.  Thread i owns the rows
-        // r = i + T g of T consecutive t (reloaded from L2; each load instruction still
-        // covers whole 128-byte segments), sums them in registers, and adds the offset of
-        // the rows before it.
+        // r = i + T g of T consecutive t (reloaded from L2), sums them in registers, and
+        // adds the offset of the rows before it.
         const float2* src3 = opaque_ptr(src);
         constexpr int G = P / T;
         float rowv[G][T];
-        if constexpr (C::USE_TMA) {
-            if (!load_tile(tile)) { timed_out = true; break; }
-        }
-        // FP64-fixup tier (tile in shared memory): over its rows each thread also sums
-        // |F(t+m) - F(t)|^2 for m = 1..fix, the direct, cancellation-free form of Eq. 1,
-        // keeping F(t .. t+FIX_MAX) in a sliding register window
-        constexpr int FM = C::FIX_MAX;
-        const int fix = (FIXUP && C::USE_TMA) ? a.fix : 0;
-        float fixp[FM];
-#pragma unroll
-        for (int k = 0; k < FM; ++k) fixp[k] = 0.f;
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int r = i + T * g;
             float acc = 0.f;
-            float2 win[FM + 1];
-            if constexpr (FIXUP && C::USE_TMA) {
-                if (fix > 0) {
-#pragma unroll
-                    for (int k = 0; k < FM; ++k) {
-                        const int tk = r * T + k;
-                        win[k] = tk < N ? xs[tk * QT + ql] : make_float2(0.f, 0.f);
-                    }
-                }
-            }
 #pragma unroll
             for (int jj = 0; jj < T; ++jj) {
                 const int t = r * T + jj;
-                float e = 0.f;
-                if constexpr (FIXUP && C::USE_TMA) {
-                    if (fix > 0) {
-                        win[FM] = (t + FM < N) ? xs[(t + FM) * QT + ql] : make_float2(0.f, 0.f);
-#pragma unroll
-                        for (int m = 1; m <= FM; ++m)
-                            if (m <= fix && t + m < N) fixp[m - 1] += cabs2(csub(win[m], win[0]));
-                        if (t < N) e = cabs2(csub(win[0], mean));
-#pragma unroll
-                        for (int k = 0; k < FM; ++k) win[k] = win[k + 1];
-                    } else {
-                        if (t < N) e = cabs2(csub(xs[t * QT + ql], mean));
-                    }
-                } else if constexpr (C::USE_TMA) {
-                    if (t < N) e = cabs2(csub(xs[t * QT + ql], mean));
-                } else {
-                    if (valid && t < N) e = cabs2(csub(__ldg(src3 + (uint32_t)t * nq32), mean));
-                }
-                acc += e;
+                if (valid && t < N) acc += cabs2(csub(__ldg(src3 + (uint32_t)t * nq32), mean));
                 rowv[g][jj] = acc;
             }
             red[r * QT + ql] = acc;
         }
         __syncthreads();
-        // the tile has been read: the upper half of the exchange buffer takes the fixup partials
-        float* fixpart = xf + (size_t)L * QT;                  // [m][i][ql]
-        if (FIXUP && fix > 0) {
-#pragma unroll
-            for (int k = 0; k < FM; ++k)
-                if (k < fix) fixpart[(k * T + i) * QT + ql] = fixp[k];
-        }
         float total = 0.f;
         float off[G];
 #pragma unroll
@@ -383,14 +673,6 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
             const int r = i + T * g;
 #pragma unroll
             for (int jj = 0; jj < T; ++jj) xf[(r * T + jj) * QT + ql] = rowv[g][jj] + off[g];
-        }
-        __syncthreads();
-        // partials of lag m = i + 1 summed in FP64 over the T threads of each sequence;
-        // D(m) parked in the row-total buffer (free now) until the D rows are staged
-        if (FIXUP && fix > 0 && i < fix && i + 1 < N) {
-            double sum = 0.0;
-            for (int ip = 0; ip < T; ++ip) sum += (double)fixpart[(i * T + ip) * QT + ql];
-            red[i * QT + ql] = (float)(sum / (double)(N - 1 - i));
         }
         __syncthreads();
 
@@ -429,39 +711,18 @@ temporal_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs
                 xf[ql * DS + m] = acc * inv[m];
             }
         }
-        if (FIXUP && fix > 0 && i < fix && i + 1 < N - kd) xf[ql * DS + i + 1] = red[i * QT + ql];
         __syncthreads();
-        if (QT == 16 && a.vec4) {
-            const int n4 = N >> 2;
-            const int total4 = QT * n4;
-            for (int f = tid; f < total4; f += NT) {
-                const int r = f / n4, j = f - r * n4;
-                const int64_t sr = tile * QT + r;
-                if (sr >= nq) break;
-                const float4 d = *reinterpret_cast<const float4*>(xf + r * DS + 4 * j);
-                bad |= !(isfinite(d.x) && isfinite(d.y) && isfinite(d.z) && isfinite(d.w));
-                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
-                reinterpret_cast<float4*>(drow)[j] = d;
-            }
-        } else {
-            for (int r = 0; r < QT; ++r) {
-                const int64_t sr = tile * QT + r;
-                if (sr >= nq) break;
-                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
-                for (int m = tid; m < N; m += NT) {
-                    const float d = xf[r * DS + m];
-                    bad |= !isfinite(d);
-                    drow[m] = d;
-                }
+        for (int r = 0; r < QT; ++r) {
+            const int64_t sr = tile * QT + r;
+            if (sr >= nq) break;
+            float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
+            for (int m = tid; m < N; m += NT) {
+                const float d = xf[r * DS + m];
+                bad |= !isfinite(d);
+                drow[m] = d;
             }
         }
         __syncthreads();
-    }
-    if (timed_out) {
-        // a tile copy never completed: report it; give an outstanding copy a last bounded
-        // chance to land before the CTA's shared memory goes away
-        atomicOr(a.status, 2u);
-        mbar_wait_bounded(&tile_bar, bar_phase);
     }
     if (bad) atomicOr(a.status, 1u);
 }
@@ -485,30 +746,21 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// 2D view of the spectrum as float32 [N][2 n_q]; boxes of 32 floats (16 complex) x 256 rows;
-// rows >= N and columns >= 2 n_q read as zero.
-bool make_spectrum_map(CUtensorMap* map, const float2* spec, int64_t n_q, int N) {
+// 2D view of the spectrum as float32 [N][2 n_q]; boxes of 2 qg floats (qg complex) x 256
+// rows; rows >= N and columns >= 2 n_q read as zero.
+bool make_spectrum_map(CUtensorMap* map, const float2* spec, int64_t n_q, int N, int qg) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)(2 * n_q), (cuuint64_t)N};
     const cuuint64_t strides[1] = {(cuuint64_t)(2 * n_q * sizeof(float))};
-    const cuuint32_t box[2] = {32, 256};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * qg), 256};
     const cuuint32_t estr[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(spec), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int LOG2L, bool FIXUP>
-ddm_status launch_t(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
-    using C = TShape<LOG2L>;
-    CUtensorMap tmap;
-    memset(&tmap, 0, sizeof(tmap));
-    if constexpr (C::USE_TMA) {
-        if ((reinterpret_cast<uintptr_t>(spec) & 15) != 0) return DDM_ERR_INVALID_ARG;
-        if (!make_spectrum_map(&tmap, spec, p->n_q, p->d.N)) return DDM_ERR_CUDA;
-    }
-    TArgs a;
+void fill_args(TArgs& a, const ddm_plan_s* p, float* D, int qt) {
     a.N = p->d.N;
     a.kd = p->kd;
     a.H = p->d.H;
@@ -517,17 +769,43 @@ ddm_status launch_t(const ddm_plan_s* p, const float2* spec, float* D, cudaStrea
     a.vec4 = (p->d.N % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
     a.fix = (p->d.precision == DDM_PREC_FP32_FP64FIX) ? p->fix_lags : 0;
     a.n_q = p->n_q;
-    a.n_tiles = (p->n_q + C::QT - 1) / C::QT;
+    a.n_tiles = (p->n_q + qt - 1) / qt;
     a.tw = p->tw_t;
     a.tw2 = p->tw2;
     a.inv = p->inv;
     a.status = p->dev_status;
+}
+
+template <int LOG2L, bool FIXUP>
+ddm_status launch_grouped(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
+    using C = GShape<LOG2L>;
+    if ((reinterpret_cast<uintptr_t>(spec) & 15) != 0) return DDM_ERR_INVALID_ARG;
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    if (!make_spectrum_map(&tmap, spec, p->n_q, p->d.N, C::QG)) return DDM_ERR_CUDA;
+    TArgs a;
+    fill_args(a, p, D, C::QG);
     auto k = temporal_sf_kernel<LOG2L, FIXUP>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
         cudaSuccess)
         return DDM_ERR_CUDA;
+    const int64_t ctas = (a.n_tiles + C::NG - 1) / C::NG;
+    const int64_t grid = ctas < p->n_sm ? ctas : p->n_sm;
+    k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(D, a, tmap);
+    return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
+}
+
+template <int LOG2L>
+ddm_status launch_small(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
+    using C = TShape<LOG2L>;
+    TArgs a;
+    fill_args(a, p, D, C::QT);
+    auto k = temporal_sf_small_kernel<LOG2L>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
+        cudaSuccess)
+        return DDM_ERR_CUDA;
     const int64_t grid = a.n_tiles < p->n_sm ? a.n_tiles : p->n_sm;
-    k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(spec, D, a, tmap);
+    k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(spec, D, a);
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 
@@ -536,17 +814,17 @@ ddm_status launch_t(const ddm_plan_s* p, const float2* spec, float* D, cudaStrea
 ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
     const bool fix = p->d.precision == DDM_PREC_FP32_FP64FIX;
     switch (ilog2(p->L)) {
-        case 0: return launch_t<0, false>(p, spec, D, s);
-        case 1: return launch_t<1, false>(p, spec, D, s);
-        case 2: return launch_t<2, false>(p, spec, D, s);
-        case 3: return launch_t<3, false>(p, spec, D, s);
-        case 4: return launch_t<4, false>(p, spec, D, s);
-        case 5: return launch_t<5, false>(p, spec, D, s);
-        case 6: return launch_t<6, false>(p, spec, D, s);
-        case 7: return launch_t<7, false>(p, spec, D, s);
-        case 8: return launch_t<8, false>(p, spec, D, s);
-        case 9: return fix ? launch_t<9, true>(p, spec, D, s) : launch_t<9, false>(p, spec, D, s);
-        case 10: return fix ? launch_t<10, true>(p, spec, D, s) : launch_t<10, false>(p, spec, D, s);
+        case 0: return launch_small<0>(p, spec, D, s);
+        case 1: return launch_small<1>(p, spec, D, s);
+        case 2: return launch_small<2>(p, spec, D, s);
+        case 3: return launch_small<3>(p, spec, D, s);
+        case 4: return launch_small<4>(p, spec, D, s);
+        case 5: return launch_small<5>(p, spec, D, s);
+        case 6: return launch_small<6>(p, spec, D, s);
+        case 7: return launch_small<7>(p, spec, D, s);
+        case 8: return launch_small<8>(p, spec, D, s);
+        case 9: return fix ? launch_grouped<9, true>(p, spec, D, s) : launch_grouped<9, false>(p, spec, D, s);
+        case 10: return fix ? launch_grouped<10, true>(p, spec, D, s) : launch_grouped<10, false>(p, spec, D, s);
         default: return DDM_ERR_UNSUPPORTED;
     }
 }
