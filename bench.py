@@ -253,6 +253,7 @@ def compare_fits(ddm, plan, Dr, stream):
         torch.cuda.synchronize()
         f = flg.cpu().numpy()
         out[name] = {"ms": e0.elapsed_time(e1) / 20, "iters_mean": float(its.cpu().numpy().mean()),
+                     "iters_max": int(its.cpu().numpy().max()),
                      "converged": float(np.mean((f & B_.DDM_FIT_CONVERGED) > 0)),
                      "mlp_accepted": float(np.mean((f & B_.DDM_FIT_MLP_ACCEPTED) > 0)),
                      "cost_sum": float(cst.cpu().numpy().astype(np.float64).sum())}

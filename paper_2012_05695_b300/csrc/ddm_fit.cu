@@ -1,6 +1,7 @@
 // Fit of the radial structure functions (not in the paper): sample every curve at 64
 // log-spaced lags, seed (heuristic or MLP), and Levenberg-Marquardt of
-// D(lag) = A (1 - exp(-(lag / tau)^beta)) + B.  One warp per curve, two lags per lane.
+// D(lag) = A (1 - exp(-(lag / tau)^beta)) + B.  Two lags per lane; the features take one
+// warp per curve, the fit one block of four warps per curve (one damping value per warp).
 //
 // Every warp reduction ends with a broadcast of lane 0's value, so all lanes hold
 // bitwise-identical sums and take identical accept / reject decisions.
@@ -82,6 +83,8 @@ __device__ __forceinline__ float cost_at(const Curve& cv, const float p[4]) {
 // Solve (H + mu diag H) dp = -g by Cholesky of the Jacobi-scaled matrix
 // S (H + mu diag H) S with S = diag(H)^(-1/2) (unit diagonal 1 + mu: better conditioned in
 // FP32 when columns of J are nearly collinear); false if not positive definite / finite.
+// The factor's pivots are kept as reciprocal square roots, so the dependent chain holds
+// multiplications instead of divisions.
 __device__ __forceinline__ bool solve4(const float H[10], const float g[4], float mu, float dp[4]) {
     // H packed: 00 10 11 20 21 22 30 31 32 33
     if (!(H[0] > 0.f && H[2] > 0.f && H[5] > 0.f && H[9] > 0.f)) return false;
@@ -90,27 +93,27 @@ __device__ __forceinline__ bool solve4(const float H[10], const float g[4], floa
     const float a10 = H[1] * s1 * s0, a20 = H[3] * s2 * s0, a21 = H[4] * s2 * s1;
     const float a30 = H[6] * s3 * s0, a31 = H[7] * s3 * s1, a32 = H[8] * s3 * s2;
     const float b0 = -g[0] * s0, b1 = -g[1] * s1, b2 = -g[2] * s2, b3 = -g[3] * s3;
-    const float l00 = sqrtf(dg);
-    const float l10 = a10 / l00, l20 = a20 / l00, l30 = a30 / l00;
+    const float i00 = rsqrtf(dg);                      // 1 / l00
+    const float l10 = a10 * i00, l20 = a20 * i00, l30 = a30 * i00;
     const float d1 = dg - l10 * l10;
     if (!(d1 > 0.f)) return false;
-    const float l11 = sqrtf(d1);
-    const float l21 = (a21 - l20 * l10) / l11, l31 = (a31 - l30 * l10) / l11;
+    const float i11 = rsqrtf(d1);
+    const float l21 = (a21 - l20 * l10) * i11, l31 = (a31 - l30 * l10) * i11;
     const float d2 = dg - l20 * l20 - l21 * l21;
     if (!(d2 > 0.f)) return false;
-    const float l22 = sqrtf(d2);
-    const float l32 = (a32 - l30 * l20 - l31 * l21) / l22;
+    const float i22 = rsqrtf(d2);
+    const float l32 = (a32 - l30 * l20 - l31 * l21) * i22;
     const float d3 = dg - l30 * l30 - l31 * l31 - l32 * l32;
     if (!(d3 > 0.f)) return false;
-    const float l33 = sqrtf(d3);
-    const float z0 = b0 / l00;
-    const float z1 = (b1 - l10 * z0) / l11;
-    const float z2 = (b2 - l20 * z0 - l21 * z1) / l22;
-    const float z3 = (b3 - l30 * z0 - l31 * z1 - l32 * z2) / l33;
-    const float e3 = z3 / l33;
-    const float e2 = (z2 - l32 * e3) / l22;
-    const float e1 = (z1 - l21 * e2 - l31 * e3) / l11;
-    const float e0 = (z0 - l10 * e1 - l20 * e2 - l30 * e3) / l00;
+    const float i33 = rsqrtf(d3);
+    const float z0 = b0 * i00;
+    const float z1 = (b1 - l10 * z0) * i11;
+    const float z2 = (b2 - l20 * z0 - l21 * z1) * i22;
+    const float z3 = (b3 - l30 * z0 - l31 * z1 - l32 * z2) * i33;
+    const float e3 = z3 * i33;
+    const float e2 = (z2 - l32 * e3) * i22;
+    const float e1 = (z1 - l21 * e2 - l31 * e3) * i11;
+    const float e0 = (z0 - l10 * e1 - l20 * e2 - l30 * e3) * i00;
     dp[0] = e0 * s0;
     dp[1] = e1 * s1;
     dp[2] = e2 * s2;
@@ -118,9 +121,47 @@ __device__ __forceinline__ bool solve4(const float H[10], const float g[4], floa
     return isfinite(dp[0]) && isfinite(dp[1]) && isfinite(dp[2]) && isfinite(dp[3]);
 }
 
-// LM from p (in/out); returns iterations, sets cost and flags
-__device__ int lm(const Curve& cv, float p[4], float& cost, int& flags) {
-    cost = cost_at(cv, p);
+// One damped trial at mu: pn = p + dp(mu) (beta clamped) with its residuals, Jacobian and
+// cost; true if it lowers the cost.
+struct Trial {
+    float p[4], r[2], J[2][4], cost;
+};
+
+__device__ __forceinline__ bool lm_trial(const Curve& cv, const float p[4], const float H[10],
+                                         const float g[4], float mu, float cost, Trial& t) {
+    float dp[4];
+    if (!solve4(H, g, mu, dp)) return false;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) t.p[a] = p[a] + dp[a];
+    t.p[3] = fminf(fmaxf(t.p[3], 0.05f), 3.f);
+    model_rows(cv, t.p, t.r, t.J);
+    t.cost = warp_sum_bcast(t.r[0] * t.r[0] + t.r[1] * t.r[1]);
+    return isfinite(t.cost) && t.cost < cost;
+}
+
+constexpr int kTrials = 4;   // damping values tried side by side: one per warp of a curve's block
+
+// what a warp's trial leaves for the other warps of the block
+struct TrialShare {
+    float p[kTrials][4];
+    float cost[kTrials];
+    int ok[kTrials];
+    float rj[kTrials][32][10];   // per lane: r[2], J[2][4]
+};
+
+// LM from p (in/out); returns iterations, sets cost and flags.  Marquardt's rule: after a
+// rejected step mu grows tenfold and the step is solved again, until a step lowers the
+// cost or mu exceeds 1e12.  The kTrials warps of the block hold the same curve and compute
+// the same normal equations; each round warp w tries the w-th of the consecutive values
+// mu, 10 mu, ... and the first that lowers the cost is taken by all: the same trial the
+// one-at-a-time loop accepts, with the same arithmetic, in fewer dependent rounds (the
+// last iteration of a converged fit rejects every value up to 1e12).  The accepted
+// trial's residuals and Jacobian serve the next iteration.  Block-uniform control flow.
+__device__ int lm(const Curve& cv, float p[4], float& cost, int& flags, TrialShare& sh) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float r[2], J[2][4];
+    model_rows(cv, p, r, J);
+    cost = warp_sum_bcast(r[0] * r[0] + r[1] * r[1]);
     if (!isfinite(cost)) {
         flags = DDM_FIT_NONFINITE;
         return 0;
@@ -130,8 +171,6 @@ __device__ int lm(const Curve& cv, float p[4], float& cost, int& flags) {
     int it = 0;
     while (it < 100) {
         ++it;
-        float r[2], J[2][4];
-        model_rows(cv, p, r, J);
         float H[10], g[4];
         {
             int k = 0;
@@ -142,32 +181,69 @@ __device__ int lm(const Curve& cv, float p[4], float& cost, int& flags) {
                 g[a] = warp_sum_bcast(J[0][a] * r[0] + J[1][a] * r[1]);
             }
         }
-        bool accepted = false, first_try = true;
-        float pn[4], cn = 0.f;
-        while (true) {
-            float dp[4];
-            if (solve4(H, g, mu, dp)) {
+        bool accepted = false, first_try = false, first_round = true;
+        float dec = 0.f;
+        // the first value is always tried; later ones only while mu <= 1e12
+        while (!accepted && (first_round || !(mu > 1e12f))) {
+            float mus[kTrials];
+            mus[0] = mu;
 #pragma unroll
-                for (int a = 0; a < 4; ++a) pn[a] = p[a] + dp[a];
-                pn[3] = fminf(fmaxf(pn[3], 0.05f), 3.f);
-                cn = cost_at(cv, pn);
-                if (isfinite(cn) && cn < cost) {
-                    accepted = true;
-                    break;
+            for (int k = 1; k < kTrials; ++k) mus[k] = mus[k - 1] * 10.f;
+            float mw = mus[0];
+#pragma unroll
+            for (int k = 1; k < kTrials; ++k)
+                if (w == k) mw = mus[k];
+            const bool tried = (w == 0 && first_round) || !(mw > 1e12f);
+            Trial t;
+            const bool ok = tried && lm_trial(cv, p, H, g, mw, cost, t);
+            if (ok) {
+                if (lane == 0) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) sh.p[w][a] = t.p[a];
+                    sh.cost[w] = t.cost;
+                }
+                sh.rj[w][lane][0] = t.r[0];
+                sh.rj[w][lane][1] = t.r[1];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    sh.rj[w][lane][2 + a] = t.J[0][a];
+                    sh.rj[w][lane][6 + a] = t.J[1][a];
                 }
             }
-            mu *= 10.f;
-            first_try = false;
-            if (mu > 1e12f) break;
+            if (lane == 0) sh.ok[w] = ok ? 1 : 0;
+            __syncthreads();
+            int acc = -1;
+#pragma unroll
+            for (int k = kTrials - 1; k >= 0; --k)
+                if (sh.ok[k]) acc = k;
+            if (acc >= 0) {
+                accepted = true;
+                first_try = first_round && acc == 0;
+#pragma unroll
+                for (int k = 0; k < kTrials; ++k)
+                    if (k == acc) mu = mus[k];
+                const float ca = sh.cost[acc];
+                dec = cost - ca;
+                cost = ca;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) p[a] = sh.p[acc][a];
+                r[0] = sh.rj[acc][lane][0];
+                r[1] = sh.rj[acc][lane][1];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    J[0][a] = sh.rj[acc][lane][2 + a];
+                    J[1][a] = sh.rj[acc][lane][6 + a];
+                }
+            } else {
+                mu = mus[kTrials - 1] * 10.f;
+            }
+            first_round = false;
+            __syncthreads();   // shared slots read before the next round writes them
         }
         if (!accepted) {
             flags = DDM_FIT_CONVERGED;
             break;
         }
-        const float dec = cost - cn;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) p[a] = pn[a];
-        cost = cn;
         mu = fmaxf(mu * 0.1f, 1e-12f);
         if (first_try && dec <= 1e-6f * cost) {
             flags = DDM_FIT_CONVERGED;
@@ -207,14 +283,15 @@ __device__ void heuristic_seed(const Curve& cv, int lane, float p[4]) {
     p[3] = 1.f;
 }
 
-// grid: ceil(n / kWarpsPerBlock); block: 32 * kWarpsPerBlock
-__global__ void lm_kernel(const float* __restrict__ x, const float* __restrict__ p8,
+// grid: n (one curve per block); block: 32 * kTrials
+__global__ void __launch_bounds__(32 * kTrials) lm_kernel(const float* __restrict__ x, const float* __restrict__ p8,
                           const float* __restrict__ mlp_o, int n, int mode,
                           const float* __restrict__ lag_ll, float* __restrict__ params,
                           float* __restrict__ cost_out, int* __restrict__ iters_out,
                           int* __restrict__ flags_out) {
+    __shared__ TrialShare sh;
     const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int c = blockIdx.x;
     if (c >= n) return;
     Curve cv;
     cv.y[0] = x[(size_t)c * kLags + lane];
@@ -226,7 +303,7 @@ __global__ void lm_kernel(const float* __restrict__ x, const float* __restrict__
     int flags = 0, it = 0;
     if (mode == DDM_FIT_LM) {
         heuristic_seed(cv, lane, p);
-        it = lm(cv, p, cost, flags);
+        it = lm(cv, p, cost, flags, sh);
     } else {
         const float o0 = mlp_o[(size_t)c * 4 + 0], o1 = mlp_o[(size_t)c * 4 + 1];
         const float o2 = mlp_o[(size_t)c * 4 + 2], o3 = mlp_o[(size_t)c * 4 + 3];
@@ -242,17 +319,17 @@ __global__ void lm_kernel(const float* __restrict__ x, const float* __restrict__
             flags = DDM_FIT_CONVERGED | DDM_FIT_MLP_ACCEPTED;
         } else {
             float q[4] = {p[0], p[1], p[2], p[3]};
-            it = lm(cv, q, cost, flags);
+            it = lm(cv, q, cost, flags, sh);
             if (flags & DDM_FIT_NONFINITE) {
                 heuristic_seed(cv, lane, q);
-                it += lm(cv, q, cost, flags);
+                it += lm(cv, q, cost, flags, sh);
                 flags |= DDM_FIT_FALLBACK;
             }
 #pragma unroll
             for (int a = 0; a < 4; ++a) p[a] = q[a];
         }
     }
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
         params[(size_t)c * 4 + 0] = p[0] * P8;
         params[(size_t)c * 4 + 1] = expf(p[2]);
         params[(size_t)c * 4 + 2] = p[3];
@@ -325,9 +402,7 @@ ddm_status launch_fit(ddm_plan_s* p, const float* Dr, int n, int mode, const ddm
             if (st != DDM_OK) return st;
         }
     }
-    const int blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    lm_kernel<<<blocks, 32 * kWarpsPerBlock, 0, s>>>(x, p8, o, n, mode, p->lag_ll, params, cost, iters,
-                                                     flags);
+    lm_kernel<<<n, 32 * kTrials, 0, s>>>(x, p8, o, n, mode, p->lag_ll, params, cost, iters, flags);
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 
