@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define DDM_ABI_VERSION 1
+#define DDM_ABI_VERSION 2
 
 typedef enum ddm_status {
     DDM_OK = 0,
@@ -85,6 +85,15 @@ typedef struct ddm_plan_desc {
     size_t max_workspace_bytes; /* 0 = no limit; else plan creation fails with
                                    DDM_ERR_OOM if the workspace would exceed it */
     int spatial_path;  /* ddm_spatial_path: which step-one kernels run */
+    int64_t q_begin;   /* stored wave vectors [q_begin, q_end) (storage order of the
+                          spectrum) that step two and the radial stage cover; 0, 0 = all.
+                          Splits one stack across GPUs: every rank runs step one in full,
+                          step two on its own range (D rows of other wave vectors are
+                          left untouched), and ddm_azimuthal_sums() over its range; the
+                          ranks' sums and counts add up to those of the whole plane.
+                          q_begin must be a multiple of 64, q_begin < q_end <= n_q;
+                          DDM_ERR_INVALID_ARG otherwise */
+    int64_t q_end;
 } ddm_plan_desc;
 
 typedef struct ddm_plan_s* ddm_plan;
@@ -151,7 +160,8 @@ ddm_status ddm_structure_function(ddm_plan p, const void* frames, float* D, void
 /* Radial (azimuthal) average over |q| bins -- not in the paper.
  *   D      [n_q][N] float32, device (as written above)
  *   Dr     [n_bins][N] float32, device, written: mean of D over the FULL-plane modes of
- *          each bin (half-plane modes with 0 < kx < W/2 count twice); 0 for empty bins
+ *          each bin (half-plane modes with 0 < kx < W/2 count twice); 0 for empty bins.
+ *          A plan restricted to a wave-vector range averages over that range only
  *   counts [n_bins] int32, device, written (may be NULL): full-plane modes per bin
  * Bins: |q| = 2 pi sqrt((ky'/H)^2 + (kx'/W)^2) rad/px (signed ky', kx'), n_bins uniform
  * bins over [0, pi sqrt 2], b = min(floor(|q| n_bins / (pi sqrt 2)), n_bins - 1), the floor
@@ -159,6 +169,18 @@ ddm_status ddm_structure_function(ddm_plan p, const void* frames, float* D, void
  * reproducible run to run.  Needs desc.n_bins > 0. */
 ddm_status ddm_azimuthal_average(ddm_plan p, const float* D, float* Dr, int* counts,
                                  void* stream);
+
+/* The radial stage before its division, for combining ranks that split a stack by
+ * wave-vector range (ddm_plan_desc.q_begin/q_end):
+ *   D      [n_q][N] float32, device (rows of the plan's range are read)
+ *   sums   [n_bins][N] float32, device, written: sum over the plan's stored wave vectors in
+ *          each bin of w_q D(q, m), w_q = 2 for 0 < kx < W/2, else 1
+ *   counts [n_bins] int32, device, written: sum of w_q over the same wave vectors
+ * Adding every rank's sums and counts and dividing (0 for empty bins) gives
+ * ddm_azimuthal_average of the whole plane up to the order of the FP32 additions.  Same
+ * fixed summation order per plan as ddm_azimuthal_average.  Needs desc.n_bins > 0. */
+ddm_status ddm_azimuthal_sums(ddm_plan p, const float* D, float* sums, int* counts,
+                              void* stream);
 
 /* ---- fit of D(|q|, dt) (not in the paper: the analysis step that follows it) ---------- */
 

@@ -57,6 +57,7 @@ class ddm_plan_desc(ctypes.Structure):
         ("n_bins", ctypes.c_int), ("subtract_ref", ctypes.c_int), ("fix_lags", ctypes.c_int),
         ("max_workspace_bytes", ctypes.c_size_t),
         ("spatial_path", ctypes.c_int),
+        ("q_begin", ctypes.c_int64), ("q_end", ctypes.c_int64),
     ]
 
 
@@ -86,6 +87,7 @@ def lib():
         "ddm_temporal_sf": (st, [vp, vp, vp, vp]),
         "ddm_structure_function": (st, [vp, vp, vp, vp]),
         "ddm_azimuthal_average": (st, [vp, vp, vp, vp, vp]),
+        "ddm_azimuthal_sums": (st, [vp, vp, vp, vp, vp]),
         "ddm_structure_function_static": (st, [vp, vp, vp, vp]),
         "ddm_fit_features": (st, [vp, vp, c_int, vp, vp, vp]),
         "ddm_fit": (st, [vp, vp, c_int, c_int, vp, vp, vp, vp, vp, vp]),
@@ -161,7 +163,8 @@ class Plan:
 
     def __init__(self, H: int, W: int, N: int, dtype: str = "u16", n_bins: int = 0,
                  precision: int = DDM_PREC_FP32, subtract_ref: int = 1, M: int = 0,
-                 fix_lags: int = 0, max_workspace_bytes: int = 0, spatial_path: int = 0):
+                 fix_lags: int = 0, max_workspace_bytes: int = 0, spatial_path: int = 0,
+                 q_begin: int = 0, q_end: int = 0):
         L = lib()
         d = ddm_plan_desc()
         _check(L.ddm_plan_desc_init(ctypes.byref(d), H, W, N), "ddm_plan_desc_init")
@@ -173,6 +176,8 @@ class Plan:
         d.fix_lags = fix_lags
         d.max_workspace_bytes = max_workspace_bytes
         d.spatial_path = spatial_path
+        d.q_begin = q_begin
+        d.q_end = q_end
         self.desc = d
         self.H, self.W, self.N, self.n_bins = H, W, N, n_bins
         self.dtype = dtype
@@ -230,6 +235,13 @@ class Plan:
         _check(lib().ddm_azimuthal_average(self._h, _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
                                            _dev_ptr(Dr, "Dr", torch.float32, self.n_bins * self.N),
                                            cp, _stream_ptr(stream)), "ddm_azimuthal_average")
+
+    def azimuthal_sums(self, D, sums, counts, stream=None):
+        import torch
+        _check(lib().ddm_azimuthal_sums(self._h, _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
+                                        _dev_ptr(sums, "sums", torch.float32, self.n_bins * self.N),
+                                        _dev_ptr(counts, "counts", torch.int32, self.n_bins),
+                                        _stream_ptr(stream)), "ddm_azimuthal_sums")
 
     def fit_features(self, Dr, n_curves, x, p8, stream=None):
         import torch

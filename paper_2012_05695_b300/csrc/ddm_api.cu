@@ -117,6 +117,11 @@ ddm_status validate(const ddm_plan_desc* d) {
         if ((int64_t)d->M < 2 * (int64_t)d->N - 1) return DDM_ERR_INVALID_ARG;
         if (d->M != 2 * L) return DDM_ERR_UNSUPPORTED;
     }
+    if (d->q_begin != 0 || d->q_end != 0) {
+        const int64_t nq = (int64_t)d->H * (d->W / 2 + 1);
+        if (d->q_begin < 0 || d->q_begin % 64 != 0 || d->q_end <= d->q_begin || d->q_end > nq)
+            return DDM_ERR_INVALID_ARG;
+    }
     if (d->max_workspace_bytes != 0 && workspace_bytes(*d) > d->max_workspace_bytes)
         return DDM_ERR_OOM;
     return DDM_OK;
@@ -189,6 +194,9 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
     p->L = 1 << ilog2(desc->N);
     p->Wh = desc->W / 2;
     p->n_q = (int64_t)desc->H * (p->Wh + 1);
+    const bool ranged = desc->q_begin != 0 || desc->q_end != 0;
+    p->q0 = ranged ? desc->q_begin : 0;
+    p->q1 = ranged ? desc->q_end : p->n_q;
     const int KD = std::min(32, p->L / 2);
     p->kd = std::min(KD, desc->N - 1);
     p->fix_lags = desc->fix_lags > 0 ? desc->fix_lags : 8;
@@ -214,14 +222,17 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
         st = upload(&p->tw2, tw2);
         if (st == DDM_OK) st = upload(&p->inv, inv);
     }
-    // radial bins: CSR of public q per bin (ascending), full-plane counts
+    // radial bins: CSR of public q per bin (ascending), full-plane counts, over the stored
+    // wave vectors of the plan's range
     if (st == DDM_OK && desc->n_bins > 0) {
         const int H = desc->H, W = desc->W, Wh = p->Wh, nb = desc->n_bins;
-        std::vector<int> bin_of((size_t)p->n_q);
+        std::vector<int> bin_of((size_t)p->n_q, -1);
         std::vector<int> count(nb, 0), start(nb + 1, 0);
         for (int ky = 0; ky < H; ++ky) {
             const int ys = ky > H / 2 ? ky - H : ky;
             for (int kx = 0; kx <= Wh; ++kx) {
+                const int64_t stored = kx < Wh ? (int64_t)ky * Wh + kx : (int64_t)H * Wh + ky;
+                if (stored < p->q0 || stored >= p->q1) continue;
                 const int b = radial_bin(ys, kx, H, W, nb);
                 bin_of[(size_t)ky * (Wh + 1) + kx] = b;
                 count[b] += (kx == 0 || kx == Wh) ? 1 : 2;
@@ -229,8 +240,9 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
             }
         }
         for (int b = 0; b < nb; ++b) start[b + 1] += start[b];
-        std::vector<int> items((size_t)p->n_q), fill(start.begin(), start.end() - 1);
-        for (int64_t q = 0; q < p->n_q; ++q) items[fill[bin_of[q]]++] = (int)q;
+        std::vector<int> items((size_t)start[nb] > 0 ? (size_t)start[nb] : 1), fill(start.begin(), start.end() - 1);
+        for (int64_t q = 0; q < p->n_q; ++q)
+            if (bin_of[q] >= 0) items[fill[bin_of[q]]++] = (int)q;
         st = upload(&p->bin_start, start);
         if (st == DDM_OK) st = upload(&p->bin_q, items);
         if (st == DDM_OK) st = upload(&p->bin_count, count);
@@ -319,7 +331,13 @@ ddm_status ddm_azimuthal_average(ddm_plan p, const float* D, float* Dr, int* cou
                                  void* stream) {
     if (!check_plan(p) || !D || !Dr) return DDM_ERR_INVALID_ARG;
     if (p->d.n_bins <= 0) return DDM_ERR_INVALID_ARG;
-    return launch_radial(p, D, Dr, counts, (cudaStream_t)stream);
+    return launch_radial(p, D, Dr, counts, true, (cudaStream_t)stream);
+}
+
+ddm_status ddm_azimuthal_sums(ddm_plan p, const float* D, float* sums, int* counts, void* stream) {
+    if (!check_plan(p) || !D || !sums || !counts) return DDM_ERR_INVALID_ARG;
+    if (p->d.n_bins <= 0) return DDM_ERR_INVALID_ARG;
+    return launch_radial(p, D, sums, counts, false, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -11,6 +11,7 @@ struct ddm_plan_s {
     int L;              // transform length in time: smallest power of two >= N (M = 2L)
     int Wh;             // W / 2
     int64_t n_q;        // H * (W/2 + 1)
+    int64_t q0, q1;     // stored wave vectors covered by step two and the radial stage
     int device;
     int n_sm;
     int kd;             // number of trailing lags evaluated by direct differences
@@ -45,7 +46,7 @@ size_t spectrum_frame_stride(const ddm_plan_s* p);   // complex elements per fra
 ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
                           cudaStream_t s);
 ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s);
-ddm_status launch_radial(const ddm_plan_s* p, const float* D, float* Dr, int* counts,
+ddm_status launch_radial(const ddm_plan_s* p, const float* D, float* Dr, int* counts, bool normalise,
                          cudaStream_t s);
 
 int ilog2(int v);

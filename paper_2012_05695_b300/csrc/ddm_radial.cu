@@ -19,7 +19,7 @@ constexpr int kWarps = 8;
 __global__ void __launch_bounds__(32 * kWarps)
 radial_kernel(const float* __restrict__ D, float* __restrict__ Dr, int N, int Wh,
               const int* __restrict__ bin_start, const int* __restrict__ bin_q,
-              const int* __restrict__ bin_count) {
+              const int* __restrict__ bin_count, int normalise) {
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -60,18 +60,18 @@ radial_kernel(const float* __restrict__ D, float* __restrict__ Dr, int N, int Wh
 #pragma unroll
         for (int j = 0; j < kLagsPerWarp; ++j)
             if (j == lane) val = acc[j];
-        Dr[(int64_t)b * N + m0 + lane] = c > 0 ? val / (float)c : 0.f;
+        Dr[(int64_t)b * N + m0 + lane] = !normalise ? val : (c > 0 ? val / (float)c : 0.f);
     }
 }
 
 }  // namespace
 
-ddm_status launch_radial(const ddm_plan_s* p, const float* D, float* Dr, int* counts,
+ddm_status launch_radial(const ddm_plan_s* p, const float* D, float* Dr, int* counts, bool normalise,
                          cudaStream_t s) {
     const int n_bins = p->d.n_bins, N = p->d.N;
     dim3 grid(n_bins, (N + kLagsPerWarp * kWarps - 1) / (kLagsPerWarp * kWarps));
     radial_kernel<<<grid, 32 * kWarps, 0, s>>>(D, Dr, N, p->Wh, p->bin_start, p->bin_q,
-                                               p->bin_count);
+                                               p->bin_count, normalise ? 1 : 0);
     if (cudaGetLastError() != cudaSuccess) return DDM_ERR_CUDA;
     if (counts) {
         if (cudaMemcpyAsync(counts, p->bin_count, sizeof(int) * (size_t)n_bins,

@@ -105,7 +105,8 @@ struct TArgs {
     int kd;           // directly evaluated trailing lags (<= 32, < N)
     int H, Wh, lwh;   // for the storage -> public q map (lwh = log2 Wh)
     int64_t n_q;      // stored wave vectors = spectrum frame stride
-    int64_t n_tiles;  // tiles (of one group, L >= 512; of one CTA, L <= 256)
+    int64_t q0, q1;   // stored wave vectors this launch covers: [q0, q1)
+    int64_t n_tiles;  // tiles of [q0, q1) (of one group, L >= 512; of one CTA, L <= 256)
     int vec4;         // D rows 16-byte aligned (N % 4 == 0 and D aligned)
     int fix;          // FP64-fixup tier: lags 1..fix by direct differences (0 = off)
     const float2* tw;
@@ -211,7 +212,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
     const AddrPaddedInterleaved<QG, T> xaddr{ql};
     const int N = a.N;
     const int kd = a.kd;
-    const int64_t nq = a.n_q;
+    const int64_t q0 = a.q0, q1 = a.q1;
     const int64_t gstride = (int64_t)gridDim.x * NG;
     bool timed_out = false;
     float chk = 0.f;                      // becomes NaN if any D value is not finite
@@ -225,7 +226,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             mbar_expect_tx(bar, (uint32_t)(C::NBOX * C::BOX_T * QG * sizeof(float2)));
 #pragma unroll
             for (int b = 0; b < C::NBOX; ++b)
-                tma_load_2d(xs + b * C::BOX_T * QG, &tmap, (int)(2 * t * QG), b * C::BOX_T, bar);
+                tma_load_2d(xs + b * C::BOX_T * QG, &tmap, (int)(2 * (q0 + t * QG)), b * C::BOX_T, bar);
         }
     };
     // Wait for the copy in flight; the decision to give up is the same in the whole group.
@@ -456,8 +457,8 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
         sync();
         if (a.vec4) {
             if (tg < QG) {
-                const int64_t sr = gt * QG + tg;
-                if (sr < nq) {
+                const int64_t sr = q0 + gt * QG + tg;
+                if (sr < q1) {
                     float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
                     bulk_store(drow, ab + tg * DS, (uint32_t)N * (uint32_t)sizeof(float));
                 }
@@ -466,8 +467,8 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
         } else {
 #pragma unroll 1
             for (int r = 0; r < QG; ++r) {
-                const int64_t sr = gt * QG + r;
-                if (sr >= nq) break;
+                const int64_t sr = q0 + gt * QG + r;
+                if (sr >= q1) break;
                 float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
                 for (int m = tg; m < N; m += GT) drow[m] = ab[r * DS + m];
             }
@@ -543,20 +544,20 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
     const int i = tid / QT;
     const int N = a.N;
     const int kd = a.kd;
-    const int64_t nq = a.n_q;
-    const uint32_t nq32 = (uint32_t)nq;   // N * n_q < 2^32 (checked at plan creation)
+    const int64_t q0 = a.q0, q1 = a.q1;
+    const uint32_t nq32 = (uint32_t)a.n_q;   // N * n_q < 2^32 (checked at plan creation)
     const AddrInterleaved<QT> addr{ql};
     bool bad = false;
 
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-        const int64_t s = tile * QT + ql;
-        const bool valid = s < nq;
+        const int64_t s = q0 + tile * QT + ql;
+        const bool valid = s < q1;
         const float2* src = spec + (valid ? s : 0);
 
         // ---- prefetch the next tile of this CTA into L2: its DRAM fetch overlaps this tile
         {
-            const int64_t sn = (tile + gridDim.x) * QT + ql;
-            if (sn < nq) {
+            const int64_t sn = q0 + (tile + gridDim.x) * QT + ql;
+            if (sn < q1) {
                 const float2* pn = spec + sn;
 #pragma unroll
                 for (int u = 0; u < P; ++u) {
@@ -713,8 +714,8 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
         }
         __syncthreads();
         for (int r = 0; r < QT; ++r) {
-            const int64_t sr = tile * QT + r;
-            if (sr >= nq) break;
+            const int64_t sr = q0 + tile * QT + r;
+            if (sr >= q1) break;
             float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
             for (int m = tid; m < N; m += NT) {
                 const float d = xf[r * DS + m];
@@ -769,7 +770,9 @@ void fill_args(TArgs& a, const ddm_plan_s* p, float* D, int qt) {
     a.vec4 = (p->d.N % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
     a.fix = (p->d.precision == DDM_PREC_FP32_FP64FIX) ? p->fix_lags : 0;
     a.n_q = p->n_q;
-    a.n_tiles = (p->n_q + qt - 1) / qt;
+    a.q0 = p->q0;
+    a.q1 = p->q1;
+    a.n_tiles = (p->q1 - p->q0 + qt - 1) / qt;
     a.tw = p->tw_t;
     a.tw2 = p->tw2;
     a.inv = p->inv;
