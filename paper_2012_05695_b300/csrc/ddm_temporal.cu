@@ -19,11 +19,11 @@
 // instead: few terms, and no cancellation against the much larger power sums.
 //
 // Two kernels share this arithmetic:
-//  * L >= 512 (the production sizes): 512-thread CTAs split into four independent groups of
-//    128 threads.  A group owns QG = 128/T consecutive stored wave vectors at a time; their
-//    tile ([L frames][QG] complex) arrives by TMA bulk tensor copies, the group's threads
-//    synchronise on a named barrier of their own, so the four groups drift apart and one
-//    group's copy wait hides behind the others' transforms.  The next tile's copy is issued
+//  * L >= 512 (the production sizes): 512-thread CTAs split into independent groups (two
+//    of 256 threads at L = 1024, four of 128 at L = 512).  A group owns QG = 8 consecutive
+//    stored wave vectors at a time; their tile ([L frames][QG] complex) arrives by TMA bulk
+//    tensor copies, the group's threads synchronise on a named barrier of their own, so the
+//    groups drift apart and one group's copy wait hides behind the others' transforms.  The next tile's copy is issued
 //    before the D rows are staged, and the D rows leave shared memory by bulk async copies.
 //    Each tile is copied three times (the odd-bin, even-bin and power-sum passes each need
 //    g and there is no room to keep it): once from DRAM, twice from L2.
@@ -90,15 +90,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
     return true;
 }
-// true in every thread of the 128-thread group on named barrier `id` if pred holds in any
-__device__ __forceinline__ bool group_any(bool pred, int id) {
+// true in every thread of the group of `nthreads` on named barrier `id` if pred holds in any
+__device__ __forceinline__ bool group_any(bool pred, int id, int nthreads) {
     uint32_t r;
     asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n"
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n"
         " selp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r) : "r"((uint32_t)pred), "r"(id) : "memory");
+        : "=r"(r) : "r"((uint32_t)pred), "r"(id), "r"(nthreads) : "memory");
     return r != 0;
 }
+
+// named barrier `id` over the threads of one group
+template <int NTHREADS>
+struct SyncGroup {
+    int id;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NTHREADS) : "memory");
+    }
+};
 
 struct TArgs {
     int N;            // frames
@@ -125,15 +134,16 @@ __device__ __forceinline__ int public_q(int s, int H, int Wh, int lwh) {
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 
 // =====================================================================================
-// L >= 512: four independent 128-thread groups per CTA, tiles by TMA
+// L >= 512: independent thread groups per CTA (NGROUPS of 512 / NGROUPS threads), tiles
+// by TMA
 // =====================================================================================
-template <int LOG2L>
+template <int LOG2L, int NGROUPS>
 struct GShape {
     static constexpr int L = 1 << LOG2L;
     using S = FftShape<L>;
     static constexpr int P = S::P, T = S::T;
-    static constexpr int NG = 4;              // groups per CTA
-    static constexpr int GT = 128;            // threads per group
+    static constexpr int NG = NGROUPS;        // groups per CTA
+    static constexpr int GT = 512 / NG;       // threads per group
     static constexpr int NT = NG * GT;
     static constexpr int QG = GT / T;         // wave vectors per group tile
     static constexpr int IW = 32 / QG;        // threads of one wave vector in a warp
@@ -163,7 +173,7 @@ struct GShape {
     static constexpr size_t OFF_FIX = OFF_RED + NG * G_RED;
     static constexpr size_t BYTES = OFF_FIX + NG * G_FIX;
     static_assert(L >= 512 && T >= 16 && QG * T == GT, "grouped kernel: L >= 512");
-    static_assert(BYTES + 64 <= 232448, "temporal kernel shared memory exceeds 227 KB");
+    static_assert(BYTES + 1024 <= 232448, "temporal kernel shared memory exceeds 227 KB");
     static_assert(G_XS % 1024 == 0, "TMA destinations stay 1024-byte aligned");
     static_assert((DS % 4) == 0 && (G_AB % 16) == 0, "D rows must be 16-byte aligned for bulk copies");
     static_assert((size_t)NWG * QG * sizeof(float2) <= G_RED, "mean partials must fit");
@@ -171,10 +181,10 @@ struct GShape {
                   "padded prefix rows must fit the tile buffer");
 };
 
-template <int LOG2L, bool FIXUP>
-__global__ void __launch_bounds__(GShape<LOG2L>::NT, 1)
+template <int LOG2L, int NGROUPS, bool FIXUP>
+__global__ void __launch_bounds__(GShape<LOG2L, NGROUPS>::NT, 1)
 temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUtensorMap tmap) {
-    using C = GShape<LOG2L>;
+    using C = GShape<LOG2L, NGROUPS>;
     constexpr int L = C::L, P = C::P, T = C::T, QG = C::QG, NG = C::NG, GT = C::GT;
     constexpr int NWG = C::NWG, G = C::G, KT = C::KT, DS = C::DS, FM = C::FIX_MAX;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -208,7 +218,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
     const int ql = tg % QG;
     const int i = tg / QG;
     const int lane = tid & 31, wg = tg >> 5;
-    const SyncGroup128 sync{bar_id};
+    const SyncGroup<GT> sync{bar_id};
     const AddrPaddedInterleaved<QG, T> xaddr{ql};
     const int N = a.N;
     const int kd = a.kd;
@@ -232,7 +242,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
     // Wait for the copy in flight; the decision to give up is the same in the whole group.
     auto wait = [&]() -> bool {
         const bool ok = mbar_wait_bounded(bar, phase);
-        if (group_any(!ok, bar_id)) return false;
+        if (group_any(!ok, bar_id, GT)) return false;
         phase ^= 1u;
         return true;
     };
@@ -247,7 +257,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
     int64_t gt = (int64_t)blockIdx.x * NG + grp;
     if (gt < a.n_tiles) issue(gt);
     for (; gt < a.n_tiles; gt += gstride) {
-        // (no L2 prefetch of later tiles: with four groups per SM their copies already
+        // (no L2 prefetch of later tiles: with several groups per SM their copies already
         // overlap the other groups' work, and prefetched lines measurably crowd the
         // current tiles' reloads out of L2 at 512x512x1024: 1.45 ms with, 1.15 ms without)
         if (!wait()) { timed_out = true; break; }
@@ -779,16 +789,16 @@ void fill_args(TArgs& a, const ddm_plan_s* p, float* D, int qt) {
     a.status = p->dev_status;
 }
 
-template <int LOG2L, bool FIXUP>
+template <int LOG2L, bool FIXUP, int NGROUPS>
 ddm_status launch_grouped(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
-    using C = GShape<LOG2L>;
+    using C = GShape<LOG2L, NGROUPS>;
     if ((reinterpret_cast<uintptr_t>(spec) & 15) != 0) return DDM_ERR_INVALID_ARG;
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof(tmap));
     if (!make_spectrum_map(&tmap, spec, p->n_q, p->d.N, C::QG)) return DDM_ERR_CUDA;
     TArgs a;
     fill_args(a, p, D, C::QG);
-    auto k = temporal_sf_kernel<LOG2L, FIXUP>;
+    auto k = temporal_sf_kernel<LOG2L, NGROUPS, FIXUP>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
         cudaSuccess)
         return DDM_ERR_CUDA;
@@ -826,8 +836,11 @@ ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cu
         case 6: return launch_small<6>(p, spec, D, s);
         case 7: return launch_small<7>(p, spec, D, s);
         case 8: return launch_small<8>(p, spec, D, s);
-        case 9: return fix ? launch_grouped<9, true>(p, spec, D, s) : launch_grouped<9, false>(p, spec, D, s);
-        case 10: return fix ? launch_grouped<10, true>(p, spec, D, s) : launch_grouped<10, false>(p, spec, D, s);
+        // groups per CTA: the choice that gives 64-byte TMA rows (QG = 8 wave vectors) at
+        // both lengths.  Measured at 512x512x1024 (L = 1024): 1 group of 512 threads (128-byte
+        // rows, lockstep) 1.13 ms, 2 groups 1.05 ms, 4 groups (32-byte rows) 1.15 ms.
+        case 9: return fix ? launch_grouped<9, true, 4>(p, spec, D, s) : launch_grouped<9, false, 4>(p, spec, D, s);
+        case 10: return fix ? launch_grouped<10, true, 2>(p, spec, D, s) : launch_grouped<10, false, 2>(p, spec, D, s);
         default: return DDM_ERR_UNSUPPORTED;
     }
 }
