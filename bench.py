@@ -431,7 +431,10 @@ def run_ours(args):
     # ---- precision tiers on the same stack: the FP32+FP64-fixup temporal stage
     tiers = {"fp32": {"temporal_ms": tm_ms}}
     D_fix = None
-    if rank == 0:
+    fix_ok = N_FRAMES > 256                         # the tier is built for 257 <= N <= 1024
+    if rank == 0 and not fix_ok:
+        tiers["fp32_fp64fix"] = {"unsupported": f"N = {N_FRAMES}: the FP64-fixup tier needs 257 <= N <= 1024"}
+    if rank == 0 and fix_ok:
         plan_fix = ddm.Plan(H, W, N_FRAMES, dtype="u16", precision=ddm.DDM_PREC_FP32_FP64FIX)
         D_fix = torch.empty_like(D)
         plan.spatial_fft(frames, spec, stream)

@@ -518,24 +518,27 @@ namespace {
 // A CTA owns PAIRS consecutive row pairs of one frame.  Those rows, and the same rows of
 // frame 0, are contiguous in memory: two cp.async.bulk copies bring them into shared
 // memory (mbarrier with a bounded wait) instead of 2-byte scattered loads, and the region
-// then serves as the transform's exchange buffer (XOR-swizzled, no padding).  ~64 KB per
-// CTA, so three CTAs share an SM.
+// then serves as the transform's exchange buffer (XOR-swizzled, no padding).  Rows of 128
+// bytes or more are staged one copy per row with a 16-byte pad after each, so that the two
+// row pairs a warp reads sit on different banks.  ~70 KB per CTA, three CTAs per SM.
 template <int W, typename In>
 struct RowBulkShape {
     static constexpr int T = FftShape<W>::T, P = FftShape<W>::P;
     static constexpr int BYTES_ROW = W * (int)sizeof(In);
+    static constexpr int PAD = (BYTES_ROW >= 128 && BYTES_ROW % 128 == 0) ? 16 : 0;
+    static constexpr int ROW_STRIDE = BYTES_ROW + PAD;                   // staged row pitch
     static constexpr int P1 = 256 / T;
     static constexpr int P2 = 16384 / BYTES_ROW > 0 ? 16384 / BYTES_ROW : 1;
     static constexpr int PAIRS = (P1 < P2 ? P1 : P2) < 1 ? 1 : (P1 < P2 ? P1 : P2);
     static constexpr int NT = PAIRS * T;
-    static constexpr size_t STAGE = (size_t)2 * 2 * PAIRS * BYTES_ROW;   // frame rows + frame-0 rows
+    static constexpr size_t STAGE = (size_t)2 * 2 * PAIRS * ROW_STRIDE;  // frame rows + frame-0 rows
     static constexpr size_t XCH = (size_t)PAIRS * W * sizeof(float2);
     static constexpr size_t XBYTES = STAGE > XCH ? STAGE : XCH;
     static constexpr size_t BYTES = XBYTES + (T > 1 ? W * sizeof(float2) : 0);
 };
 
 template <int W, typename In>
-__global__ void __launch_bounds__(RowBulkShape<W, In>::NT)
+__global__ void __launch_bounds__(RowBulkShape<W, In>::NT, 3)
 row_bulk_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H, size_t frame_stride,
                 int subtract_ref, const float2* __restrict__ tw_g, unsigned* status) {
     using C = RowBulkShape<W, In>;
@@ -552,23 +555,39 @@ row_bulk_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
     const In* src = frames + ((size_t)t * H + 2 * pair0) * W;
     const In* ref = frames + (size_t)(2 * pair0) * W;
     unsigned char* stage_f = smem_raw;
-    unsigned char* stage_r = smem_raw + (size_t)2 * PAIRS * C::BYTES_ROW;
+    unsigned char* stage_r = smem_raw + (size_t)2 * PAIRS * C::ROW_STRIDE;
     if (tid == 0) {
         mbar_init_s(&bar);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cvta_smem(&bar)),
                      "r"(subtract_ref ? 2 * bytes : bytes) : "memory");
-        for (uint32_t off = 0; off < bytes; off += 16384u) {
-            const uint32_t n = bytes - off < 16384u ? bytes - off : 16384u;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                ::"r"(cvta_smem(stage_f + off)), "l"(reinterpret_cast<const unsigned char*>(src) + off),
-                "r"(n), "r"(cvta_smem(&bar)) : "memory");
-            if (subtract_ref)
+        if constexpr (C::PAD == 0) {
+            for (uint32_t off = 0; off < bytes; off += 16384u) {
+                const uint32_t n = bytes - off < 16384u ? bytes - off : 16384u;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                    ::"r"(cvta_smem(stage_r + off)), "l"(reinterpret_cast<const unsigned char*>(ref) + off),
+                    ::"r"(cvta_smem(stage_f + off)), "l"(reinterpret_cast<const unsigned char*>(src) + off),
                     "r"(n), "r"(cvta_smem(&bar)) : "memory");
+                if (subtract_ref)
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                        ::"r"(cvta_smem(stage_r + off)), "l"(reinterpret_cast<const unsigned char*>(ref) + off),
+                        "r"(n), "r"(cvta_smem(&bar)) : "memory");
+            }
+        } else {
+            for (int r = 0; r < 2 * npairs; ++r) {
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                    ::"r"(cvta_smem(stage_f + (size_t)r * C::ROW_STRIDE)),
+                    "l"(reinterpret_cast<const unsigned char*>(src) + (size_t)r * C::BYTES_ROW),
+                    "r"((uint32_t)C::BYTES_ROW), "r"(cvta_smem(&bar)) : "memory");
+                if (subtract_ref)
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                        ::"r"(cvta_smem(stage_r + (size_t)r * C::ROW_STRIDE)),
+                        "l"(reinterpret_cast<const unsigned char*>(ref) + (size_t)r * C::BYTES_ROW),
+                        "r"((uint32_t)C::BYTES_ROW), "r"(cvta_smem(&bar)) : "memory");
+            }
         }
     }
     if constexpr (T > 1) {
@@ -578,8 +597,10 @@ row_bulk_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
     const bool ok = mbar_wait_s(&bar, 0);
     const int i = tid % T, j = tid / T;
     const bool active = j < npairs;
-    const In* fa = reinterpret_cast<const In*>(stage_f) + (size_t)(2 * j) * W;
-    const In* ra = reinterpret_cast<const In*>(stage_r) + (size_t)(2 * j) * W;
+    const In* fa = reinterpret_cast<const In*>(stage_f + (size_t)(2 * j) * C::ROW_STRIDE);
+    const In* fb = reinterpret_cast<const In*>(stage_f + (size_t)(2 * j + 1) * C::ROW_STRIDE);
+    const In* ra = reinterpret_cast<const In*>(stage_r + (size_t)(2 * j) * C::ROW_STRIDE);
+    const In* rb = reinterpret_cast<const In*>(stage_r + (size_t)(2 * j + 1) * C::ROW_STRIDE);
     float2 v[P];
 #pragma unroll
     for (int u = 0; u < P; ++u) {
@@ -588,10 +609,10 @@ row_bulk_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
         if (active) {
             if constexpr (sizeof(In) == 2) {
                 a = (float)((int)fa[x] - (subtract_ref ? (int)ra[x] : 0));
-                b = (float)((int)fa[W + x] - (subtract_ref ? (int)ra[W + x] : 0));
+                b = (float)((int)fb[x] - (subtract_ref ? (int)rb[x] : 0));
             } else {
                 a = subtract_ref ? (float)fa[x] - (float)ra[x] : (float)fa[x];
-                b = subtract_ref ? (float)fa[W + x] - (float)ra[W + x] : (float)fa[W + x];
+                b = subtract_ref ? (float)fb[x] - (float)rb[x] : (float)fb[x];
             }
         }
         v[u] = make_float2(a, b);
@@ -629,6 +650,9 @@ cudaError_t launch_rows_bulk_t(const ddm_plan_s* p, const void* frames, float2* 
     using C = RowBulkShape<W, In>;
     auto k = row_bulk_kernel<W, In>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     dim3 grid((p->d.H / 2 + C::PAIRS - 1) / C::PAIRS, p->d.N);
     k<<<grid, C::NT, C::BYTES, s>>>((const In*)frames, spec, p->d.H, (size_t)p->n_q, p->d.subtract_ref,
