@@ -503,7 +503,7 @@ def run_ours(args):
                           "frac": STEP_BYTES / ((sp_ms + tm_ms) / 1e3) / 1e9 / peak,
                           "spatial_gbs": sp_achieved, "spatial_frac": sp_achieved / peak},
         "max_rel_err": max_err,
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 7 * args.steps,
         "clocks": clocks,
     }
     out["precision_tiers"] = tiers

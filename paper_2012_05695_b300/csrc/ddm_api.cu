@@ -23,6 +23,8 @@ namespace {
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+constexpr int kRadialChunk = 64;   // wave vectors per radial partial sum
+
 constexpr int kMaxSide = 1024;
 constexpr int kMaxFrames = 1024;
 
@@ -68,6 +70,9 @@ void free_plan(ddm_plan_s* p) {
     cudaFree(p->bin_start);
     cudaFree(p->bin_q);
     cudaFree(p->bin_count);
+    cudaFree(p->chunk_start);
+    cudaFree(p->bin_chunk);
+    cudaFree(p->radial_part);
     cudaFree(p->lag_j);
     cudaFree(p->lag_f);
     cudaFree(p->lag_ll);
@@ -241,11 +246,31 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
         }
         for (int b = 0; b < nb; ++b) start[b + 1] += start[b];
         std::vector<int> items((size_t)start[nb] > 0 ? (size_t)start[nb] : 1), fill(start.begin(), start.end() - 1);
-        for (int64_t q = 0; q < p->n_q; ++q)
-            if (bin_of[q] >= 0) items[fill[bin_of[q]]++] = (int)q;
+        for (int64_t q = 0; q < p->n_q; ++q) {
+            if (bin_of[q] < 0) continue;
+            const int kx = (int)(q % (Wh + 1));
+            items[fill[bin_of[q]]++] = (int)(q << 1) | ((kx == 0 || kx == Wh) ? 0 : 1);
+        }
+        // chunks of <= kRadialChunk entries, never crossing a bin
+        std::vector<int> cstart, bchunk(nb + 1, 0);
+        for (int b = 0; b < nb; ++b) {
+            bchunk[b] = (int)cstart.size();
+            for (int e = start[b]; e < start[b + 1]; e += kRadialChunk) cstart.push_back(e);
+        }
+        bchunk[nb] = (int)cstart.size();
+        cstart.push_back(start[nb]);
+        p->n_chunks = bchunk[nb];
         st = upload(&p->bin_start, start);
         if (st == DDM_OK) st = upload(&p->bin_q, items);
         if (st == DDM_OK) st = upload(&p->bin_count, count);
+        if (st == DDM_OK) st = upload(&p->chunk_start, cstart);
+        if (st == DDM_OK) st = upload(&p->bin_chunk, bchunk);
+        if (st == DDM_OK && p->n_chunks > 0) {
+            if (cudaMalloc(&p->radial_part, sizeof(float) * (size_t)p->n_chunks * desc->N) != cudaSuccess) {
+                cudaGetLastError();
+                st = DDM_ERR_OOM;
+            }
+        }
     }
     if (st == DDM_OK) st = make_fit_tables(p);
     if (st == DDM_OK) {

@@ -23,9 +23,13 @@ struct ddm_plan_s {
     float2* tw2;        // exp(-i pi t / L), t < L
     float* inv;         // 1 / (N - m), m < N; 0 at m = 0
     int* bin_start;     // [n_bins + 1] CSR offsets into bin_q
-    int* bin_q;         // public q indices grouped by bin, ascending inside a bin
+    int* bin_q;         // per bin, ascending: (public q << 1) | (q stands for itself and -q)
     int* bin_count;     // [n_bins] full-plane modes per bin
     int max_bin_items;
+    int n_chunks;       // radial partial sums: runs of <= 64 consecutive entries of one bin
+    int* chunk_start;   // [n_chunks + 1] offsets into bin_q
+    int* bin_chunk;     // [n_bins + 1] CSR offsets into the chunks
+    float* radial_part; // [n_chunks][N] partial sums
     int* lag_j;         // fit: integer part of the 64 log lags
     float* lag_f;       // fit: fractional part
     float* lag_ll;      // fit: ln(lag)
