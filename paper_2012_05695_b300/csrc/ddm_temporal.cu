@@ -25,8 +25,9 @@
 //    tensor copies, the group's threads synchronise on a named barrier of their own, so the
 //    groups drift apart and one group's copy wait hides behind the others' transforms.  The next tile's copy is issued
 //    before the D rows are staged, and the D rows leave shared memory by bulk async copies.
-//    Each tile is copied three times (the odd-bin, even-bin and power-sum passes each need
-//    g and there is no room to keep it): once from DRAM, twice from L2.
+//    The tile is copied twice at L = 1024 (once from DRAM, once from L2 for the power
+//    sums: the odd-bin transform exchanges through the spare buffer, in halves, so the tile
+//    survives for the even-bin one) and three times at L = 512.
 //  * L <= 256: one group per CTA, each thread loads its own samples (every warp load
 //    instruction covers whole 128-byte row segments F[t][q0 .. q0+QT) of the [t][q]
 //    spectrum).
@@ -161,7 +162,10 @@ struct GShape {
     //   red: row totals of the prefix sums; the mean's warp partials
     //   fix: warp partials of the FP64-fixup lags
     static constexpr size_t G_XS = (size_t)(L + L / T) * QG * sizeof(float2);
-    static constexpr size_t G_AB = cmax((size_t)L * QG * sizeof(float), (size_t)QG * DS * sizeof(float));
+    // (at T == P the odd-bin transform exchanges through ab, in halves: (L + L/T) * QG floats)
+    static constexpr bool SPLIT = (T == P);
+    static constexpr size_t G_AB = cmax(cmax((size_t)L * QG * sizeof(float), (size_t)QG * DS * sizeof(float)),
+                                        SPLIT ? (size_t)(L + L / T) * QG * sizeof(float) : 0);
     static constexpr size_t G_RED = (size_t)P * QG * sizeof(float);
     static constexpr size_t G_FIX = (size_t)FIX_MAX * NWG * QG * sizeof(float);
     static constexpr size_t OFF_TW = 0;
@@ -276,6 +280,8 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
         }
         if (lane < QG) red2[wg * QG + ql] = part;
+        // the previous tile's D copies must have left ab before it is written again
+        if (tg < QG) bulk_wait_read_all();
         sync();
         float2 mean = make_float2(0.f, 0.f);
 #pragma unroll
@@ -287,8 +293,6 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
 #pragma unroll
         for (int u = 0; u < P; ++u)
             if (i + T * u < N) v[u] = csub(v[u], mean);
-        // the previous tile's D copies must have left ab before it is written again
-        if (tg < QG) bulk_wait_read_all();
 
         // ---- odd bins: L-point DFT of g(t) e^{-i pi t / L}; |.|^2 parked in ab
 #pragma unroll
@@ -296,13 +300,19 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             v[u] = cmul(v[u], tw2[i + T * u]);
             if ((u & 7) == 7) hoist_fence();
         }
-        fft_cyclic<L, false>(v, i, xs, xaddr, tw, sync);
+        if constexpr (C::SPLIT) {
+            fft_cyclic_split<L, false>(v, i, ab, xaddr, tw, sync);   // the tile stays in xs
+        } else {
+            fft_cyclic<L, false>(v, i, xs, xaddr, tw, sync);
+        }
 #pragma unroll
         for (int u = 0; u < P; ++u) ab[(i + T * u) * QG + ql] = cabs2(v[u]);
 
-        // ---- even bins: L-point DFT of g (the tile again, from L2)
-        issue(gt);
-        if (!wait()) { timed_out = true; break; }
+        // ---- even bins: L-point DFT of g (still in xs at T == P; else the tile again, from L2)
+        if constexpr (!C::SPLIT) {
+            issue(gt);
+            if (!wait()) { timed_out = true; break; }
+        }
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             const int t = i + T * u;
