@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fit-compare", action="store_true")
+    ap.add_argument("--kmax", type=int, default=63,
+                    help="also time the low-frequency restriction |ky'|, kx <= kmax (0 = skip)")
     ap.add_argument("--shape", default=None,
                     help="HxWxN of a smaller blob stack for profiling captures (default 512x512x1024)")
     args = ap.parse_args()
@@ -448,6 +450,33 @@ def run_ours(args):
         torch.cuda.synchronize()
         tiers["fp32_fp64fix"] = {"temporal_ms": f0.elapsed_time(f1) / 10, "fix_lags": 8}
 
+    # ---- the low-frequency restriction (Sec. 3) on the same stack: cropped spectrum store
+    low_q = None
+    if rank == 0 and args.kmax > 0 and args.kmax < min(H, W) // 2:
+        lp = ddm.Plan(H, W, N_FRAMES, dtype="u16", n_bins=N_BINS, kmax=args.kmax)
+        spec_c = torch.empty(2 * N_FRAMES * lp.n_q, dtype=torch.float32, device=dev)
+        D_c = torch.empty(lp.n_q * N_FRAMES, dtype=torch.float32, device=dev)
+        lev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(10)]
+        for k in range(13):
+            e = lev[k - 3] if k >= 3 else None
+            if e:
+                e[0].record(stream)
+            lp.spatial_fft(frames, spec_c, stream)
+            if e:
+                e[1].record(stream)
+            lp.temporal_sf(spec_c, D_c, stream)
+            if e:
+                e[2].record(stream)
+            lp.azimuthal_average(D_c, Dr, counts, stream)
+            if e:
+                e[3].record(stream)
+        torch.cuda.synchronize()
+        ls = [sum(e[j].elapsed_time(e[j + 1]) for e in lev) / 10 for j in range(3)]
+        low_q = {"kmax": args.kmax, "n_q": lp.n_q, "kept_fraction": lp.n_q / N_Q,
+                 "stages_ms": {"spatial_fft": ls[0], "temporal_sf": ls[1], "azimuthal_average": ls[2]},
+                 "frames_per_s": N_FRAMES / (sum(ls) / 1e3)}
+        del spec_c, D_c, lp
+
     # ---- fit of the 362 radial curves: plain LM vs LM seeded by the trained MLP
     fit_cmp = None
     if rank == 0 and not args.no_fit_compare:
@@ -520,6 +549,8 @@ def run_ours(args):
         "clocks": clocks,
     }
     out["precision_tiers"] = tiers
+    if low_q:
+        out["low_q"] = low_q
     if fit_cmp:
         out["fit"] = fit_cmp
     if e2e:

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define DDM_ABI_VERSION 2
+#define DDM_ABI_VERSION 3
 
 typedef enum ddm_status {
     DDM_OK = 0,
@@ -94,12 +94,23 @@ typedef struct ddm_plan_desc {
                           q_begin must be a multiple of 64, q_begin < q_end <= n_q;
                           DDM_ERR_INVALID_ARG otherwise */
     int64_t q_end;
+    int kmax;          /* low-frequency restriction (Sec. 3): 0 = every wave vector; else only
+                          wave vectors with |ky'| <= kmax and 0 <= kx <= kmax (ky' the signed
+                          row frequency) are kept, in a cropped spectrum store
+                          [N][n_q], n_q = (2 kmax + 1)(kmax + 1), stored order
+                          ky' = 0..kmax, -kmax..-1 (outer) by kx = 0..kmax (inner); D rows
+                          follow the same order.  kmax must be odd and below H/2 and W/2
+                          (DDM_ERR_INVALID_ARG otherwise).  The plan then also owns an
+                          intermediate of N * H * (kmax + 1) complex64 for step one */
 } ddm_plan_desc;
 
 typedef struct ddm_plan_s* ddm_plan;
 
 /* Library version of this header's ABI. */
 int ddm_abi_version(void);
+
+/* sizeof(ddm_plan_desc) in this build: a binding checks its mirror of the struct against it. */
+size_t ddm_plan_desc_size(void);
 
 /* Static, never NULL. */
 const char* ddm_status_string(ddm_status s);
@@ -127,7 +138,8 @@ ddm_status ddm_plan_workspace_size(ddm_plan p, size_t* bytes);
  * ownership and must keep it alive while work is enqueued. */
 ddm_status ddm_plan_set_workspace(ddm_plan p, void* dev_ptr, size_t bytes);
 
-/* n_q = H * (W/2 + 1), the number of stored wave vectors. */
+/* n_q = H * (W/2 + 1), the number of stored wave vectors ((2 kmax + 1)(kmax + 1) for a
+ * plan with the low-frequency restriction). */
 ddm_status ddm_plan_n_q(ddm_plan p, int64_t* n_q);
 
 /* Kernel-detected status of the last completed calls on this plan (DDM_OK,

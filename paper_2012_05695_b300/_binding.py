@@ -58,6 +58,7 @@ class ddm_plan_desc(ctypes.Structure):
         ("max_workspace_bytes", ctypes.c_size_t),
         ("spatial_path", ctypes.c_int),
         ("q_begin", ctypes.c_int64), ("q_end", ctypes.c_int64),
+        ("kmax", ctypes.c_int),
     ]
 
 
@@ -75,6 +76,7 @@ def lib():
     vp, c_int, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
     sigs = {
         "ddm_abi_version": (c_int, []),
+        "ddm_plan_desc_size": (ctypes.c_size_t, []),
         "ddm_status_string": (ctypes.c_char_p, [st]),
         "ddm_plan_desc_init": (st, [ctypes.POINTER(ddm_plan_desc), c_int, c_int, c_int]),
         "ddm_plan_create": (st, [ctypes.POINTER(vp), ctypes.POINTER(ddm_plan_desc)]),
@@ -103,6 +105,8 @@ def lib():
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
+    if L.ddm_plan_desc_size() != ctypes.sizeof(ddm_plan_desc):
+        raise RuntimeError("ddm_plan_desc layout of the binding does not match the library")
     _lib = L
     return L
 
@@ -164,7 +168,7 @@ class Plan:
     def __init__(self, H: int, W: int, N: int, dtype: str = "u16", n_bins: int = 0,
                  precision: int = DDM_PREC_FP32, subtract_ref: int = 1, M: int = 0,
                  fix_lags: int = 0, max_workspace_bytes: int = 0, spatial_path: int = 0,
-                 q_begin: int = 0, q_end: int = 0):
+                 q_begin: int = 0, q_end: int = 0, kmax: int = 0):
         L = lib()
         d = ddm_plan_desc()
         _check(L.ddm_plan_desc_init(ctypes.byref(d), H, W, N), "ddm_plan_desc_init")
@@ -178,8 +182,10 @@ class Plan:
         d.spatial_path = spatial_path
         d.q_begin = q_begin
         d.q_end = q_end
+        d.kmax = kmax
         self.desc = d
         self.H, self.W, self.N, self.n_bins = H, W, N, n_bins
+        self.kmax = kmax
         self.dtype = dtype
         h = ctypes.c_void_p()
         _check(L.ddm_plan_create(ctypes.byref(h), ctypes.byref(d)), "ddm_plan_create")
@@ -191,6 +197,19 @@ class Plan:
     @property
     def handle(self):
         return self._h
+
+    def wave_vectors(self):
+        """(ky, kx) of every D row, ky in 0..H-1 (numpy int arrays of length n_q)."""
+        import numpy as np
+        if self.kmax > 0:
+            k = self.kmax
+            r = np.arange(2 * k + 1)
+            kys = np.where(r <= k, r, r - (2 * k + 1)) % self.H
+            ky = np.repeat(kys, k + 1)
+            kx = np.tile(np.arange(k + 1), 2 * k + 1)
+            return ky, kx
+        q = np.arange(self.n_q)
+        return q // (self.W // 2 + 1), q % (self.W // 2 + 1)
 
     def _frames(self, frames):
         import torch

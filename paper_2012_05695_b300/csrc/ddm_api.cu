@@ -73,6 +73,7 @@ void free_plan(ddm_plan_s* p) {
     cudaFree(p->chunk_start);
     cudaFree(p->bin_chunk);
     cudaFree(p->radial_part);
+    cudaFree(p->crop_inter);
     cudaFree(p->lag_j);
     cudaFree(p->lag_f);
     cudaFree(p->lag_ll);
@@ -91,8 +92,13 @@ std::vector<float2> pass_twiddles(int L) {
     return t;
 }
 
+size_t stored_wave_vectors(const ddm_plan_desc& d) {
+    if (d.kmax > 0) return (size_t)(2 * d.kmax + 1) * (size_t)(d.kmax + 1);
+    return (size_t)d.H * (size_t)(d.W / 2 + 1);
+}
+
 size_t workspace_bytes(const ddm_plan_desc& d) {
-    const size_t nq = (size_t)d.H * (size_t)(d.W / 2 + 1);
+    const size_t nq = stored_wave_vectors(d);
     const size_t b = nq * (size_t)d.N * sizeof(float2);
     return (b + 255) & ~(size_t)255;
 }
@@ -122,8 +128,11 @@ ddm_status validate(const ddm_plan_desc* d) {
         if ((int64_t)d->M < 2 * (int64_t)d->N - 1) return DDM_ERR_INVALID_ARG;
         if (d->M != 2 * L) return DDM_ERR_UNSUPPORTED;
     }
+    if (d->kmax < 0) return DDM_ERR_INVALID_ARG;
+    if (d->kmax > 0 && (d->kmax % 2 == 0 || d->kmax >= d->H / 2 || d->kmax >= d->W / 2))
+        return DDM_ERR_INVALID_ARG;
     if (d->q_begin != 0 || d->q_end != 0) {
-        const int64_t nq = (int64_t)d->H * (d->W / 2 + 1);
+        const int64_t nq = (int64_t)stored_wave_vectors(*d);
         if (d->q_begin < 0 || d->q_begin % 64 != 0 || d->q_end <= d->q_begin || d->q_end > nq)
             return DDM_ERR_INVALID_ARG;
     }
@@ -155,6 +164,8 @@ using namespace ddm;
 extern "C" {
 
 int ddm_abi_version(void) { return DDM_ABI_VERSION; }
+
+size_t ddm_plan_desc_size(void) { return sizeof(ddm_plan_desc); }
 
 const char* ddm_status_string(ddm_status s) {
     switch (s) {
@@ -198,7 +209,8 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
     p->device = dev;
     p->L = 1 << ilog2(desc->N);
     p->Wh = desc->W / 2;
-    p->n_q = (int64_t)desc->H * (p->Wh + 1);
+    p->kc = desc->kmax;
+    p->n_q = (int64_t)stored_wave_vectors(*desc);
     const bool ranged = desc->q_begin != 0 || desc->q_end != 0;
     p->q0 = ranged ? desc->q_begin : 0;
     p->q1 = ranged ? desc->q_end : p->n_q;
@@ -231,16 +243,22 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
     // wave vectors of the plan's range
     if (st == DDM_OK && desc->n_bins > 0) {
         const int H = desc->H, W = desc->W, Wh = p->Wh, nb = desc->n_bins;
+        // D row of (ky, kx) and its stored index: the full half plane (D row ky*(Wh+1)+kx;
+        // stored main block then the kx = W/2 column) or the cropped window (both in the
+        // window's order)
         std::vector<int> bin_of((size_t)p->n_q, -1);
         std::vector<int> count(nb, 0), start(nb + 1, 0);
-        for (int ky = 0; ky < H; ++ky) {
-            const int ys = ky > H / 2 ? ky - H : ky;
-            for (int kx = 0; kx <= Wh; ++kx) {
-                const int64_t stored = kx < Wh ? (int64_t)ky * Wh + kx : (int64_t)H * Wh + ky;
+        const int KC = p->kc;
+        const int rows = KC > 0 ? 2 * KC + 1 : H, cols = KC > 0 ? KC + 1 : Wh + 1;
+        for (int r = 0; r < rows; ++r) {
+            const int ys = KC > 0 ? (r <= KC ? r : r - (2 * KC + 1)) : (r > H / 2 ? r - H : r);
+            for (int kx = 0; kx < cols; ++kx) {
+                const int64_t stored = KC > 0 ? (int64_t)r * cols + kx
+                                              : (kx < Wh ? (int64_t)r * Wh + kx : (int64_t)H * Wh + r);
                 if (stored < p->q0 || stored >= p->q1) continue;
                 const int b = radial_bin(ys, kx, H, W, nb);
-                bin_of[(size_t)ky * (Wh + 1) + kx] = b;
-                count[b] += (kx == 0 || kx == Wh) ? 1 : 2;
+                bin_of[(size_t)r * cols + kx] = b;
+                count[b] += (kx == 0 || (KC == 0 && kx == Wh)) ? 1 : 2;
                 start[b + 1] += 1;
             }
         }
@@ -248,8 +266,9 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
         std::vector<int> items((size_t)start[nb] > 0 ? (size_t)start[nb] : 1), fill(start.begin(), start.end() - 1);
         for (int64_t q = 0; q < p->n_q; ++q) {
             if (bin_of[q] < 0) continue;
-            const int kx = (int)(q % (Wh + 1));
-            items[fill[bin_of[q]]++] = (int)(q << 1) | ((kx == 0 || kx == Wh) ? 0 : 1);
+            const int kx = (int)(q % cols);
+            const bool single = kx == 0 || (KC == 0 && kx == Wh);
+            items[fill[bin_of[q]]++] = (int)(q << 1) | (single ? 0 : 1);
         }
         // chunks of <= kRadialChunk entries, never crossing a bin
         std::vector<int> cstart, bchunk(nb + 1, 0);
@@ -270,6 +289,13 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
                 cudaGetLastError();
                 st = DDM_ERR_OOM;
             }
+        }
+    }
+    if (st == DDM_OK && p->kc > 0) {
+        const size_t bytes = sizeof(float2) * (size_t)desc->N * desc->H * (size_t)(p->kc + 1);
+        if (cudaMalloc(&p->crop_inter, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            st = DDM_ERR_OOM;
         }
     }
     if (st == DDM_OK) st = make_fit_tables(p);

@@ -12,6 +12,8 @@ struct ddm_plan_s {
     int Wh;             // W / 2
     int64_t n_q;        // H * (W/2 + 1)
     int64_t q0, q1;     // stored wave vectors covered by step two and the radial stage
+    int kc;             // low-frequency restriction: kmax (0 = full half plane)
+    float2* crop_inter; // kc > 0: row-pass output [N][H][kc + 1]
     int device;
     int n_sm;
     int kd;             // number of trailing lags evaluated by direct differences

@@ -161,6 +161,76 @@ col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
     }
 }
 
+// Low-frequency restriction (Sec. 3): H-point FFTs down the columns kx = 0..kc of the
+// row-pass output [N][H][kc + 1]; only ky' = 0..kc and -kc..-1 are kept, written to the
+// cropped spectrum [N][(2 kc + 1)(kc + 1)] (rows in that ky' order, kx inner).
+// grid: (ceil((kc + 1) / QC), N); block: QC * T threads.
+template <int H, int QC>
+__global__ void __launch_bounds__(QC * FftShape<H>::T)
+col_crop_kernel(const float2* __restrict__ inter, float2* __restrict__ spec, int kc,
+                const float2* __restrict__ tw_g) {
+    using S = FftShape<H>;
+    constexpr int P = S::P, T = S::T, NT = QC * T;
+    extern __shared__ float2 smem[];
+    float2* tw = smem;                                   // H entries (T > 1)
+    float2* xs = smem + (T > 1 ? H : 0);                 // H * QC
+
+    const int tid = threadIdx.x;
+    if constexpr (T > 1) {
+        for (int k = tid; k < H; k += NT) tw[k] = tw_g[k];
+    }
+    const int ql = tid % QC;
+    const int i = tid / QC;
+    const int cols = kc + 1;
+    const int kx = blockIdx.x * QC + ql;
+    const bool valid = kx <= kc;
+    const int t = blockIdx.y;
+    const float2* src = inter + (size_t)t * H * cols + (valid ? kx : 0);
+    float2 v[P];
+#pragma unroll
+    for (int u = 0; u < P; ++u)
+        v[u] = valid ? __ldg(src + (size_t)(i + T * u) * cols) : make_float2(0.f, 0.f);
+    __syncthreads();
+    AddrInterleaved<QC> addr{ql};
+    fft_cyclic<H, false>(v, i, xs, addr, tw, SyncBlock{});
+    if (!valid) return;                                  // after the transform's last barrier
+    float2* dst = spec + (size_t)t * (size_t)(2 * kc + 1) * cols + kx;
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+        const int ky = i + T * u;
+        const int r = ky <= kc ? ky : (ky >= H - kc ? ky - H + 2 * kc + 1 : -1);
+        if (r >= 0) dst[(size_t)r * cols] = v[u];
+    }
+}
+
+template <int H>
+cudaError_t launch_cols_crop(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
+    using S = FftShape<H>;
+    constexpr int QC = 16;
+    const int kc = p->kc;
+    dim3 grid((kc + 1 + QC - 1) / QC, p->d.N);
+    const size_t smem = sizeof(float2) * ((S::T > 1 ? H : 0) + (size_t)H * QC);
+    auto k = col_crop_kernel<H, QC>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, QC * S::T, smem, s>>>(p->crop_inter, spec, kc, p->tw_col);
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_cols_crop(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
+    switch (p->d.H) {
+        case 4: return launch_cols_crop<4>(p, spec, s);
+        case 8: return launch_cols_crop<8>(p, spec, s);
+        case 16: return launch_cols_crop<16>(p, spec, s);
+        case 32: return launch_cols_crop<32>(p, spec, s);
+        case 64: return launch_cols_crop<64>(p, spec, s);
+        case 128: return launch_cols_crop<128>(p, spec, s);
+        case 256: return launch_cols_crop<256>(p, spec, s);
+        case 512: return launch_cols_crop<512>(p, spec, s);
+        case 1024: return launch_cols_crop<1024>(p, spec, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int W, typename In>
 cudaError_t launch_rows(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
     using S = FftShape<W>;
@@ -242,6 +312,13 @@ cudaError_t launch_rows_bulk(const ddm_plan_s* p, const void* frames, float2* sp
 // Path: DDM_SPATIAL_FUSED (cluster kernel) where supported and asked for; otherwise the
 // row pass (bulk-staged where rows allow it) followed by the column pass.
 ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+    if (p->kc > 0) {
+        // low-frequency restriction: bulk-staged row pass into the intermediate, then the
+        // cropping column pass
+        if (!rows_bulk_supported(p, frames)) return DDM_ERR_UNSUPPORTED;
+        if (launch_rows_bulk(p, frames, spec, s) != cudaSuccess) return DDM_ERR_CUDA;
+        return dispatch_cols_crop(p, spec, s) == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
+    }
     if (p->d.spatial_path == DDM_SPATIAL_FUSED && fused_spatial_supported(p) &&
         (reinterpret_cast<uintptr_t>(frames) & 15) == 0)
         return launch_spatial_fused(p, frames, spec, s);
@@ -540,7 +617,7 @@ struct RowBulkShape {
 template <int W, typename In>
 __global__ void __launch_bounds__(RowBulkShape<W, In>::NT, 3)
 row_bulk_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H, size_t frame_stride,
-                int subtract_ref, const float2* __restrict__ tw_g, unsigned* status) {
+                int subtract_ref, const float2* __restrict__ tw_g, unsigned* status, int kc) {
     using C = RowBulkShape<W, In>;
     constexpr int T = C::T, P = C::P, PAIRS = C::PAIRS, NT = C::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -624,17 +701,20 @@ row_bulk_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
     for (int u = 0; u < P; ++u) X[addr(i + T * u)] = v[u];
     __syncthreads();
     if (active) {
-        float2* outa = spec + (size_t)t * frame_stride + (size_t)(2 * (pair0 + j)) * (W / 2);
-        float2* outb = outa + W / 2;
+        // kc > 0 (low-frequency restriction): rows of kx = 0..kc, no Nyquist packing
+        const int rowlen = kc > 0 ? kc + 1 : W / 2;
+        float2* outa = spec + (size_t)t * frame_stride + (size_t)(2 * (pair0 + j)) * rowlen;
+        float2* outb = outa + rowlen;
 #pragma unroll
         for (int u = 0; u < (P + 1) / 2; ++u) {
             const int k = i + T * u;
-            if (k >= W / 2) break;
+            if (k >= rowlen) break;
             const float2 z = X[addr(k)];
             if (k == 0) {
-                const float2 zn = X[addr(W / 2)];
-                outa[0] = make_float2(z.x, zn.x);
-                outb[0] = make_float2(z.y, zn.y);
+                const float nyq_a = kc > 0 ? 0.f : X[addr(W / 2)].x;
+                const float nyq_b = kc > 0 ? 0.f : X[addr(W / 2)].y;
+                outa[0] = make_float2(z.x, nyq_a);
+                outb[0] = make_float2(z.y, nyq_b);
             } else {
                 const float2 zr = X[addr(W - k)];
                 outa[k] = make_float2(0.5f * (z.x + zr.x), 0.5f * (z.y - zr.y));
@@ -655,8 +735,13 @@ cudaError_t launch_rows_bulk_t(const ddm_plan_s* p, const void* frames, float2* 
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     dim3 grid((p->d.H / 2 + C::PAIRS - 1) / C::PAIRS, p->d.N);
-    k<<<grid, C::NT, C::BYTES, s>>>((const In*)frames, spec, p->d.H, (size_t)p->n_q, p->d.subtract_ref,
-                                     p->tw_row, p->dev_status);
+    // full: the spectrum itself, frame stride n_q; low-frequency restriction: the plan's
+    // intermediate [N][H][kc + 1]
+    const bool crop = p->kc > 0;
+    float2* out = crop ? p->crop_inter : spec;
+    const size_t fstride = crop ? (size_t)p->d.H * (size_t)(p->kc + 1) : (size_t)p->n_q;
+    k<<<grid, C::NT, C::BYTES, s>>>((const In*)frames, out, p->d.H, fstride, p->d.subtract_ref,
+                                     p->tw_row, p->dev_status, p->kc);
     return cudaGetLastError();
 }
 

@@ -114,6 +114,7 @@ struct TArgs {
     int N;            // frames
     int kd;           // directly evaluated trailing lags (<= 32, < N)
     int H, Wh, lwh;   // for the storage -> public q map (lwh = log2 Wh)
+    int crop;         // low-frequency restriction: D rows in stored order
     int64_t n_q;      // stored wave vectors = spectrum frame stride
     int64_t q0, q1;   // stored wave vectors this launch covers: [q0, q1)
     int64_t n_tiles;  // tiles of [q0, q1) (of one group, L >= 512; of one CTA, L <= 256)
@@ -125,8 +126,10 @@ struct TArgs {
     unsigned* status;
 };
 
-// storage index -> public q = ky * (Wh + 1) + kx (Wh = W/2 is a power of two)
-__device__ __forceinline__ int public_q(int s, int H, int Wh, int lwh) {
+// storage index -> public q = ky * (Wh + 1) + kx (Wh = W/2 is a power of two); with the
+// low-frequency restriction (crop) the stored order is the D order
+__device__ __forceinline__ int public_q(int s, int H, int Wh, int lwh, int crop) {
+    if (crop) return s;
     const int main = H << lwh;
     if (s < main) return (s >> lwh) * (Wh + 1) + (s & (Wh - 1));
     return (s - main) * (Wh + 1) + Wh;
@@ -479,7 +482,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             if (tg < QG) {
                 const int64_t sr = q0 + gt * QG + tg;
                 if (sr < q1) {
-                    float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
+                    float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
                     bulk_store(drow, ab + tg * DS, (uint32_t)N * (uint32_t)sizeof(float));
                 }
                 bulk_commit();
@@ -489,7 +492,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             for (int r = 0; r < QG; ++r) {
                 const int64_t sr = q0 + gt * QG + r;
                 if (sr >= q1) break;
-                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
+                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
                 for (int m = tg; m < N; m += GT) drow[m] = ab[r * DS + m];
             }
         }
@@ -736,7 +739,7 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
         for (int r = 0; r < QT; ++r) {
             const int64_t sr = q0 + tile * QT + r;
             if (sr >= q1) break;
-            float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh) * N;
+            float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
             for (int m = tid; m < N; m += NT) {
                 const float d = xf[r * DS + m];
                 bad |= !isfinite(d);
@@ -787,6 +790,7 @@ void fill_args(TArgs& a, const ddm_plan_s* p, float* D, int qt) {
     a.H = p->d.H;
     a.Wh = p->Wh;
     a.lwh = ilog2(p->Wh);
+    a.crop = p->kc > 0;
     a.vec4 = (p->d.N % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
     a.fix = (p->d.precision == DDM_PREC_FP32_FP64FIX) ? p->fix_lags : 0;
     a.n_q = p->n_q;

@@ -12,7 +12,7 @@ from conftest import cuda_available
 
 def test_library_is_in_tree_and_loads():
     L = ddm.lib()
-    assert L.ddm_abi_version() == 2
+    assert L.ddm_abi_version() == 3
     assert ddm.LIB_PATH.endswith("paper_2012_05695_b300/_lib/libddm_b300.so")
 
 
@@ -66,6 +66,9 @@ def test_desc_init_defaults():
     ("q_begin", 32, B.DDM_ERR_INVALID_ARG),       # range start not a multiple of 64
     ("q_end", 41, B.DDM_ERR_INVALID_ARG),         # past n_q = 8 * 5 = 40
     ("q_begin", -64, B.DDM_ERR_INVALID_ARG),
+    ("kmax", 2, B.DDM_ERR_INVALID_ARG),           # the cropped window needs kmax odd
+    ("kmax", 5, B.DDM_ERR_INVALID_ARG),           # and below H/2 = W/2 = 4
+    ("kmax", -1, B.DDM_ERR_INVALID_ARG),
 ])
 def test_plan_create_validates_before_touching_the_device(field, value, status):
     d = _desc(8, 8, 4)
@@ -76,12 +79,12 @@ def test_plan_create_validates_before_touching_the_device(field, value, status):
 
 
 def test_plan_desc_layout_matches_the_header():
-    """The ctypes mirror of ddm_plan_desc has the C layout: q_begin/q_end are 8-byte
-    fields after spatial_path, and ddm_plan_desc_init zeroes them."""
+    """The ctypes mirror of ddm_plan_desc has the C layout (its size is the library's
+    sizeof), and ddm_plan_desc_init zeroes the optional fields."""
     d = _desc(16, 16, 8)
-    assert (d.q_begin, d.q_end) == (0, 0)
+    assert (d.q_begin, d.q_end, d.kmax) == (0, 0, 0)
+    assert ctypes.sizeof(B.ddm_plan_desc) == ddm.lib().ddm_plan_desc_size()
     assert B.ddm_plan_desc.q_begin.offset % 8 == 0
-    assert ctypes.sizeof(B.ddm_plan_desc) == B.ddm_plan_desc.q_end.offset + 8
     d.q_begin, d.q_end = 64, 32      # empty range
     h = ctypes.c_void_p(123)
     assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == B.DDM_ERR_INVALID_ARG
