@@ -26,7 +26,7 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 constexpr int kRadialChunk = 64;   // wave vectors per radial partial sum
 
 constexpr int kMaxSide = 1024;
-constexpr int kMaxFrames = 1024;
+constexpr int kMaxFrames = 4096;
 
 // floor(n_bins * |q| / (pi sqrt 2)) with |q| = 2 pi sqrt((ky/H)^2 + (kx/W)^2):
 // the largest b with (b H W)^2 <= 2 n_bins^2 (ky^2 W^2 + kx^2 H^2), in exact integers.
@@ -65,6 +65,7 @@ void free_plan(ddm_plan_s* p) {
     cudaFree(p->tw_row);
     cudaFree(p->tw_col);
     cudaFree(p->tw_t);
+    cudaFree(p->tw_tin);
     cudaFree(p->tw2);
     cudaFree(p->inv);
     cudaFree(p->bin_start);
@@ -227,6 +228,7 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
     if (st == DDM_OK) st = upload(&p->tw_row, pass_twiddles(desc->W));
     if (st == DDM_OK) st = upload(&p->tw_col, pass_twiddles(desc->H));
     if (st == DDM_OK) st = upload(&p->tw_t, pass_twiddles(p->L));
+    if (st == DDM_OK && p->L >= 2048) st = upload(&p->tw_tin, pass_twiddles(p->L / 32));
     // exp(-i pi t / L) and 1/(N - m)
     if (st == DDM_OK) {
         std::vector<float2> tw2(p->L);

@@ -348,4 +348,53 @@ __device__ __forceinline__ void fft_cyclic_split(float2 (&v)[FftShape<L>::P], in
     dft_reg<T, INV>(v);
 }
 
+// ------------------------------------------------------------------ three-pass FFT
+// L = P * T with T = P * R threads per transform (R <= P): lengths 2048 .. 32768 at P = 32.
+// Pass 1: P-point DFT over u inside each thread (data x[i + T u]), twiddle w_L^{i k1}; one
+// exchange hands each group of R threads one k1 (thread j plays (k1, r) = (j / R, j % R)
+// and holds i = r + R u); the inner T-point DFT over i is the two-pass fft_cyclic<T> run by
+// those R threads.  The result X[k1 + P k2], k2 = r + R u, sits in thread j at
+// X[sigma(j) + T u], sigma(j) = (j / R) + P (j % R): cyclic in the permuted index sigma(j),
+// which later stages (and an inverse transform called with i = sigma(j)) use as the
+// thread's logical index.
+__host__ __device__ constexpr int fft3_sigma(int j, int P, int R) { return j / R + P * (j % R); }
+
+// Exchange placement for the pass-1 -> inner handover: element (k1, i) of transform ql at
+// (k1 * (T + PAD) + i) * QT + ql; PAD makes the reads (four k1 per warp) use both halves of
+// the banks.  (P * (T + PAD) * QT elements.)
+template <int QT, int T, int PAD>
+struct AddrHandover {
+    int ql;
+    __device__ __forceinline__ int operator()(int k1, int i) const { return (k1 * (T + PAD) + i) * QT + ql; }
+};
+
+// xs holds max(P (T + PAD) QT, L QT) elements; QT transforms interleaved (transform ql).
+template <int L, bool INV, int QT, int PAD, typename Sync>
+__device__ __forceinline__ void fft_cyclic3(float2 (&v)[32], int i, int ql, float2* xs,
+                                            const float2* tw1, const float2* tw_in, Sync sync) {
+    constexpr int P = 32;
+    constexpr int T = L / P;
+    constexpr int R = T / P;
+    static_assert(T % P == 0 && R >= 2 && R <= P, "three-pass FFT: 2048 <= L <= 32768");
+    const AddrHandover<QT, T, PAD> hand{ql};
+    dft_reg<P, INV>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+        float2 a = v[k1];
+        if (k1 > 0) {
+            const float2 w = tw1[k1 * T + i];
+            a = INV ? cmul_conj(a, w) : cmul(a, w);
+        }
+        xs[hand(k1, i)] = a;
+        if ((k1 & 7) == 7) hoist_fence();
+    }
+    sync();
+    const int k1 = i / R, r = i % R;
+#pragma unroll
+    for (int u = 0; u < P; ++u) v[u] = xs[hand(k1, r + R * u)];
+    sync();                                   // handover read: the region takes the inner exchange
+    const AddrInterleaved<P * QT> inner{k1 * QT + ql};
+    fft_cyclic<T, INV>(v, r, xs, inner, tw_in, sync);
+}
+
 }  // namespace ddm

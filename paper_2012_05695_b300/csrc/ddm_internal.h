@@ -22,6 +22,7 @@ struct ddm_plan_s {
     float2* tw_row;     // pass twiddles of the W-point row transform
     float2* tw_col;     // pass twiddles of the H-point column transform
     float2* tw_t;       // pass twiddles of the L-point time transform
+    float2* tw_tin;     // L >= 2048: pass twiddles of the inner L/32-point transform
     float2* tw2;        // exp(-i pi t / L), t < L
     float* inv;         // 1 / (N - m), m < N; 0 at m = 0
     int* bin_start;     // [n_bins + 1] CSR offsets into bin_q

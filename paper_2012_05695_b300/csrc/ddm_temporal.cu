@@ -508,6 +508,255 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
 }
 
 // =====================================================================================
+// L = 2048, 4096 (N up to 4096): one 256-thread CTA per SM, three-pass transforms
+// =====================================================================================
+// A CTA owns QG = 256 / T wave vectors at a time (T = L / 32 threads each, 32 samples per
+// thread).  Tiles arrive by TMA as above; the three transforms are fft_cyclic3 (32-point
+// register DFT, handover exchange, inner two-pass T-point transform), whose output order
+// is the permuted thread index sigma(i); the inverse runs with i = sigma(i) and leaves
+// lag m = sigma(sigma(i)) + T u in thread i.  Prefix sums: thread i owns the chunk of 32
+// consecutive frames starting at 32 i.
+template <int LOG2L>
+struct LShape {
+    static constexpr int L = 1 << LOG2L;
+    static constexpr int P = 32, T = L / P, R = T / P;
+    static constexpr int NT = 256;
+    static constexpr int QG = NT / T;             // wave vectors per tile
+    static constexpr int IW = 32 / QG;            // threads of one wave vector per warp
+    static constexpr int NWG = NT / 32;
+    static constexpr int KD = 32;
+    static constexpr int PAD = (QG == 2) ? 4 : 2; // (T + PAD) * QG = 8 mod 16: handover reads spread
+    static constexpr int DS = L + 4;              // D staging row stride (floats)
+    static constexpr int BOX_T = 256, NBOX = L / BOX_T;
+    static constexpr size_t XS_ELEMS = (size_t)P * (T + PAD) * QG > (size_t)L * QG
+                                           ? (size_t)P * (T + PAD) * QG : (size_t)L * QG;
+    static constexpr size_t OFF_TW1 = 0;
+    static constexpr size_t OFF_TWI = OFF_TW1 + (size_t)L * sizeof(float2);
+    static constexpr size_t OFF_TW2 = OFF_TWI + (size_t)T * sizeof(float2);
+    static constexpr size_t OFF_INV = OFF_TW2 + (size_t)L * sizeof(float2);
+    static constexpr size_t OFF_XS = (OFF_INV + (size_t)L * sizeof(float) + 1023) & ~size_t(1023);
+    static constexpr size_t OFF_AB = OFF_XS + XS_ELEMS * sizeof(float2);
+    static constexpr size_t OFF_RED = OFF_AB + cmax((size_t)L * QG, (size_t)QG * DS) * sizeof(float);
+    static constexpr size_t BYTES = OFF_RED + (size_t)T * QG * sizeof(float);
+    static_assert(T % P == 0 && QG * T == NT && QG >= 2, "long kernel: L = 2048 or 4096");
+    static_assert(BYTES + 1024 <= 232448, "temporal kernel shared memory exceeds 227 KB");
+    static_assert((size_t)(L + L / P) * QG <= 2 * XS_ELEMS, "padded prefix chunks must fit");
+    static_assert((size_t)NWG * QG * 2 <= (size_t)T * QG, "mean partials must fit");
+};
+
+template <int LOG2L>
+__global__ void __launch_bounds__(LShape<LOG2L>::NT, 1)
+temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUtensorMap tmap,
+                        const float2* __restrict__ tw_in_g) {
+    using C = LShape<LOG2L>;
+    constexpr int L = C::L, P = C::P, T = C::T, R = C::R, QG = C::QG, NT = C::NT, NWG = C::NWG;
+    constexpr int DS = C::DS, PAD = C::PAD;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint64_t tile_bar;
+    float2* tw1 = reinterpret_cast<float2*>(smem_raw + C::OFF_TW1);
+    float2* twi = reinterpret_cast<float2*>(smem_raw + C::OFF_TWI);
+    float2* tw2 = reinterpret_cast<float2*>(smem_raw + C::OFF_TW2);
+    float* inv = reinterpret_cast<float*>(smem_raw + C::OFF_INV);
+    float2* xs = reinterpret_cast<float2*>(smem_raw + C::OFF_XS);
+    float* xf = reinterpret_cast<float*>(xs);
+    float* ab = reinterpret_cast<float*>(smem_raw + C::OFF_AB);
+    float* red = reinterpret_cast<float*>(smem_raw + C::OFF_RED);
+    float2* red2 = reinterpret_cast<float2*>(red);
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&tile_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int k = tid; k < L; k += NT) {
+        tw1[k] = a.tw[k];
+        tw2[k] = a.tw2[k];
+        inv[k] = a.inv[k];
+    }
+    for (int k = tid; k < T; k += NT) twi[k] = tw_in_g[k];
+    __syncthreads();
+
+    const int ql = tid % QG, i = tid / QG;
+    const int lane = tid & 31, wg = tid >> 5;
+    const int s1 = fft3_sigma(i, P, R);          // forward output order
+    const int s2 = fft3_sigma(s1, P, R);         // inverse output order (input order s1)
+    const int N = a.N, kd = a.kd;
+    const int64_t q0 = a.q0, q1 = a.q1;
+    bool timed_out = false;
+    float chk = 0.f;
+    uint32_t phase = 0;
+    auto load = [&](int64_t t) -> bool {
+        if (tid == 0) {
+            fence_proxy_async();
+            mbar_expect_tx(&tile_bar, (uint32_t)(C::NBOX * C::BOX_T * QG * sizeof(float2)));
+#pragma unroll
+            for (int b = 0; b < C::NBOX; ++b)
+                tma_load_2d(xs + b * C::BOX_T * QG, &tmap, (int)(2 * (q0 + t * QG)), b * C::BOX_T, &tile_bar);
+        }
+        const bool ok = mbar_wait_bounded(&tile_bar, phase);
+        if (__syncthreads_or(ok ? 0 : 1)) return false;
+        phase ^= 1u;
+        return true;
+    };
+    // this thread's trailing lag, if < N: the one it also holds in the combination's order
+    const int m_lo = N - kd;
+    const int m_tail = m_lo + ((s2 - m_lo) % T + T) % T;
+
+    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+        __syncthreads();                                   // the previous tile is done with smem
+        if (!load(tile)) { timed_out = true; break; }
+        // ---- time sequence (cyclic, thread i holds t = i + T u) and its mean
+        float2 v[P];
+        float2 part = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            v[u] = xs[(i + T * u) * QG + ql];
+            part = cadd(part, v[u]);
+        }
+#pragma unroll
+        for (int o = QG; o < 32; o <<= 1) {
+            part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
+            part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
+        }
+        if (lane < QG) red2[wg * QG + ql] = part;
+        __syncthreads();
+        float2 mean = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < NWG; ++w) mean = cadd(mean, red2[w * QG + ql]);
+        {
+            const float rn = 1.0f / (float)N;
+            mean = make_float2(mean.x * rn, mean.y * rn);
+        }
+        // ---- odd bins: DFT of g(t) e^{-i pi t / L}; |.|^2 parked in ab by frequency
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int t = i + T * u;
+            v[u] = (t < N) ? cmul(csub(v[u], mean), tw2[t]) : make_float2(0.f, 0.f);
+            if ((u & 7) == 7) hoist_fence();
+        }
+        fft_cyclic3<L, false, QG, PAD>(v, i, ql, xs, tw1, twi, SyncBlock{});
+#pragma unroll
+        for (int u = 0; u < P; ++u) ab[(s1 + T * u) * QG + ql] = cabs2(v[u]);
+        // ---- even bins: DFT of g (the tile again)
+        if (!load(tile)) { timed_out = true; break; }
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int t = i + T * u;
+            v[u] = (t < N) ? csub(xs[t * QG + ql], mean) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        fft_cyclic3<L, false, QG, PAD>(v, i, ql, xs, tw1, twi, SyncBlock{});
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            v[u] = make_float2(cabs2(v[u]), ab[(s1 + T * u) * QG + ql]);
+            if ((u & 7) == 7) hoist_fence();
+        }
+        // ---- inverse of Z = |X_even|^2 + i |X_odd|^2 (input order s1, output order s2)
+        fft_cyclic3<L, true, QG, PAD>(v, s1, ql, xs, tw1, twi, SyncBlock{});
+#pragma unroll
+        for (int u = 0; u < P; ++u) xs[(s2 + T * u) * QG + ql] = v[u];
+        __syncthreads();
+        {
+            const float scale = 0.25f / (float)L;
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+                const int m = s2 + T * u;
+                const float2 z = v[u];
+                const float2 zr = xs[((L - m) & (L - 1)) * QG + ql];
+                const float2 w = tw2[m];
+                ab[m * QG + ql] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
+                if ((u & 7) == 7) hoist_fence();
+            }
+        }
+        // ---- the tile a third time: |g - mean|^2 and the trailing lags (Eq. 1)
+        __syncthreads();                                   // partner reads done: xs is free
+        if (!load(tile)) { timed_out = true; break; }
+        float e[P];
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int t = i + T * u;
+            e[u] = (t < N) ? cabs2(csub(xs[t * QG + ql], mean)) : 0.f;
+        }
+        float tl = 0.f;
+        if (m_tail < N) {
+            for (int t = 0; t < N - m_tail; ++t)
+                tl += cabs2(csub(xs[(t + m_tail) * QG + ql], xs[t * QG + ql]));
+            tl *= inv[m_tail];
+            chk = fmaf(tl, 0.f, chk);
+        }
+        __syncthreads();                                   // tile read
+        // |g|^2 at padded positions t + t / 32 (chunk-wise reads below are conflict-free)
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int t = i + T * u;
+            xf[(t + (t >> 5)) * QG + ql] = e[u];
+        }
+        __syncthreads();
+        // ---- inclusive prefix sums: thread i owns frames 32 i .. 32 i + 31
+        float rowv[P];
+        {
+            float acc = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < P; ++jj) {
+                acc += xf[(i * (P + 1) + jj) * QG + ql];
+                rowv[jj] = acc;
+            }
+            red[i * QG + ql] = acc;
+        }
+        __syncthreads();
+        float total = 0.f, off = 0.f;
+        for (int c = 0; c < T; ++c) {
+            const float x = red[c * QG + ql];
+            if (c < i) off += x;
+            total += x;
+        }
+#pragma unroll
+        for (int jj = 0; jj < P; ++jj) xf[(i * (P + 1) + jj) * QG + ql] = rowv[jj] + off;
+        __syncthreads();
+        // ---- D(m) = (P1 + P2 - 2 Re C) / (N - m) for 0 < m < N - kd, m = s2 + T u
+        float dv[P];
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int m = s2 + T * u;
+            float d = 0.f;
+            if (m > 0 && m < N - kd) {
+                const int ta = N - 1 - m, tb = m - 1;
+                const float p1 = xf[(ta + (ta >> 5)) * QG + ql];
+                const float p2 = total - xf[(tb + (tb >> 5)) * QG + ql];
+                d = (p1 + p2 - 2.f * ab[m * QG + ql]) * inv[m];
+                chk = fmaf(d, 0.f, chk);
+            }
+            dv[u] = d;
+            if ((u & 7) == 7) hoist_fence();
+        }
+        __syncthreads();                                   // reads of S and Re C done
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int m = s2 + T * u;
+            if (m < N) ab[ql * DS + m] = dv[u];
+        }
+        if (m_tail < N) ab[ql * DS + m_tail] = tl;
+        __syncthreads();
+        for (int r = 0; r < QG; ++r) {
+            const int64_t sr = q0 + tile * QG + r;
+            if (sr >= q1) break;
+            float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
+            if (a.vec4) {
+                for (int m4 = tid; m4 < N / 4; m4 += NT)
+                    reinterpret_cast<float4*>(drow)[m4] = *reinterpret_cast<const float4*>(ab + r * DS + 4 * m4);
+            } else {
+                for (int m = tid; m < N; m += NT) drow[m] = ab[r * DS + m];
+            }
+        }
+    }
+    if (timed_out) {
+        if (tid == 0) atomicOr(a.status, 2u);
+        mbar_wait_bounded(&tile_bar, phase);
+    }
+    if (chk != chk) atomicOr(a.status, 1u);
+}
+
+// =====================================================================================
 // L <= 256: one group per CTA, per-thread loads
 // =====================================================================================
 template <int LOG2L>
@@ -823,6 +1072,24 @@ ddm_status launch_grouped(const ddm_plan_s* p, const float2* spec, float* D, cud
 }
 
 template <int LOG2L>
+ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
+    using C = LShape<LOG2L>;
+    if ((reinterpret_cast<uintptr_t>(spec) & 15) != 0 || !p->tw_tin) return DDM_ERR_INVALID_ARG;
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    if (!make_spectrum_map(&tmap, spec, p->n_q, p->d.N, C::QG)) return DDM_ERR_CUDA;
+    TArgs a;
+    fill_args(a, p, D, C::QG);
+    auto k = temporal_sf_long_kernel<LOG2L>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
+        cudaSuccess)
+        return DDM_ERR_CUDA;
+    const int64_t grid = a.n_tiles < p->n_sm ? a.n_tiles : p->n_sm;
+    k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(D, a, tmap, p->tw_tin);
+    return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
+}
+
+template <int LOG2L>
 ddm_status launch_small(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
     using C = TShape<LOG2L>;
     TArgs a;
@@ -855,6 +1122,8 @@ ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cu
         // rows, lockstep) 1.13 ms, 2 groups 1.05 ms, 4 groups (32-byte rows) 1.15 ms.
         case 9: return fix ? launch_grouped<9, true, 4>(p, spec, D, s) : launch_grouped<9, false, 4>(p, spec, D, s);
         case 10: return fix ? launch_grouped<10, true, 2>(p, spec, D, s) : launch_grouped<10, false, 2>(p, spec, D, s);
+        case 11: return launch_long<11>(p, spec, D, s);
+        case 12: return launch_long<12>(p, spec, D, s);
         default: return DDM_ERR_UNSUPPORTED;
     }
 }

@@ -82,7 +82,8 @@ def test_spatial_fft_without_reference_subtraction():
 
 
 # ------------------------------------------------------------------ step two alone
-@pytest.mark.parametrize("N", [1, 2, 3, 5, 17, 33, 64, 100, 128, 255, 256, 511, 1000, 1024])
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 17, 33, 64, 100, 128, 255, 256, 511, 1000, 1024,
+                               1025, 1500, 2048, 2049, 3000, 4096])
 def test_temporal_matches_oracle(N):
     """Oracle spectrum in, oracle D out: isolates the time-sequence stage."""
     import torch
@@ -104,6 +105,37 @@ def test_temporal_matches_oracle(N):
         return
     assert np.all(D[..., 0] == 0)
     assert oracle.scaled_error(D, D_ref, s_q) <= TOL
+
+
+@pytest.mark.parametrize("H,W,N,dtype,kw", [
+    (16, 16, 3000, "u16", {}),                               # L = 4096, many tiles
+    (32, 16, 2000, "f32", {"q_begin": 64, "q_end": 200}),    # L = 2048, a wave-vector range
+    (32, 32, 2500, "u16", {"kmax": 7}),                      # L = 4096 on the cropped store
+])
+def test_long_sequences_end_to_end(H, W, N, dtype, kw):
+    """N above 1024: the three-pass time transforms, from frames to D."""
+    import torch
+    if dtype == "u16":
+        frames = synth.blob_stack(H, W, N, n_particles=8, sigma_px=1.5, D0=0.3, seed=N)
+    else:
+        frames = synth.ou_stack(H, W, N, 0.2, synth.gaussian_spectrum(0.7), 0.05, seed=N)
+    plan = ddm.Plan(H, W, N, dtype=dtype, **kw)
+    D = torch.full((plan.n_q * N,), float("nan"), device="cuda")
+    plan.structure_function(to_device(frames), D)
+    torch.cuda.synchronize()
+    assert plan.last_device_status() == 0
+    D = D.cpu().numpy().reshape(plan.n_q, N)
+    ky, kx = plan.wave_vectors()
+    kmax = kw.get("kmax", 0)
+    D_ref, s_q = oracle.structure_function(frames, kx_sel=list(range(kmax + 1)) if kmax else None)
+    rows = np.arange(plan.n_q)
+    if "q_begin" in kw:               # stored range -> D rows
+        sky, skx = (np.asarray(a) for a in ddm.spectrum_index_map(H, W))
+        st = np.arange(kw["q_begin"], kw["q_end"])
+        rows = sky[st] * (W // 2 + 1) + skx[st]
+    Dt, Dr, sq = D[rows], D_ref[ky[rows], kx[rows]], s_q[ky[rows], kx[rows]]
+    assert np.all(Dt[:, 0] == 0)
+    assert oracle.scaled_error(Dt, Dr, sq) <= TOL
 
 
 def test_temporal_many_tiles_random_spectrum():
