@@ -651,20 +651,23 @@ row_bulk_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
                         ::"r"(cvta_smem(stage_r + off)), "l"(reinterpret_cast<const unsigned char*>(ref) + off),
                         "r"(n), "r"(cvta_smem(&bar)) : "memory");
             }
-        } else {
-            for (int r = 0; r < 2 * npairs; ++r) {
+        }
+    }
+    if constexpr (C::PAD != 0) {
+        // one row per thread: the barrier expects the bytes before any copy is issued
+        __syncthreads();
+        for (int r = tid; r < 2 * npairs; r += NT) {
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                ::"r"(cvta_smem(stage_f + (size_t)r * C::ROW_STRIDE)),
+                "l"(reinterpret_cast<const unsigned char*>(src) + (size_t)r * C::BYTES_ROW),
+                "r"((uint32_t)C::BYTES_ROW), "r"(cvta_smem(&bar)) : "memory");
+            if (subtract_ref)
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                    ::"r"(cvta_smem(stage_f + (size_t)r * C::ROW_STRIDE)),
-                    "l"(reinterpret_cast<const unsigned char*>(src) + (size_t)r * C::BYTES_ROW),
+                    ::"r"(cvta_smem(stage_r + (size_t)r * C::ROW_STRIDE)),
+                    "l"(reinterpret_cast<const unsigned char*>(ref) + (size_t)r * C::BYTES_ROW),
                     "r"((uint32_t)C::BYTES_ROW), "r"(cvta_smem(&bar)) : "memory");
-                if (subtract_ref)
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                        ::"r"(cvta_smem(stage_r + (size_t)r * C::ROW_STRIDE)),
-                        "l"(reinterpret_cast<const unsigned char*>(ref) + (size_t)r * C::BYTES_ROW),
-                        "r"((uint32_t)C::BYTES_ROW), "r"(cvta_smem(&bar)) : "memory");
-            }
         }
     }
     if constexpr (T > 1) {
