@@ -81,6 +81,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's time (every rank gets it): the job is done when the last rank is."""
+    if dist is None:
+        return ms
+    import torch
+    tt = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(n_ranks, frames_per_rank, steps, ms_total):
+    """Whole-job frames/s: every rank processes its own stacks (replicas), so the units all
+    ranks processed over the slowest rank's time."""
+    return n_ranks * frames_per_rank * steps / (ms_total / 1e3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -361,18 +377,14 @@ def run_ours(args):
         if dist:
             dist.barrier()
     clocks = clk.summary(t0, t1)
-    ms_total = start.elapsed_time(end)
-    if dist:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(start.elapsed_time(end), dist, dev)
     ms_step = ms_total / args.steps
     sp_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
     tm_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
     rd_ms = sum(e[2].elapsed_time(e[3]) for e in evs) / args.steps
     ft_ms = sum(e[3].elapsed_time(e[4]) for e in evs) / args.steps
     n_gpus = ws
-    value = n_gpus * N_FRAMES * args.steps / (ms_total / 1e3)
+    value = job_throughput(n_gpus, N_FRAMES, args.steps, ms_total)
     peak, peak_kind = measured_peaks()
 
     # ---- end to end through the public API: pinned host frames in, radial average and fit
@@ -417,12 +429,8 @@ def run_ours(args):
         e2e_run(k_e2e, s0)
         s1.record(stream)
         torch.cuda.synchronize()
-        e_ms = s0.elapsed_time(s1)
-        if dist:
-            tt = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
-        e2e = {"value": n_gpus * N_FRAMES * k_e2e / (e_ms / 1e3), "unit": "frames/s",
+        e_ms = max_over_ranks(s0.elapsed_time(s1), dist, dev)
+        e2e = {"value": job_throughput(n_gpus, N_FRAMES, k_e2e, e_ms), "unit": "frames/s",
                "h2d_bytes_per_step": int(host.numel() * host.element_size()),
                "d2h_bytes_per_step": int(Dr_host.numel() * Dr_host.element_size()
                                          + params_host.numel() * params_host.element_size()),

@@ -1,0 +1,41 @@
+"""bench.py's multi-rank arithmetic on CPU ranks (gloo, world size 2): every rank sees the
+slowest rank's time, and the reported throughput is the whole job's."""
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = bench.max_over_ranks(100.0 + 50.0 * rank, dist)     # rank 1 is the slow one
+        with open(os.path.join(out_dir, f"r{rank}.txt"), "w") as f:
+            f.write(repr(ms))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_two_gloo_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    mp.spawn(_rank, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        assert float((tmp_path / f"r{r}.txt").read_text()) == 150.0
+
+
+def test_single_rank_and_throughput():
+    assert bench.max_over_ranks(12.5) == 12.5
+    # two ranks, 1024 frames each, 10 steps in 20 ms -> 1,024,000 frames/s for the job
+    assert bench.job_throughput(2, 1024, 10, 20.0) == pytest.approx(1.024e6)
+    assert bench.job_throughput(1, 1024, 10, 20.0) == pytest.approx(5.12e5)
