@@ -66,6 +66,7 @@ void free_plan(ddm_plan_s* p) {
     cudaFree(p->tw_col);
     cudaFree(p->tw_t);
     cudaFree(p->tw_tin);
+    cudaFree(p->tw_long);
     cudaFree(p->tw2);
     cudaFree(p->inv);
     cudaFree(p->bin_start);
@@ -229,6 +230,23 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
     if (st == DDM_OK) st = upload(&p->tw_col, pass_twiddles(desc->H));
     if (st == DDM_OK) st = upload(&p->tw_t, pass_twiddles(p->L));
     if (st == DDM_OK && p->L >= 2048) st = upload(&p->tw_tin, pass_twiddles(p->L / 32));
+    if (st == DDM_OK && p->L >= 2048) {
+        const int L = p->L, Tl = L / 32;
+        std::vector<float2> t;
+        for (int k = 0; k < L / 4; ++k) {
+            const cx_cs cs = cx_cossin_frac(k, L);
+            t.push_back(make_float2((float)cs.c, (float)cs.s));
+        }
+        for (int i = 0; i < Tl; ++i) {
+            const cx_cs cs = cx_cossin_frac(i, 2L * L);
+            t.push_back(make_float2((float)cs.c, (float)-cs.s));
+        }
+        for (int u = 0; u < 32; ++u) {
+            const cx_cs cs = cx_cossin_frac(u, 64);
+            t.push_back(make_float2((float)cs.c, (float)-cs.s));
+        }
+        st = upload(&p->tw_long, t);
+    }
     // exp(-i pi t / L) and 1/(N - m)
     if (st == DDM_OK) {
         std::vector<float2> tw2(p->L);

@@ -369,9 +369,32 @@ struct AddrHandover {
 };
 
 // xs holds max(P (T + PAD) QT, L QT) elements; QT transforms interleaved (transform ql).
-template <int L, bool INV, int QT, int PAD, typename Sync>
+// Pass-1 twiddles w_L^{i k1} from a quarter-wave table q[k] = (cos 2 pi k / L, sin 2 pi k / L),
+// k = 0 .. L/4, and the quadrant of the exponent (exact symmetry: no extra rounding).
+template <int L>
+struct TwiddleQuarter {
+    const float2* q;
+    __device__ __forceinline__ float2 operator()(int k1, int i) const {
+        const int j = (k1 * i) & (L - 1);
+        const int quad = j / (L / 4), r = j & (L / 4 - 1);
+        const float2 b = q[r];
+        const float cq = (quad & 1) ? b.y : b.x;          // cos / sin of the reduced angle,
+        const float sq = (quad & 1) ? b.x : b.y;          // swapped in odd quadrants
+        const float c = (quad == 1 || quad == 2) ? -cq : cq;
+        const float s = (quad >= 2) ? -sq : sq;
+        return make_float2(c, -s);                        // exp(-2 pi i j / L)
+    }
+};
+// ... or from a full table in host_pass_twiddles layout
+struct TwiddleTable {
+    const float2* t;
+    int T;
+    __device__ __forceinline__ float2 operator()(int k1, int i) const { return t[k1 * T + i]; }
+};
+
+template <int L, bool INV, int QT, int PAD, typename Tw1, typename Sync>
 __device__ __forceinline__ void fft_cyclic3(float2 (&v)[32], int i, int ql, float2* xs,
-                                            const float2* tw1, const float2* tw_in, Sync sync) {
+                                            Tw1 tw1, const float2* tw_in, Sync sync) {
     constexpr int P = 32;
     constexpr int T = L / P;
     constexpr int R = T / P;
@@ -382,7 +405,7 @@ __device__ __forceinline__ void fft_cyclic3(float2 (&v)[32], int i, int ql, floa
     for (int k1 = 0; k1 < P; ++k1) {
         float2 a = v[k1];
         if (k1 > 0) {
-            const float2 w = tw1[k1 * T + i];
+            const float2 w = tw1(k1, i);
             a = INV ? cmul_conj(a, w) : cmul(a, w);
         }
         xs[hand(k1, i)] = a;

@@ -23,6 +23,8 @@ struct ddm_plan_s {
     float2* tw_col;     // pass twiddles of the H-point column transform
     float2* tw_t;       // pass twiddles of the L-point time transform
     float2* tw_tin;     // L >= 2048: pass twiddles of the inner L/32-point transform
+    float2* tw_long;    // L >= 2048: (cos, sin) 2 pi k / L for k < L/4; exp(-i pi i / L) for
+                        // i < L/32; exp(-i pi u / 32) for u < 32
     float2* tw2;        // exp(-i pi t / L), t < L
     float* inv;         // 1 / (N - m), m < N; 0 at m = 0
     int* bin_start;     // [n_bins + 1] CSR offsets into bin_q

@@ -508,55 +508,65 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
 }
 
 // =====================================================================================
-// L = 2048, 4096 (N up to 4096): one 256-thread CTA per SM, three-pass transforms
+// L = 2048, 4096 (N up to 4096): 256-thread CTAs, two per SM, three-pass transforms
 // =====================================================================================
 // A CTA owns QG = 256 / T wave vectors at a time (T = L / 32 threads each, 32 samples per
 // thread).  Tiles arrive by TMA as above; the three transforms are fft_cyclic3 (32-point
 // register DFT, handover exchange, inner two-pass T-point transform), whose output order
 // is the permuted thread index sigma(i); the inverse runs with i = sigma(i) and leaves
 // lag m = sigma(sigma(i)) + T u in thread i.  Prefix sums: thread i owns the chunk of 32
-// consecutive frames starting at 32 i.
+// consecutive frames starting at 32 i.  Small tables so that two CTAs share an SM: pass
+// twiddles from a quarter-wave table; e^{-i pi t / L} for t = i + T u as e^{-i pi i / L}
+// (one per thread) times e^{-i pi u / 32}; 1/(N - m) as a correctly rounded reciprocal.
+// The next tile's copy is issued before the D rows are staged; the rows leave by bulk
+// copies, as in the kernel above.
 template <int LOG2L>
 struct LShape {
     static constexpr int L = 1 << LOG2L;
     static constexpr int P = 32, T = L / P, R = T / P;
     static constexpr int NT = 256;
     static constexpr int QG = NT / T;             // wave vectors per tile
-    static constexpr int IW = 32 / QG;            // threads of one wave vector per warp
     static constexpr int NWG = NT / 32;
-    static constexpr int KD = 32;
     static constexpr int PAD = (QG == 2) ? 4 : 2; // (T + PAD) * QG = 8 mod 16: handover reads spread
     static constexpr int DS = L + 4;              // D staging row stride (floats)
     static constexpr int BOX_T = 256, NBOX = L / BOX_T;
     static constexpr size_t XS_ELEMS = (size_t)P * (T + PAD) * QG > (size_t)L * QG
                                            ? (size_t)P * (T + PAD) * QG : (size_t)L * QG;
-    static constexpr size_t OFF_TW1 = 0;
-    static constexpr size_t OFF_TWI = OFF_TW1 + (size_t)L * sizeof(float2);
-    static constexpr size_t OFF_TW2 = OFF_TWI + (size_t)T * sizeof(float2);
-    static constexpr size_t OFF_INV = OFF_TW2 + (size_t)L * sizeof(float2);
-    static constexpr size_t OFF_XS = (OFF_INV + (size_t)L * sizeof(float) + 1023) & ~size_t(1023);
+    static constexpr size_t OFF_TWQ = 0;                                        // L/4 entries
+    static constexpr size_t OFF_TWI = OFF_TWQ + (size_t)(L / 4) * sizeof(float2);  // T entries
+    static constexpr size_t OFF_CI = OFF_TWI + (size_t)T * sizeof(float2);         // T entries
+    static constexpr size_t OFF_W64 = OFF_CI + (size_t)T * sizeof(float2);         // 32 entries
+    static constexpr size_t OFF_XS = (OFF_W64 + 32 * sizeof(float2) + 1023) & ~size_t(1023);
     static constexpr size_t OFF_AB = OFF_XS + XS_ELEMS * sizeof(float2);
     static constexpr size_t OFF_RED = OFF_AB + cmax((size_t)L * QG, (size_t)QG * DS) * sizeof(float);
     static constexpr size_t BYTES = OFF_RED + (size_t)T * QG * sizeof(float);
     static_assert(T % P == 0 && QG * T == NT && QG >= 2, "long kernel: L = 2048 or 4096");
-    static_assert(BYTES + 1024 <= 232448, "temporal kernel shared memory exceeds 227 KB");
+    static_assert(2 * (BYTES + 1024) <= 233472, "two CTAs per SM");
     static_assert((size_t)(L + L / P) * QG <= 2 * XS_ELEMS, "padded prefix chunks must fit");
     static_assert((size_t)NWG * QG * 2 <= (size_t)T * QG, "mean partials must fit");
+    static_assert((DS % 4) == 0 && (OFF_AB % 16) == 0, "D rows 16-byte aligned for bulk copies");
+};
+
+struct LTables {
+    const float2* quarter;   // (cos, sin) of 2 pi k / L, k < L / 4
+    const float2* inner;     // pass twiddles of the inner T-point transform
+    const float2* ci;        // exp(-i pi i / L), i < T
+    const float2* w64;       // exp(-i pi u / 32), u < 32
 };
 
 template <int LOG2L>
-__global__ void __launch_bounds__(LShape<LOG2L>::NT, 1)
+__global__ void __launch_bounds__(LShape<LOG2L>::NT, 2)
 temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUtensorMap tmap,
-                        const float2* __restrict__ tw_in_g) {
+                        LTables tb) {
     using C = LShape<LOG2L>;
     constexpr int L = C::L, P = C::P, T = C::T, R = C::R, QG = C::QG, NT = C::NT, NWG = C::NWG;
     constexpr int DS = C::DS, PAD = C::PAD;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t tile_bar;
-    float2* tw1 = reinterpret_cast<float2*>(smem_raw + C::OFF_TW1);
+    float2* twq = reinterpret_cast<float2*>(smem_raw + C::OFF_TWQ);
     float2* twi = reinterpret_cast<float2*>(smem_raw + C::OFF_TWI);
-    float2* tw2 = reinterpret_cast<float2*>(smem_raw + C::OFF_TW2);
-    float* inv = reinterpret_cast<float*>(smem_raw + C::OFF_INV);
+    float2* ci = reinterpret_cast<float2*>(smem_raw + C::OFF_CI);
+    float2* w64 = reinterpret_cast<float2*>(smem_raw + C::OFF_W64);
     float2* xs = reinterpret_cast<float2*>(smem_raw + C::OFF_XS);
     float* xf = reinterpret_cast<float*>(xs);
     float* ab = reinterpret_cast<float*>(smem_raw + C::OFF_AB);
@@ -568,24 +578,26 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
         mbar_init(&tile_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int k = tid; k < L; k += NT) {
-        tw1[k] = a.tw[k];
-        tw2[k] = a.tw2[k];
-        inv[k] = a.inv[k];
+    for (int k = tid; k < L / 4; k += NT) twq[k] = tb.quarter[k];
+    for (int k = tid; k < T; k += NT) {
+        twi[k] = tb.inner[k];
+        ci[k] = tb.ci[k];
     }
-    for (int k = tid; k < T; k += NT) twi[k] = tw_in_g[k];
+    if (tid < 32) w64[tid] = tb.w64[tid];
     __syncthreads();
 
     const int ql = tid % QG, i = tid / QG;
     const int lane = tid & 31, wg = tid >> 5;
     const int s1 = fft3_sigma(i, P, R);          // forward output order
     const int s2 = fft3_sigma(s1, P, R);         // inverse output order (input order s1)
+    const float2 c_i = ci[i], c_s2 = ci[s2];
+    const TwiddleQuarter<L> tw1{twq};
     const int N = a.N, kd = a.kd;
     const int64_t q0 = a.q0, q1 = a.q1;
     bool timed_out = false;
     float chk = 0.f;
     uint32_t phase = 0;
-    auto load = [&](int64_t t) -> bool {
+    auto issue = [&](int64_t t) {
         if (tid == 0) {
             fence_proxy_async();
             mbar_expect_tx(&tile_bar, (uint32_t)(C::NBOX * C::BOX_T * QG * sizeof(float2)));
@@ -593,18 +605,20 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             for (int b = 0; b < C::NBOX; ++b)
                 tma_load_2d(xs + b * C::BOX_T * QG, &tmap, (int)(2 * (q0 + t * QG)), b * C::BOX_T, &tile_bar);
         }
+    };
+    auto wait = [&]() -> bool {
         const bool ok = mbar_wait_bounded(&tile_bar, phase);
         if (__syncthreads_or(ok ? 0 : 1)) return false;
         phase ^= 1u;
         return true;
     };
-    // this thread's trailing lag, if < N: the one it also holds in the combination's order
+    // trailing lag of this thread, if < N: the one it also holds in the combination's order
     const int m_lo = N - kd;
     const int m_tail = m_lo + ((s2 - m_lo) % T + T) % T;
 
+    if ((int64_t)blockIdx.x < a.n_tiles) issue(blockIdx.x);
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-        __syncthreads();                                   // the previous tile is done with smem
-        if (!load(tile)) { timed_out = true; break; }
+        if (!wait()) { timed_out = true; break; }
         // ---- time sequence (cyclic, thread i holds t = i + T u) and its mean
         float2 v[P];
         float2 part = make_float2(0.f, 0.f);
@@ -619,6 +633,7 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
         }
         if (lane < QG) red2[wg * QG + ql] = part;
+        if (tid < QG) bulk_wait_read_all();                // the previous rows have left ab
         __syncthreads();
         float2 mean = make_float2(0.f, 0.f);
 #pragma unroll
@@ -631,14 +646,15 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             const int t = i + T * u;
-            v[u] = (t < N) ? cmul(csub(v[u], mean), tw2[t]) : make_float2(0.f, 0.f);
+            v[u] = (t < N) ? cmul(cmul(csub(v[u], mean), c_i), w64[u]) : make_float2(0.f, 0.f);
             if ((u & 7) == 7) hoist_fence();
         }
         fft_cyclic3<L, false, QG, PAD>(v, i, ql, xs, tw1, twi, SyncBlock{});
 #pragma unroll
         for (int u = 0; u < P; ++u) ab[(s1 + T * u) * QG + ql] = cabs2(v[u]);
         // ---- even bins: DFT of g (the tile again)
-        if (!load(tile)) { timed_out = true; break; }
+        issue(tile);
+        if (!wait()) { timed_out = true; break; }
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             const int t = i + T * u;
@@ -663,14 +679,15 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
                 const int m = s2 + T * u;
                 const float2 z = v[u];
                 const float2 zr = xs[((L - m) & (L - 1)) * QG + ql];
-                const float2 w = tw2[m];
+                const float2 w = cmul(c_s2, w64[u]);       // e^{-i pi m / L}
                 ab[m * QG + ql] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
                 if ((u & 7) == 7) hoist_fence();
             }
         }
         // ---- the tile a third time: |g - mean|^2 and the trailing lags (Eq. 1)
         __syncthreads();                                   // partner reads done: xs is free
-        if (!load(tile)) { timed_out = true; break; }
+        issue(tile);
+        if (!wait()) { timed_out = true; break; }
         float e[P];
 #pragma unroll
         for (int u = 0; u < P; ++u) {
@@ -681,7 +698,7 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
         if (m_tail < N) {
             for (int t = 0; t < N - m_tail; ++t)
                 tl += cabs2(csub(xs[(t + m_tail) * QG + ql], xs[t * QG + ql]));
-            tl *= inv[m_tail];
+            tl *= __frcp_rn((float)(N - m_tail));
             chk = fmaf(tl, 0.f, chk);
         }
         __syncthreads();                                   // tile read
@@ -720,31 +737,40 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             const int m = s2 + T * u;
             float d = 0.f;
             if (m > 0 && m < N - kd) {
-                const int ta = N - 1 - m, tb = m - 1;
+                const int ta = N - 1 - m, tb2 = m - 1;
                 const float p1 = xf[(ta + (ta >> 5)) * QG + ql];
-                const float p2 = total - xf[(tb + (tb >> 5)) * QG + ql];
-                d = (p1 + p2 - 2.f * ab[m * QG + ql]) * inv[m];
+                const float p2 = total - xf[(tb2 + (tb2 >> 5)) * QG + ql];
+                d = (p1 + p2 - 2.f * ab[m * QG + ql]) * __frcp_rn((float)(N - m));
                 chk = fmaf(d, 0.f, chk);
             }
             dv[u] = d;
             if ((u & 7) == 7) hoist_fence();
         }
         __syncthreads();                                   // reads of S and Re C done
+        // ---- the next tile's copy overlaps the staging and the stores of this one
+        if (tile + gridDim.x < a.n_tiles) issue(tile + gridDim.x);
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             const int m = s2 + T * u;
             if (m < N) ab[ql * DS + m] = dv[u];
         }
         if (m_tail < N) ab[ql * DS + m_tail] = tl;
+        if (a.vec4) fence_proxy_async();
         __syncthreads();
-        for (int r = 0; r < QG; ++r) {
-            const int64_t sr = q0 + tile * QG + r;
-            if (sr >= q1) break;
-            float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
-            if (a.vec4) {
-                for (int m4 = tid; m4 < N / 4; m4 += NT)
-                    reinterpret_cast<float4*>(drow)[m4] = *reinterpret_cast<const float4*>(ab + r * DS + 4 * m4);
-            } else {
+        if (a.vec4) {
+            if (tid < QG) {
+                const int64_t sr = q0 + tile * QG + tid;
+                if (sr < q1) {
+                    float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
+                    bulk_store(drow, ab + tid * DS, (uint32_t)N * (uint32_t)sizeof(float));
+                }
+                bulk_commit();
+            }
+        } else {
+            for (int r = 0; r < QG; ++r) {
+                const int64_t sr = q0 + tile * QG + r;
+                if (sr >= q1) break;
+                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
                 for (int m = tid; m < N; m += NT) drow[m] = ab[r * DS + m];
             }
         }
@@ -753,6 +779,7 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
         if (tid == 0) atomicOr(a.status, 2u);
         mbar_wait_bounded(&tile_bar, phase);
     }
+    if (tid < QG) bulk_wait_all();
     if (chk != chk) atomicOr(a.status, 1u);
 }
 
@@ -1074,7 +1101,7 @@ ddm_status launch_grouped(const ddm_plan_s* p, const float2* spec, float* D, cud
 template <int LOG2L>
 ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
     using C = LShape<LOG2L>;
-    if ((reinterpret_cast<uintptr_t>(spec) & 15) != 0 || !p->tw_tin) return DDM_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(spec) & 15) != 0 || !p->tw_tin || !p->tw_long) return DDM_ERR_INVALID_ARG;
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof(tmap));
     if (!make_spectrum_map(&tmap, spec, p->n_q, p->d.N, C::QG)) return DDM_ERR_CUDA;
@@ -1084,8 +1111,16 @@ ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaSt
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
         cudaSuccess)
         return DDM_ERR_CUDA;
-    const int64_t grid = a.n_tiles < p->n_sm ? a.n_tiles : p->n_sm;
-    k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(D, a, tmap, p->tw_tin);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return DDM_ERR_CUDA;
+    LTables tb;
+    tb.quarter = p->tw_long;                      // [L/4] quarter wave, then [T] ci, then [32] w64
+    tb.ci = p->tw_long + p->L / 4;
+    tb.w64 = p->tw_long + p->L / 4 + p->L / 32;
+    tb.inner = p->tw_tin;
+    const int64_t grid = a.n_tiles < 2 * (int64_t)p->n_sm ? a.n_tiles : 2 * (int64_t)p->n_sm;
+    k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(D, a, tmap, tb);
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 
