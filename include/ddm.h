@@ -71,7 +71,7 @@ typedef enum ddm_spatial_path {
 
 typedef struct ddm_plan_desc {
     int H, W;          /* frame height and width in pixels (powers of two, 2..1024) */
-    int N;             /* number of frames, 1 .. 4096 */
+    int N;             /* number of frames, 1 .. 8192 */
     int dtype;         /* ddm_dtype */
     int precision;     /* ddm_precision */
     int M;             /* temporal pad length; 0 = N_2 of Eq. B4.  Any M >= 2N-1 gives

@@ -26,7 +26,7 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 constexpr int kRadialChunk = 64;   // wave vectors per radial partial sum
 
 constexpr int kMaxSide = 1024;
-constexpr int kMaxFrames = 4096;
+constexpr int kMaxFrames = 8192;
 
 // floor(n_bins * |q| / (pi sqrt 2)) with |q| = 2 pi sqrt((ky/H)^2 + (kx/W)^2):
 // the largest b with (b H W)^2 <= 2 n_bins^2 (ky^2 W^2 + kx^2 H^2), in exact integers.

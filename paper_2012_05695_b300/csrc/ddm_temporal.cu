@@ -508,7 +508,8 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
 }
 
 // =====================================================================================
-// L = 2048, 4096 (N up to 4096): 256-thread CTAs, two per SM, three-pass transforms
+// L = 2048 .. 8192 (N up to 8192): three-pass transforms; 256-thread CTAs, two per SM, at
+// L = 2048, 4096; one 512-thread CTA per SM at L = 8192
 // =====================================================================================
 // A CTA owns QG = 256 / T wave vectors at a time (T = L / 32 threads each, 32 samples per
 // thread).  Tiles arrive by TMA as above; the three transforms are fft_cyclic3 (32-point
@@ -524,7 +525,8 @@ template <int LOG2L>
 struct LShape {
     static constexpr int L = 1 << LOG2L;
     static constexpr int P = 32, T = L / P, R = T / P;
-    static constexpr int NT = 256;
+    static constexpr int NT = L >= 8192 ? 512 : 256;   // QG = 2 at L = 4096 and 8192
+    static constexpr int CTAS_PER_SM = NT == 256 ? 2 : 1;
     static constexpr int QG = NT / T;             // wave vectors per tile
     static constexpr int NWG = NT / 32;
     static constexpr int PAD = (QG == 2) ? 4 : 2; // (T + PAD) * QG = 8 mod 16: handover reads spread
@@ -540,8 +542,8 @@ struct LShape {
     static constexpr size_t OFF_AB = OFF_XS + XS_ELEMS * sizeof(float2);
     static constexpr size_t OFF_RED = OFF_AB + cmax((size_t)L * QG, (size_t)QG * DS) * sizeof(float);
     static constexpr size_t BYTES = OFF_RED + (size_t)T * QG * sizeof(float);
-    static_assert(T % P == 0 && QG * T == NT && QG >= 2, "long kernel: L = 2048 or 4096");
-    static_assert(2 * (BYTES + 1024) <= 233472, "two CTAs per SM");
+    static_assert(T % P == 0 && QG * T == NT && QG >= 2, "long kernel: L = 2048 .. 8192");
+    static_assert(CTAS_PER_SM * (BYTES + 1024) <= 233472, "shared memory per SM");
     static_assert((size_t)(L + L / P) * QG <= 2 * XS_ELEMS, "padded prefix chunks must fit");
     static_assert((size_t)NWG * QG * 2 <= (size_t)T * QG, "mean partials must fit");
     static_assert((DS % 4) == 0 && (OFF_AB % 16) == 0, "D rows 16-byte aligned for bulk copies");
@@ -555,7 +557,7 @@ struct LTables {
 };
 
 template <int LOG2L>
-__global__ void __launch_bounds__(LShape<LOG2L>::NT, 2)
+__global__ void __launch_bounds__(LShape<LOG2L>::NT, LShape<LOG2L>::CTAS_PER_SM)
 temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUtensorMap tmap,
                         LTables tb) {
     using C = LShape<LOG2L>;
@@ -1119,7 +1121,8 @@ ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaSt
     tb.ci = p->tw_long + p->L / 4;
     tb.w64 = p->tw_long + p->L / 4 + p->L / 32;
     tb.inner = p->tw_tin;
-    const int64_t grid = a.n_tiles < 2 * (int64_t)p->n_sm ? a.n_tiles : 2 * (int64_t)p->n_sm;
+    const int64_t slots = (int64_t)C::CTAS_PER_SM * p->n_sm;
+    const int64_t grid = a.n_tiles < slots ? a.n_tiles : slots;
     k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(D, a, tmap, tb);
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
@@ -1159,6 +1162,7 @@ ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cu
         case 10: return fix ? launch_grouped<10, true, 2>(p, spec, D, s) : launch_grouped<10, false, 2>(p, spec, D, s);
         case 11: return launch_long<11>(p, spec, D, s);
         case 12: return launch_long<12>(p, spec, D, s);
+        case 13: return launch_long<13>(p, spec, D, s);
         default: return DDM_ERR_UNSUPPORTED;
     }
 }

@@ -53,7 +53,7 @@ def test_desc_init_defaults():
     ("W", 0, B.DDM_ERR_INVALID_ARG),
     ("H", 2048, B.DDM_ERR_UNSUPPORTED),
     ("N", 0, B.DDM_ERR_INVALID_ARG),
-    ("N", 5000, B.DDM_ERR_UNSUPPORTED),
+    ("N", 9000, B.DDM_ERR_UNSUPPORTED),
     ("dtype", 7, B.DDM_ERR_INVALID_ARG),
     ("precision", 9, B.DDM_ERR_INVALID_ARG),
     ("precision", 1, B.DDM_ERR_UNSUPPORTED),      # FP64 fixup needs 257 <= N <= 1024
