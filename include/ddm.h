@@ -57,7 +57,7 @@ typedef enum ddm_precision {
     DDM_PREC_FP32_FP64FIX = 1 /* as FP32, plus: lags 1..fix_lags recomputed by direct
                                  differences (Eq. 1), FP32 over each thread's 32 frames and
                                  FP64 across threads: no cancellation against the power
-                                 sums.  This build: 257 <= N <= 1024, fix_lags <= 8 */
+                                 sums.  This build: 257 <= N <= 8192, fix_lags <= 8 */
 } ddm_precision;
 
 /* Kernels of step one.  Both give the same spectrum (to FP32 rounding). */

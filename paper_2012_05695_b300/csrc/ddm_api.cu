@@ -117,7 +117,7 @@ ddm_status validate(const ddm_plan_desc* d) {
     if (d->precision == DDM_PREC_FP32_FP64FIX) {
         // built for the time transforms whose tiles arrive whole in shared memory
         const int Lf = 1 << ilog2(d->N);
-        if (Lf != 512 && Lf != 1024) return DDM_ERR_UNSUPPORTED;
+        if (Lf < 512) return DDM_ERR_UNSUPPORTED;
         if (d->fix_lags > 8) return DDM_ERR_UNSUPPORTED;
     }
     if (d->subtract_ref != 0 && d->subtract_ref != 1) return DDM_ERR_INVALID_ARG;

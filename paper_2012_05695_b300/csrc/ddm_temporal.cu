@@ -541,7 +541,9 @@ struct LShape {
     static constexpr size_t OFF_XS = (OFF_W64 + 32 * sizeof(float2) + 1023) & ~size_t(1023);
     static constexpr size_t OFF_AB = OFF_XS + XS_ELEMS * sizeof(float2);
     static constexpr size_t OFF_RED = OFF_AB + cmax((size_t)L * QG, (size_t)QG * DS) * sizeof(float);
-    static constexpr size_t BYTES = OFF_RED + (size_t)T * QG * sizeof(float);
+    static constexpr int FIX_MAX = 8;
+    static constexpr size_t OFF_FIX = OFF_RED + (size_t)T * QG * sizeof(float);
+    static constexpr size_t BYTES = OFF_FIX + (size_t)FIX_MAX * NWG * QG * sizeof(float);
     static_assert(T % P == 0 && QG * T == NT && QG >= 2, "long kernel: L = 2048 .. 8192");
     static_assert(CTAS_PER_SM * (BYTES + 1024) <= 233472, "shared memory per SM");
     static_assert((size_t)(L + L / P) * QG <= 2 * XS_ELEMS, "padded prefix chunks must fit");
@@ -556,13 +558,13 @@ struct LTables {
     const float2* w64;       // exp(-i pi u / 32), u < 32
 };
 
-template <int LOG2L>
+template <int LOG2L, bool FIXUP>
 __global__ void __launch_bounds__(LShape<LOG2L>::NT, LShape<LOG2L>::CTAS_PER_SM)
 temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUtensorMap tmap,
                         LTables tb) {
     using C = LShape<LOG2L>;
     constexpr int L = C::L, P = C::P, T = C::T, R = C::R, QG = C::QG, NT = C::NT, NWG = C::NWG;
-    constexpr int DS = C::DS, PAD = C::PAD;
+    constexpr int DS = C::DS, PAD = C::PAD, FM = C::FIX_MAX;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t tile_bar;
     float2* twq = reinterpret_cast<float2*>(smem_raw + C::OFF_TWQ);
@@ -574,6 +576,7 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
     float* ab = reinterpret_cast<float*>(smem_raw + C::OFF_AB);
     float* red = reinterpret_cast<float*>(smem_raw + C::OFF_RED);
     float2* red2 = reinterpret_cast<float2*>(red);
+    float* fixw = reinterpret_cast<float*>(smem_raw + C::OFF_FIX);
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -703,6 +706,30 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             tl *= __frcp_rn((float)(N - m_tail));
             chk = fmaf(tl, 0.f, chk);
         }
+        if constexpr (FIXUP) {
+            // FP64-fixup tier: sum over this thread's samples of |g(t+m) - g(t)|^2, m = 1..fix,
+            // then over the lanes of the same wave vector in the warp
+            const int fix = a.fix;
+            float fp[FM];
+#pragma unroll
+            for (int k = 0; k < FM; ++k) fp[k] = 0.f;
+#pragma unroll 4
+            for (int u = 0; u < P; ++u) {
+                const int t = i + T * u;
+                if (t < N) {
+                    const float2 g0 = xs[t * QG + ql];
+#pragma unroll
+                    for (int k = 0; k < FM; ++k)
+                        if (k < fix && t + k + 1 < N) fp[k] += cabs2(csub(xs[(t + k + 1) * QG + ql], g0));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < FM; ++k) {
+#pragma unroll
+                for (int o = QG; o < 32; o <<= 1) fp[k] += __shfl_xor_sync(0xffffffffu, fp[k], o);
+                if (lane < QG) fixw[(k * NWG + wg) * QG + ql] = fp[k];
+            }
+        }
         __syncthreads();                                   // tile read
         // |g|^2 at padded positions t + t / 32 (chunk-wise reads below are conflict-free)
 #pragma unroll
@@ -732,6 +759,16 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
 #pragma unroll
         for (int jj = 0; jj < P; ++jj) xf[(i * (P + 1) + jj) * QG + ql] = rowv[jj] + off;
         __syncthreads();
+        // FP64-fixup tier: lag m = s2 (1 <= s2 <= fix), held by this thread at u = 0, summed
+        // over the warps in FP64
+        float fixd = 0.f;
+        const bool has_fix = FIXUP && a.fix > 0 && s2 >= 1 && s2 <= a.fix && s2 < N - kd;
+        if (has_fix) {
+            double sum = 0.0;
+            for (int w = 0; w < NWG; ++w) sum += (double)fixw[((s2 - 1) * NWG + w) * QG + ql];
+            fixd = (float)(sum / (double)(N - s2));
+            chk = fmaf(fixd, 0.f, chk);
+        }
         // ---- D(m) = (P1 + P2 - 2 Re C) / (N - m) for 0 < m < N - kd, m = s2 + T u
         float dv[P];
 #pragma unroll
@@ -757,6 +794,7 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             if (m < N) ab[ql * DS + m] = dv[u];
         }
         if (m_tail < N) ab[ql * DS + m_tail] = tl;
+        if (has_fix) ab[ql * DS + s2] = fixd;
         if (a.vec4) fence_proxy_async();
         __syncthreads();
         if (a.vec4) {
@@ -1100,7 +1138,7 @@ ddm_status launch_grouped(const ddm_plan_s* p, const float2* spec, float* D, cud
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 
-template <int LOG2L>
+template <int LOG2L, bool FIXUP>
 ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
     using C = LShape<LOG2L>;
     if ((reinterpret_cast<uintptr_t>(spec) & 15) != 0 || !p->tw_tin || !p->tw_long) return DDM_ERR_INVALID_ARG;
@@ -1109,7 +1147,7 @@ ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaSt
     if (!make_spectrum_map(&tmap, spec, p->n_q, p->d.N, C::QG)) return DDM_ERR_CUDA;
     TArgs a;
     fill_args(a, p, D, C::QG);
-    auto k = temporal_sf_long_kernel<LOG2L>;
+    auto k = temporal_sf_long_kernel<LOG2L, FIXUP>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
         cudaSuccess)
         return DDM_ERR_CUDA;
@@ -1160,9 +1198,9 @@ ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cu
         // rows, lockstep) 1.13 ms, 2 groups 1.05 ms, 4 groups (32-byte rows) 1.15 ms.
         case 9: return fix ? launch_grouped<9, true, 4>(p, spec, D, s) : launch_grouped<9, false, 4>(p, spec, D, s);
         case 10: return fix ? launch_grouped<10, true, 2>(p, spec, D, s) : launch_grouped<10, false, 2>(p, spec, D, s);
-        case 11: return launch_long<11>(p, spec, D, s);
-        case 12: return launch_long<12>(p, spec, D, s);
-        case 13: return launch_long<13>(p, spec, D, s);
+        case 11: return fix ? launch_long<11, true>(p, spec, D, s) : launch_long<11, false>(p, spec, D, s);
+        case 12: return fix ? launch_long<12, true>(p, spec, D, s) : launch_long<12, false>(p, spec, D, s);
+        case 13: return fix ? launch_long<13, true>(p, spec, D, s) : launch_long<13, false>(p, spec, D, s);
         default: return DDM_ERR_UNSUPPORTED;
     }
 }

@@ -56,7 +56,7 @@ def test_desc_init_defaults():
     ("N", 9000, B.DDM_ERR_UNSUPPORTED),
     ("dtype", 7, B.DDM_ERR_INVALID_ARG),
     ("precision", 9, B.DDM_ERR_INVALID_ARG),
-    ("precision", 1, B.DDM_ERR_UNSUPPORTED),      # FP64 fixup needs 257 <= N <= 1024
+    ("precision", 1, B.DDM_ERR_UNSUPPORTED),      # FP64 fixup needs N >= 257
     ("M", 6, B.DDM_ERR_INVALID_ARG),          # M < 2N - 1 wraps around (App. B)
     ("M", 7, B.DDM_ERR_UNSUPPORTED),          # legal pad length, not the one built
     ("subtract_ref", 2, B.DDM_ERR_INVALID_ARG),

@@ -304,7 +304,7 @@ def test_side_stream():
 
 
 # ------------------------------------------------------------------ FP64-fixup tier
-@pytest.mark.parametrize("N", [300, 1024])
+@pytest.mark.parametrize("N", [300, 1024, 2000, 4096, 6000])
 def test_fp64_fixup_tier_small_lags_relative_to_D(N):
     """Slow dynamics: D(1) is ~1e-5 of the plateau, so P1 + P2 - 2 Re C cancels most of
     its FP32 digits.  The fixup tier recomputes lags 1..8 by direct differences (FP64
