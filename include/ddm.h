@@ -70,7 +70,11 @@ typedef enum ddm_spatial_path {
 } ddm_spatial_path;
 
 typedef struct ddm_plan_desc {
-    int H, W;          /* frame height and width in pixels (powers of two, 2..1024) */
+    int H, W;          /* frame height and width in pixels, even, 2..1024: powers of two
+                          by radix-2 register FFTs; other even sides from 18 by
+                          Bluestein's chirp-z transform (a cyclic convolution of length
+                          2^ceil(log2(2n - 1)) <= 2048); odd sides DDM_ERR_INVALID_ARG,
+                          non-powers of two below 17 DDM_ERR_UNSUPPORTED */
     int N;             /* number of frames, 1 .. 8192 */
     int dtype;         /* ddm_dtype */
     int precision;     /* ddm_precision */
@@ -100,7 +104,9 @@ typedef struct ddm_plan_desc {
                           [N][n_q], n_q = (2 kmax + 1)(kmax + 1), stored order
                           ky' = 0..kmax, -kmax..-1 (outer) by kx = 0..kmax (inner); D rows
                           follow the same order.  kmax must be odd and below H/2 and W/2
-                          (DDM_ERR_INVALID_ARG otherwise).  The plan then also owns an
+                          (DDM_ERR_INVALID_ARG otherwise); this build crops only frames
+                          whose sides are powers of two (DDM_ERR_UNSUPPORTED otherwise).
+                          The plan then also owns an
                           intermediate of N * H * (kmax + 1) complex64 for step one */
 } ddm_plan_desc;
 

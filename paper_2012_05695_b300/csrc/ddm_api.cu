@@ -26,6 +26,7 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 constexpr int kRadialChunk = 64;   // wave vectors per radial partial sum
 
 constexpr int kMaxSide = 1024;
+constexpr int kMinBluesteinSide = 17;   // smallest side that is not a power of two: M >= 64
 constexpr int kMaxFrames = 8192;
 
 // floor(n_bins * |q| / (pi sqrt 2)) with |q| = 2 pi sqrt((ky/H)^2 + (kx/W)^2):
@@ -66,6 +67,12 @@ void free_plan(ddm_plan_s* p) {
     cudaFree(p->tw_col);
     cudaFree(p->tw_t);
     cudaFree(p->tw_tin);
+    for (ddm_bluestein* b : {&p->blue_w, &p->blue_h}) {
+        cudaFree(b->chirp);
+        cudaFree(b->filt);
+        cudaFree(b->tw);
+        cudaFree(b->twin);
+    }
     cudaFree(p->tw_long);
     cudaFree(p->tw2);
     cudaFree(p->inv);
@@ -83,6 +90,54 @@ void free_plan(ddm_plan_s* p) {
     cudaFree(p->dev_status);
     if (p->ws_owned) cudaFree(p->workspace);
     delete p;
+}
+
+std::vector<float2> pass_twiddles(int L);
+
+// Bluestein tables for length n, built in double precision: the chirp's angle reduced
+// exactly (j^2 mod 2n in integers), the filter's DFT by a plain O(M^2) sum in double.
+ddm_status make_bluestein(ddm_bluestein* b, int n) {
+    int M = 1;
+    while (M < 2 * n - 1) M *= 2;
+    b->n = n;
+    b->M = M;
+    std::vector<double> cr(n), ci(n);
+    for (int j = 0; j < n; ++j) {
+        const long r = (long)((long long)j * j % (2LL * n));
+        const cx_cs cs = cx_cossin_frac(r, 2L * n);      // angle 2 pi r / 2n = pi r / n
+        cr[j] = cs.c;
+        ci[j] = cs.s;
+    }
+    std::vector<double> pr(M, 0.0), pi(M, 0.0);          // c placed circularly: c_{-m} = c_m
+    for (int j = 0; j < n; ++j) {
+        pr[j] = cr[j];
+        pi[j] = ci[j];
+        if (j > 0) {
+            pr[M - j] = cr[j];
+            pi[M - j] = ci[j];
+        }
+    }
+    std::vector<float2> chirp(n), filt(M);
+    for (int j = 0; j < n; ++j) chirp[j] = make_float2((float)cr[j], (float)ci[j]);
+    std::vector<double> wc(M), ws(M);                    // cos / sin of 2 pi r / M
+    for (int r = 0; r < M; ++r) {
+        const cx_cs w = cx_cossin_frac(r, M);
+        wc[r] = w.c;
+        ws[r] = w.s;
+    }
+    for (int k = 0; k < M; ++k) {
+        double sr = 0.0, si = 0.0;
+        for (int m = 0, r = 0; m < M; ++m, r = (r + k) & (M - 1)) {   // r = k m mod M
+            sr += pr[m] * wc[r] + pi[m] * ws[r];                        // times exp(-2 pi i r / M)
+            si += pi[m] * wc[r] - pr[m] * ws[r];
+        }
+        filt[k] = make_float2((float)(sr / M), (float)(si / M));
+    }
+    ddm_status st = upload(&b->chirp, chirp);
+    if (st == DDM_OK) st = upload(&b->filt, filt);
+    if (st == DDM_OK) st = upload(&b->tw, pass_twiddles(M));
+    if (st == DDM_OK && M >= 2048) st = upload(&b->twin, pass_twiddles(M / 32));
+    return st;
 }
 
 std::vector<float2> pass_twiddles(int L) {
@@ -107,8 +162,11 @@ size_t workspace_bytes(const ddm_plan_desc& d) {
 
 ddm_status validate(const ddm_plan_desc* d) {
     if (!d) return DDM_ERR_INVALID_ARG;
-    if (!is_pow2(d->H) || !is_pow2(d->W) || d->H < 2 || d->W < 2) return DDM_ERR_INVALID_ARG;
+    if (d->H < 2 || d->W < 2 || d->H % 2 != 0 || d->W % 2 != 0) return DDM_ERR_INVALID_ARG;
     if (d->H > kMaxSide || d->W > kMaxSide) return DDM_ERR_UNSUPPORTED;
+    // sides that are not powers of two: Bluestein transforms of length M <= 2048
+    for (int side : {d->H, d->W})
+        if (!is_pow2(side) && side < kMinBluesteinSide) return DDM_ERR_UNSUPPORTED;
     if (d->N < 1) return DDM_ERR_INVALID_ARG;
     if (d->N > kMaxFrames) return DDM_ERR_UNSUPPORTED;
     if (d->dtype != DDM_IN_U16 && d->dtype != DDM_IN_F32) return DDM_ERR_INVALID_ARG;
@@ -133,6 +191,7 @@ ddm_status validate(const ddm_plan_desc* d) {
     if (d->kmax < 0) return DDM_ERR_INVALID_ARG;
     if (d->kmax > 0 && (d->kmax % 2 == 0 || d->kmax >= d->H / 2 || d->kmax >= d->W / 2))
         return DDM_ERR_INVALID_ARG;
+    if (d->kmax > 0 && (!is_pow2(d->H) || !is_pow2(d->W))) return DDM_ERR_UNSUPPORTED;
     if (d->q_begin != 0 || d->q_end != 0) {
         const int64_t nq = (int64_t)stored_wave_vectors(*d);
         if (d->q_begin < 0 || d->q_begin % 64 != 0 || d->q_end <= d->q_begin || d->q_end > nq)
@@ -226,8 +285,13 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
     }
     ddm_status st = DDM_OK;
     // pass twiddles of the three transform lengths
-    if (st == DDM_OK) st = upload(&p->tw_row, pass_twiddles(desc->W));
-    if (st == DDM_OK) st = upload(&p->tw_col, pass_twiddles(desc->H));
+    const bool pow2_w = is_pow2(desc->W), pow2_h = is_pow2(desc->H);
+    if (st == DDM_OK && pow2_w) st = upload(&p->tw_row, pass_twiddles(desc->W));
+    if (st == DDM_OK && pow2_h) st = upload(&p->tw_col, pass_twiddles(desc->H));
+    // Bluestein tables: rows when W is not a power of two; columns when either side is not
+    // (the power-of-two column kernel takes whole blocks of 16 stored columns)
+    if (st == DDM_OK && !pow2_w) st = make_bluestein(&p->blue_w, desc->W);
+    if (st == DDM_OK && !(pow2_w && pow2_h)) st = make_bluestein(&p->blue_h, desc->H);
     if (st == DDM_OK) st = upload(&p->tw_t, pass_twiddles(p->L));
     if (st == DDM_OK && p->L >= 2048) st = upload(&p->tw_tin, pass_twiddles(p->L / 32));
     if (st == DDM_OK && p->L >= 2048) {

@@ -6,6 +6,17 @@
 
 #include "../../include/ddm.h"
 
+// Bluestein tables of one non-power-of-two transform length n (M = 2^ceil(log2(2n - 1))):
+// chirp c_j = exp(i pi (j^2 mod 2n) / n), j < n; filter F = DFT_M(c circularly placed) / M;
+// pass twiddles of M (and of its inner M/32 transform when M >= 2048).
+struct ddm_bluestein {
+    int n = 0, M = 0;
+    float2* chirp = nullptr;
+    float2* filt = nullptr;
+    float2* tw = nullptr;
+    float2* twin = nullptr;
+};
+
 struct ddm_plan_s {
     ddm_plan_desc d;
     int L;              // transform length in time: smallest power of two >= N (M = 2L)
@@ -13,6 +24,7 @@ struct ddm_plan_s {
     int64_t n_q;        // H * (W/2 + 1)
     int64_t q0, q1;     // stored wave vectors covered by step two and the radial stage
     int kc;             // low-frequency restriction: kmax (0 = full half plane)
+    ddm_bluestein blue_w, blue_h;   // rows / columns of non-power-of-two length
     float2* crop_inter; // kc > 0: row-pass output [N][H][kc + 1]
     int device;
     int n_sm;
@@ -55,6 +67,8 @@ size_t spectrum_frame_stride(const ddm_plan_s* p);   // complex elements per fra
 ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
                           cudaStream_t s);
 ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s);
+cudaError_t launch_rows_bluestein(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
+cudaError_t launch_cols_bluestein(const ddm_plan_s* p, float2* spec, cudaStream_t s);
 ddm_status launch_radial(const ddm_plan_s* p, const float* D, float* Dr, int* counts, bool normalise,
                          cudaStream_t s);
 

@@ -309,7 +309,8 @@ ddm_status launch_spatial_fused(const ddm_plan_s* p, const void* frames, float2*
 bool rows_bulk_supported(const ddm_plan_s* p, const void* frames);
 cudaError_t launch_rows_bulk(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
 
-// Path: DDM_SPATIAL_FUSED (cluster kernel) where supported and asked for; otherwise the
+// Path: Bluestein transforms where a side is not a power of two; DDM_SPATIAL_FUSED (cluster
+// kernel) where supported and asked for; otherwise the
 // row pass (bulk-staged where rows allow it) followed by the column pass.
 ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
     if (p->kc > 0) {
@@ -318,6 +319,20 @@ ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
         if (!rows_bulk_supported(p, frames)) return DDM_ERR_UNSUPPORTED;
         if (launch_rows_bulk(p, frames, spec, s) != cudaSuccess) return DDM_ERR_CUDA;
         return dispatch_cols_crop(p, spec, s) == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
+    }
+    if (p->blue_h.M > 0) {
+        // a side that is not a power of two: Bluestein rows (or the power-of-two row pass),
+        // then Bluestein columns
+        cudaError_t e;
+        if (p->blue_w.M > 0)
+            e = launch_rows_bluestein(p, frames, spec, s);
+        else if (rows_bulk_supported(p, frames))
+            e = launch_rows_bulk(p, frames, spec, s);
+        else
+            e = (p->d.dtype == DDM_IN_U16) ? dispatch_rows<uint16_t>(p, frames, spec, s)
+                                           : dispatch_rows<float>(p, frames, spec, s);
+        if (e != cudaSuccess) return DDM_ERR_CUDA;
+        return launch_cols_bluestein(p, spec, s) == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
     }
     if (p->d.spatial_path == DDM_SPATIAL_FUSED && fused_spatial_supported(p) &&
         (reinterpret_cast<uintptr_t>(frames) & 15) == 0)

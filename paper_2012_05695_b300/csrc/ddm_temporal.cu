@@ -113,7 +113,7 @@ struct SyncGroup {
 struct TArgs {
     int N;            // frames
     int kd;           // directly evaluated trailing lags (<= 32, < N)
-    int H, Wh, lwh;   // for the storage -> public q map (lwh = log2 Wh)
+    int H, Wh;        // for the storage -> public q map
     int crop;         // low-frequency restriction: D rows in stored order
     int64_t n_q;      // stored wave vectors = spectrum frame stride
     int64_t q0, q1;   // stored wave vectors this launch covers: [q0, q1)
@@ -128,10 +128,13 @@ struct TArgs {
 
 // storage index -> public q = ky * (Wh + 1) + kx (Wh = W/2 is a power of two); with the
 // low-frequency restriction (crop) the stored order is the D order
-__device__ __forceinline__ int public_q(int s, int H, int Wh, int lwh, int crop) {
+__device__ __forceinline__ int public_q(int s, int H, int Wh, int crop) {
     if (crop) return s;
-    const int main = H << lwh;
-    if (s < main) return (s >> lwh) * (Wh + 1) + (s & (Wh - 1));
+    const int main = H * Wh;
+    if (s < main) {
+        const int ky = s / Wh;
+        return ky * (Wh + 1) + (s - ky * Wh);
+    }
     return (s - main) * (Wh + 1) + Wh;
 }
 
@@ -482,7 +485,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             if (tg < QG) {
                 const int64_t sr = q0 + gt * QG + tg;
                 if (sr < q1) {
-                    float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
+                    float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.crop) * N;
                     bulk_store(drow, ab + tg * DS, (uint32_t)N * (uint32_t)sizeof(float));
                 }
                 bulk_commit();
@@ -492,7 +495,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             for (int r = 0; r < QG; ++r) {
                 const int64_t sr = q0 + gt * QG + r;
                 if (sr >= q1) break;
-                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
+                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.crop) * N;
                 for (int m = tg; m < N; m += GT) drow[m] = ab[r * DS + m];
             }
         }
@@ -801,7 +804,7 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             if (tid < QG) {
                 const int64_t sr = q0 + tile * QG + tid;
                 if (sr < q1) {
-                    float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
+                    float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.crop) * N;
                     bulk_store(drow, ab + tid * DS, (uint32_t)N * (uint32_t)sizeof(float));
                 }
                 bulk_commit();
@@ -810,7 +813,7 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             for (int r = 0; r < QG; ++r) {
                 const int64_t sr = q0 + tile * QG + r;
                 if (sr >= q1) break;
-                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
+                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.crop) * N;
                 for (int m = tid; m < N; m += NT) drow[m] = ab[r * DS + m];
             }
         }
@@ -1055,7 +1058,7 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
         for (int r = 0; r < QT; ++r) {
             const int64_t sr = q0 + tile * QT + r;
             if (sr >= q1) break;
-            float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.lwh, a.crop) * N;
+            float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.crop) * N;
             for (int m = tid; m < N; m += NT) {
                 const float d = xf[r * DS + m];
                 bad |= !isfinite(d);
@@ -1105,7 +1108,6 @@ void fill_args(TArgs& a, const ddm_plan_s* p, float* D, int qt) {
     a.kd = p->kd;
     a.H = p->d.H;
     a.Wh = p->Wh;
-    a.lwh = ilog2(p->Wh);
     a.crop = p->kc > 0;
     a.vec4 = (p->d.N % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
     a.fix = (p->d.precision == DDM_PREC_FP32_FP64FIX) ? p->fix_lags : 0;

@@ -168,6 +168,12 @@ def ou_64x64x128(seed: int = 0) -> np.ndarray:
     return ou_stack(64, 64, 128, 0.5, gaussian_spectrum(0.3), 0.01, seed)
 
 
+def blobs_two_species_600x800(seed: int = 0, N: int = 3000, H: int = 600, W: int = 800) -> np.ndarray:
+    """600x800 uint16, N = 3000: 4000 blobs (sigma 2 px), half with D0 = 0.05 and half with
+    D0 = 0.8 px^2/frame, mean 2000, Poisson, a 1 % linear illumination drift over the stack."""
+    return blob_stack(H, W, N, 4000, 2.0, two_species_d0(4000, 0.05, 0.8), seed, drift=0.01)
+
+
 def blobs_512x512x1024(seed: int = 0, N: int = 1024, H: int = 512, W: int = 512) -> np.ndarray:
     """512x512 uint16, N = 1024, 3000 blobs (sigma 2 px), D0 = 0.2, mean 2000, Poisson."""
     return blob_stack(H, W, N, 3000, 2.0, 0.2, seed)

@@ -50,6 +50,9 @@ def test_desc_init_defaults():
 
 @pytest.mark.parametrize("field,value,status", [
     ("H", 3, B.DDM_ERR_INVALID_ARG),
+    ("H", 21, B.DDM_ERR_INVALID_ARG),             # odd sides: rows are transformed in pairs
+    ("H", 6, B.DDM_ERR_UNSUPPORTED),              # not a power of two and below 17
+    ("W", 12, B.DDM_ERR_UNSUPPORTED),
     ("W", 0, B.DDM_ERR_INVALID_ARG),
     ("H", 2048, B.DDM_ERR_UNSUPPORTED),
     ("N", 0, B.DDM_ERR_INVALID_ARG),
@@ -111,4 +114,12 @@ def test_valid_plan_without_device_is_a_cuda_error():
     d = _desc(8, 8, 4)
     h = ctypes.c_void_p()
     assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == B.DDM_ERR_CUDA
+    assert not h.value
+
+
+def test_low_frequency_window_needs_power_of_two_sides():
+    d = _desc(600, 800, 4)
+    d.kmax = 31
+    h = ctypes.c_void_p(123)
+    assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == B.DDM_ERR_UNSUPPORTED
     assert not h.value
