@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fit-compare", action="store_true")
+    ap.add_argument("--no-camera", action="store_true",
+                    help="skip the 600x800x3000 (non-power-of-two sides) timing")
     ap.add_argument("--kmax", type=int, default=63,
                     help="also time the low-frequency restriction |ky'|, kx <= kmax (0 = skip)")
     ap.add_argument("--shape", default=None,
@@ -278,6 +280,40 @@ def compare_fits(ddm, plan, Dr, stream):
     return out
 
 
+def time_camera(ddm, dev, stream, seed, H=600, W=800, N=3000, n_bins=500, steps=5):
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    frames = torch.randint(1800, 2201, (N, H, W), generator=g, device=dev, dtype=torch.int32).to(torch.uint16)
+    plan = ddm.Plan(H, W, N, dtype="u16", n_bins=n_bins)
+    spec = torch.empty(2 * N * plan.n_q, dtype=torch.float32, device=dev)
+    D = torch.empty(plan.n_q * N, dtype=torch.float32, device=dev)
+    Dr = torch.empty(n_bins * N, dtype=torch.float32, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for k in range(3 + steps):
+        e = ev[k - 3] if k >= 3 else None
+        if e:
+            e[0].record(stream)
+        plan.spatial_fft(frames, spec, stream)
+        if e:
+            e[1].record(stream)
+        plan.temporal_sf(spec, D, stream)
+        if e:
+            e[2].record(stream)
+        plan.azimuthal_average(D, Dr, None, stream)
+        if e:
+            e[3].record(stream)
+    torch.cuda.synchronize()
+    ms = [sum(e[j].elapsed_time(e[j + 1]) for e in ev) / steps for j in range(3)]
+    status = plan.last_device_status()
+    plan.close()
+    return {"workload": f"camera_{H}x{W}x{N}_u16", "H": H, "W": W, "N": N, "n_bins": n_bins,
+            "frames": "uniform counts 1800..2200 drawn on the device (timing only)",
+            "spatial": "Bluestein rows and columns, convolution length 2048",
+            "stages_ms": {"spatial_fft": ms[0], "temporal_sf": ms[1], "azimuthal_average": ms[2]},
+            "frames_per_s": N / (sum(ms) / 1e3), "device_status": status, "steps": steps}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -441,9 +477,9 @@ def run_ours(args):
     # ---- precision tiers on the same stack: the FP32+FP64-fixup temporal stage
     tiers = {"fp32": {"temporal_ms": tm_ms}}
     D_fix = None
-    fix_ok = N_FRAMES > 256                         # the tier is built for 257 <= N <= 1024
+    fix_ok = N_FRAMES > 256                         # the tier is built for 257 <= N <= 8192
     if rank == 0 and not fix_ok:
-        tiers["fp32_fp64fix"] = {"unsupported": f"N = {N_FRAMES}: the FP64-fixup tier needs 257 <= N <= 1024"}
+        tiers["fp32_fp64fix"] = {"unsupported": f"N = {N_FRAMES}: the FP64-fixup tier needs 257 <= N <= 8192"}
     if rank == 0 and fix_ok:
         plan_fix = ddm.Plan(H, W, N_FRAMES, dtype="u16", precision=ddm.DDM_PREC_FP32_FP64FIX)
         D_fix = torch.empty_like(D)
@@ -484,6 +520,14 @@ def run_ours(args):
                  "stages_ms": {"spatial_fft": ls[0], "temporal_sf": ls[1], "azimuthal_average": ls[2]},
                  "frames_per_s": N_FRAMES / (sum(ls) / 1e3)}
         del spec_c, D_c, lp
+
+    # ---- a camera whose sides are not powers of two (Bluestein spatial transforms) and a
+    # long stack: 600 x 800 x 3000 uint16.  Timing only (kernel times do not depend on the
+    # pixel values), so the counts are drawn on the device; the tests check this shape
+    # against the oracle on the two-species blob stack.
+    camera = None
+    if rank == 0 and not args.no_camera:
+        camera = time_camera(ddm, dev, stream, args.seed)
 
     # ---- fit of the 362 radial curves: plain LM vs LM seeded by the trained MLP
     fit_cmp = None
@@ -559,6 +603,8 @@ def run_ours(args):
     out["precision_tiers"] = tiers
     if low_q:
         out["low_q"] = low_q
+    if camera:
+        out["camera"] = camera
     if fit_cmp:
         out["fit"] = fit_cmp
     if e2e:
