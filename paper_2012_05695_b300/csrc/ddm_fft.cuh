@@ -263,6 +263,28 @@ struct AddrPaddedInterleaved {
     __device__ __forceinline__ int at(int hi, int lo) const { return (hi * (T + 1) + lo) * QT + ql; }
 };
 
+// QC columns per row (QC = P * QT), XOR-swizzled per row: column c of row idx sits at
+// idx * QC + (c ^ (CW * key(idx))), key = (idx ^ (idx / R)) mod (R / 2), CW = 32 / R.  For
+// the inner R-thread transform of fft_cyclic3 a warp touches R rows at once (consecutive
+// idx in pass 1, idx strided by R in pass 2) with CW consecutive columns each; the key
+// places those rows on different bank groups in both patterns (needs QT * R <= 32).
+template <int QC, int R>
+struct AddrInterleavedSwz {
+    int c;
+    static constexpr int CW = 32 / R, NPOS = R / 2;
+    static_assert(R >= 1 && (R & (R - 1)) == 0 && CW * R == 32, "R a power of two <= 32");
+    __device__ __forceinline__ static int key(int idx) {
+        if constexpr (NPOS > 1) return (idx ^ (idx / R)) & (NPOS - 1);
+        else return 0;
+    }
+    __device__ __forceinline__ int operator()(int idx) const { return idx * QC + (c ^ (CW * key(idx))); }
+    template <int T_>
+    __device__ __forceinline__ int at(int hi, int lo) const {
+        const int idx = hi * T_ + lo;
+        return idx * QC + (c ^ (CW * key(idx)));
+    }
+};
+
 struct SyncBlock {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
@@ -416,7 +438,8 @@ __device__ __forceinline__ void fft_cyclic3(float2 (&v)[32], int i, int ql, floa
 #pragma unroll
     for (int u = 0; u < P; ++u) v[u] = xs[hand(k1, r + R * u)];
     sync();                                   // handover read: the region takes the inner exchange
-    const AddrInterleaved<P * QT> inner{k1 * QT + ql};
+    static_assert(QT * R <= 32, "a warp covers whole groups of R threads");
+    const AddrInterleavedSwz<P * QT, R> inner{k1 * QT + ql};
     fft_cyclic<T, INV>(v, r, xs, inner, tw_in, sync);
 }
 

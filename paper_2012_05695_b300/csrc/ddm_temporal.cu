@@ -533,7 +533,8 @@ struct LShape {
     static constexpr int QG = NT / T;             // wave vectors per tile
     static constexpr int NWG = NT / 32;
     static constexpr int PAD = (QG == 2) ? 4 : 2; // (T + PAD) * QG = 8 mod 16: handover reads spread
-    static constexpr int DS = L + 4;              // D staging row stride (floats)
+    static constexpr int DS = L + 32 / QG;        // D staging row stride (floats): rows of the
+                                                  // QG wave vectors start on different banks
     static constexpr int BOX_T = 256, NBOX = L / BOX_T;
     static constexpr size_t XS_ELEMS = (size_t)P * (T + PAD) * QG > (size_t)L * QG
                                            ? (size_t)P * (T + PAD) * QG : (size_t)L * QG;
@@ -598,7 +599,10 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
     const int lane = tid & 31, wg = tid >> 5;
     const int s1 = fft3_sigma(i, P, R);          // forward output order
     const int s2 = fft3_sigma(s1, P, R);         // inverse output order (input order s1)
-    const float2 c_i = ci[i], c_s2 = ci[s2];
+    const float2 c_i = ci[i];
+    // inverse output, re-read in cyclic order: lag m at slot m ^ ((m / 8) mod 8), so that
+    // both the s2-order writes (lanes 8 lags apart) and the cyclic reads spread over banks
+    auto zslot = [](int m) { return m ^ ((m >> 3) & 7); };
     const TwiddleQuarter<L> tw1{twq};
     const int N = a.N, kd = a.kd;
     const int64_t q0 = a.q0, q1 = a.q1;
@@ -620,9 +624,10 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
         phase ^= 1u;
         return true;
     };
-    // trailing lag of this thread, if < N: the one it also holds in the combination's order
+    // trailing lag of this thread, if < N: the one it also holds in the combination's
+    // (cyclic) order, m = i + T u
     const int m_lo = N - kd;
-    const int m_tail = m_lo + ((s2 - m_lo) % T + T) % T;
+    const int m_tail = m_lo + ((i - m_lo) % T + T) % T;
 
     if ((int64_t)blockIdx.x < a.n_tiles) issue(blockIdx.x);
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
@@ -658,8 +663,9 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             if ((u & 7) == 7) hoist_fence();
         }
         fft_cyclic3<L, false, QG, PAD>(v, i, ql, xs, tw1, twi, SyncBlock{});
+        // parked by (u, i): the same thread reads it back with the same indices
 #pragma unroll
-        for (int u = 0; u < P; ++u) ab[(s1 + T * u) * QG + ql] = cabs2(v[u]);
+        for (int u = 0; u < P; ++u) ab[(u * T + i) * QG + ql] = cabs2(v[u]);
         // ---- even bins: DFT of g (the tile again)
         issue(tile);
         if (!wait()) { timed_out = true; break; }
@@ -672,22 +678,22 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
         fft_cyclic3<L, false, QG, PAD>(v, i, ql, xs, tw1, twi, SyncBlock{});
 #pragma unroll
         for (int u = 0; u < P; ++u) {
-            v[u] = make_float2(cabs2(v[u]), ab[(s1 + T * u) * QG + ql]);
+            v[u] = make_float2(cabs2(v[u]), ab[(u * T + i) * QG + ql]);
             if ((u & 7) == 7) hoist_fence();
         }
         // ---- inverse of Z = |X_even|^2 + i |X_odd|^2 (input order s1, output order s2)
         fft_cyclic3<L, true, QG, PAD>(v, s1, ql, xs, tw1, twi, SyncBlock{});
 #pragma unroll
-        for (int u = 0; u < P; ++u) xs[(s2 + T * u) * QG + ql] = v[u];
+        for (int u = 0; u < P; ++u) xs[zslot(s2 + T * u) * QG + ql] = v[u];
         __syncthreads();
         {
             const float scale = 0.25f / (float)L;
 #pragma unroll
             for (int u = 0; u < P; ++u) {
-                const int m = s2 + T * u;
-                const float2 z = v[u];
-                const float2 zr = xs[((L - m) & (L - 1)) * QG + ql];
-                const float2 w = cmul(c_s2, w64[u]);       // e^{-i pi m / L}
+                const int m = i + T * u;
+                const float2 z = xs[zslot(m) * QG + ql];
+                const float2 zr = xs[zslot((L - m) & (L - 1)) * QG + ql];
+                const float2 w = cmul(c_i, w64[u]);        // e^{-i pi m / L}
                 ab[m * QG + ql] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
                 if ((u & 7) == 7) hoist_fence();
             }
@@ -762,21 +768,21 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
 #pragma unroll
         for (int jj = 0; jj < P; ++jj) xf[(i * (P + 1) + jj) * QG + ql] = rowv[jj] + off;
         __syncthreads();
-        // FP64-fixup tier: lag m = s2 (1 <= s2 <= fix), held by this thread at u = 0, summed
+        // FP64-fixup tier: lag m = i (1 <= i <= fix), held by this thread at u = 0, summed
         // over the warps in FP64
         float fixd = 0.f;
-        const bool has_fix = FIXUP && a.fix > 0 && s2 >= 1 && s2 <= a.fix && s2 < N - kd;
+        const bool has_fix = FIXUP && a.fix > 0 && i >= 1 && i <= a.fix && i < N - kd;
         if (has_fix) {
             double sum = 0.0;
-            for (int w = 0; w < NWG; ++w) sum += (double)fixw[((s2 - 1) * NWG + w) * QG + ql];
-            fixd = (float)(sum / (double)(N - s2));
+            for (int w = 0; w < NWG; ++w) sum += (double)fixw[((i - 1) * NWG + w) * QG + ql];
+            fixd = (float)(sum / (double)(N - i));
             chk = fmaf(fixd, 0.f, chk);
         }
-        // ---- D(m) = (P1 + P2 - 2 Re C) / (N - m) for 0 < m < N - kd, m = s2 + T u
+        // ---- D(m) = (P1 + P2 - 2 Re C) / (N - m) for 0 < m < N - kd, m = i + T u
         float dv[P];
 #pragma unroll
         for (int u = 0; u < P; ++u) {
-            const int m = s2 + T * u;
+            const int m = i + T * u;
             float d = 0.f;
             if (m > 0 && m < N - kd) {
                 const int ta = N - 1 - m, tb2 = m - 1;
@@ -793,11 +799,11 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
         if (tile + gridDim.x < a.n_tiles) issue(tile + gridDim.x);
 #pragma unroll
         for (int u = 0; u < P; ++u) {
-            const int m = s2 + T * u;
+            const int m = i + T * u;
             if (m < N) ab[ql * DS + m] = dv[u];
         }
         if (m_tail < N) ab[ql * DS + m_tail] = tl;
-        if (has_fix) ab[ql * DS + s2] = fixd;
+        if (has_fix) ab[ql * DS + i] = fixd;
         if (a.vec4) fence_proxy_async();
         __syncthreads();
         if (a.vec4) {
