@@ -382,12 +382,20 @@ __device__ __forceinline__ void fft_cyclic_split(float2 (&v)[FftShape<L>::P], in
 __host__ __device__ constexpr int fft3_sigma(int j, int P, int R) { return j / R + P * (j % R); }
 
 // Exchange placement for the pass-1 -> inner handover: element (k1, i) of transform ql at
-// (k1 * (T + PAD) + i) * QT + ql; PAD makes the reads (four k1 per warp) use both halves of
-// the banks.  (P * (T + PAD) * QT elements.)
+// (k1 * (T + PAD) + j) * QT + ql.  PAD makes the reads (several k1 per warp) use both halves
+// of the banks.  With R >= 8, j = i ^ ((i >> 4) mod 8) spreads writes whose lanes hold
+// indices 32 / R apart (a transform fed in another one's output order: eight-way on one
+// bank otherwise); below that j = i (two-way at R = 4 measured cheaper than the swizzle's
+// per-element index arithmetic).  (P * (T + PAD) * QT elements.)
 template <int QT, int T, int PAD>
 struct AddrHandover {
     int ql;
-    __device__ __forceinline__ int operator()(int k1, int i) const { return (k1 * (T + PAD) + i) * QT + ql; }
+    static constexpr bool SWZ = T >= 256;
+    static_assert(T % 8 == 0, "the swizzle changes only the low three bits of i");
+    __device__ __forceinline__ int operator()(int k1, int i) const {
+        const int j = SWZ ? (i ^ ((i >> 4) & 7)) : i;
+        return (k1 * (T + PAD) + j) * QT + ql;
+    }
 };
 
 // xs holds max(P (T + PAD) QT, L QT) elements; QT transforms interleaved (transform ql).
@@ -406,16 +414,28 @@ struct TwiddleQuarter {
         const float s = (quad >= 2) ? -sq : sq;
         return make_float2(c, -s);                        // exp(-2 pi i j / L)
     }
+    // Lanes read q at indices k1 * i apart: a power-of-two factor of k1 folds them onto
+    // fewer banks.  fft_cyclic3 reads only odd k1 from the table and forms
+    // w^{k1 i} = w^{(k1 - 1) i} w^{i} for even k1 (one more rounding, no bank conflict).
+    static constexpr bool kEvenByProduct = true;
 };
 // ... or from a full table in host_pass_twiddles layout
 struct TwiddleTable {
+    static constexpr bool kEvenByProduct = false;
     const float2* t;
     int T;
     __device__ __forceinline__ float2 operator()(int k1, int i) const { return t[k1 * T + i]; }
 };
 
-template <int L, bool INV, int QT, int PAD, typename Tw1, typename Sync>
-__device__ __forceinline__ void fft_cyclic3(float2 (&v)[32], int i, int ql, float2* xs,
+// i_in: the thread's input index (it holds x[i_in + T u]); i_grp: the index whose group it
+// joins for the inner transform (k1 = i_grp / R, r = i_grp % R); the output is
+// X[sigma(i_grp) + T u].  i_in = i_grp = i is the plain transform.  A transform whose input
+// arrives in another transform's output order calls it with i_in = sigma(i), i_grp = i: no
+// reordering exchange, the lanes of a warp then read their pass-1 twiddles 32 / R index
+// steps apart, so PERM forms them by the recurrence w^{k1 i} = w^{(k1 - 1) i} w^{i} with a
+// table read every eight steps (at most seven extra roundings).
+template <int L, bool INV, int QT, int PAD, bool PERM = false, typename Tw1, typename Sync>
+__device__ __forceinline__ void fft_cyclic3(float2 (&v)[32], int i_in, int i_grp, int ql, float2* xs,
                                             Tw1 tw1, const float2* tw_in, Sync sync) {
     constexpr int P = 32;
     constexpr int T = L / P;
@@ -423,18 +443,28 @@ __device__ __forceinline__ void fft_cyclic3(float2 (&v)[32], int i, int ql, floa
     static_assert(T % P == 0 && R >= 2 && R <= P, "three-pass FFT: 2048 <= L <= 32768");
     const AddrHandover<QT, T, PAD> hand{ql};
     dft_reg<P, INV>(v);
+    float2 w_one = make_float2(1.f, 0.f), w_prev = w_one;
 #pragma unroll
     for (int k1 = 0; k1 < P; ++k1) {
         float2 a = v[k1];
         if (k1 > 0) {
-            const float2 w = tw1(k1, i);
+            float2 w;
+            if constexpr (PERM) {
+                w = (k1 == 1 || (k1 & 7) == 0) ? tw1(k1, i_in) : cmul(w_prev, w_one);
+            } else if constexpr (Tw1::kEvenByProduct) {
+                w = (k1 & 1) ? tw1(k1, i_in) : cmul(w_prev, w_one);
+            } else {
+                w = tw1(k1, i_in);
+            }
+            if (k1 == 1) w_one = w;
+            w_prev = w;
             a = INV ? cmul_conj(a, w) : cmul(a, w);
         }
-        xs[hand(k1, i)] = a;
+        xs[hand(k1, i_in)] = a;
         if ((k1 & 7) == 7) hoist_fence();
     }
     sync();
-    const int k1 = i / R, r = i % R;
+    const int k1 = i_grp / R, r = i_grp % R;
 #pragma unroll
     for (int u = 0; u < P; ++u) v[u] = xs[hand(k1, r + R * u)];
     sync();                                   // handover read: the region takes the inner exchange

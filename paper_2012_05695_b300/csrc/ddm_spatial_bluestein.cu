@@ -50,12 +50,12 @@ __device__ __forceinline__ int bluestein_core(float2 (&v)[32], int i, int ql, fl
     } else {
         constexpr int R = T / 32;
         const TwiddleTable tw1{tw, T};
-        fft_cyclic3<M, false, QT, C::PAD>(v, i, ql, xs, tw1, b.twin, sync);
+        fft_cyclic3<M, false, QT, C::PAD>(v, i, i, ql, xs, tw1, b.twin, sync);
         const int s1 = fft3_sigma(i, 32, R);
 #pragma unroll
         for (int u = 0; u < 32; ++u) v[u] = cmul(v[u], filt[s1 + T * u]);
-        fft_cyclic3<M, true, QT, C::PAD>(v, s1, ql, xs, tw1, b.twin, sync);
-        return fft3_sigma(s1, 32, R);
+        fft_cyclic3<M, true, QT, C::PAD, true>(v, s1, i, ql, xs, tw1, b.twin, sync);
+        return s1;
     }
 }
 

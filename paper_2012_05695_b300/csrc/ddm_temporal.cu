@@ -598,11 +598,14 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
     const int ql = tid % QG, i = tid / QG;
     const int lane = tid & 31, wg = tid >> 5;
     const int s1 = fft3_sigma(i, P, R);          // forward output order
-    const int s2 = fft3_sigma(s1, P, R);         // inverse output order (input order s1)
     const float2 c_i = ci[i];
-    // inverse output, re-read in cyclic order: lag m at slot m ^ ((m / 8) mod 8), so that
-    // both the s2-order writes (lanes 8 lags apart) and the cyclic reads spread over banks
-    auto zslot = [](int m) { return m ^ ((m >> 3) & 7); };
+    // Transform outputs come in the order s1 = sigma(i) (a warp's lanes 32 / R apart in
+    // index); they go back to cyclic order (m = i + T u) through xs, index m at slot
+    // m ^ ((m >> ZS) mod 8), which spreads both access patterns over the banks.
+    constexpr int ZS = R >= 8 ? 4 : 3;
+    auto zslot = [](int m) { return m ^ ((m >> ZS) & 7); };
+    static_assert(((T >> ZS) & 7) == 0, "zslot(j + T u) = zslot(j) + T u");
+    const int zs1 = zslot(s1), zsi = zslot(i);
     const TwiddleQuarter<L> tw1{twq};
     const int N = a.N, kd = a.kd;
     const int64_t q0 = a.q0, q1 = a.q1;
@@ -655,43 +658,54 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             const float rn = 1.0f / (float)N;
             mean = make_float2(mean.x * rn, mean.y * rn);
         }
-        // ---- odd bins: DFT of g(t) e^{-i pi t / L}; |.|^2 parked in ab by frequency
+        // ---- pass 0, odd bins: DFT of g(t) e^{-i pi t / L}, |.|^2 parked in ab;
+        //      pass 1, even bins: DFT of g (the tile again).  One copy of the transform's
+        //      code for both (the unrolled transform is most of the kernel's instructions).
+        bool tile_lost = false;
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 0) {
 #pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int t = i + T * u;
-            v[u] = (t < N) ? cmul(cmul(csub(v[u], mean), c_i), w64[u]) : make_float2(0.f, 0.f);
-            if ((u & 7) == 7) hoist_fence();
+                for (int u = 0; u < P; ++u) {
+                    const int t = i + T * u;
+                    v[u] = (t < N) ? cmul(cmul(csub(v[u], mean), c_i), w64[u]) : make_float2(0.f, 0.f);
+                    if ((u & 7) == 7) hoist_fence();
+                }
+            } else {
+                issue(tile);
+                if (!wait()) { tile_lost = true; break; }
+#pragma unroll
+                for (int u = 0; u < P; ++u) {
+                    const int t = i + T * u;
+                    v[u] = (t < N) ? csub(xs[t * QG + ql], mean) : make_float2(0.f, 0.f);
+                }
+                __syncthreads();
+            }
+            fft_cyclic3<L, false, QG, PAD>(v, i, i, ql, xs, tw1, twi, SyncBlock{});
+            if (pass == 0) {
+                // parked by (u, i): the same thread reads it back with the same indices
+#pragma unroll
+                for (int u = 0; u < P; ++u) ab[(u * T + i) * QG + ql] = cabs2(v[u]);
+            }
         }
-        fft_cyclic3<L, false, QG, PAD>(v, i, ql, xs, tw1, twi, SyncBlock{});
-        // parked by (u, i): the same thread reads it back with the same indices
-#pragma unroll
-        for (int u = 0; u < P; ++u) ab[(u * T + i) * QG + ql] = cabs2(v[u]);
-        // ---- even bins: DFT of g (the tile again)
-        issue(tile);
-        if (!wait()) { timed_out = true; break; }
-#pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int t = i + T * u;
-            v[u] = (t < N) ? csub(xs[t * QG + ql], mean) : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        fft_cyclic3<L, false, QG, PAD>(v, i, ql, xs, tw1, twi, SyncBlock{});
+        if (tile_lost) { timed_out = true; break; }
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             v[u] = make_float2(cabs2(v[u]), ab[(u * T + i) * QG + ql]);
             if ((u & 7) == 7) hoist_fence();
         }
-        // ---- inverse of Z = |X_even|^2 + i |X_odd|^2 (input order s1, output order s2)
-        fft_cyclic3<L, true, QG, PAD>(v, s1, ql, xs, tw1, twi, SyncBlock{});
+        // ---- inverse of Z = |X_even|^2 + i |X_odd|^2: input order s1, groups by i, output
+        // order s1
+        fft_cyclic3<L, true, QG, PAD, true>(v, s1, i, ql, xs, tw1, twi, SyncBlock{});
 #pragma unroll
-        for (int u = 0; u < P; ++u) xs[zslot(s2 + T * u) * QG + ql] = v[u];
+        for (int u = 0; u < P; ++u) xs[(zs1 + T * u) * QG + ql] = v[u];
         __syncthreads();
         {
             const float scale = 0.25f / (float)L;
 #pragma unroll
             for (int u = 0; u < P; ++u) {
                 const int m = i + T * u;
-                const float2 z = xs[zslot(m) * QG + ql];
+                const float2 z = xs[(zsi + T * u) * QG + ql];
                 const float2 zr = xs[zslot((L - m) & (L - 1)) * QG + ql];
                 const float2 w = cmul(c_i, w64[u]);        // e^{-i pi m / L}
                 ab[m * QG + ql] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
