@@ -75,7 +75,7 @@ typedef struct ddm_plan_desc {
                           Bluestein's chirp-z transform (a cyclic convolution of length
                           2^ceil(log2(2n - 1)) <= 2048); odd sides DDM_ERR_INVALID_ARG,
                           non-powers of two below 17 DDM_ERR_UNSUPPORTED */
-    int N;             /* number of frames, 1 .. 8192 */
+    int N;             /* number of frames, 1 .. 16384 */
     int dtype;         /* ddm_dtype */
     int precision;     /* ddm_precision */
     int M;             /* temporal pad length; 0 = N_2 of Eq. B4.  Any M >= 2N-1 gives

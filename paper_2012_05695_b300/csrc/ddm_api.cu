@@ -27,7 +27,7 @@ constexpr int kRadialChunk = 64;   // wave vectors per radial partial sum
 
 constexpr int kMaxSide = 1024;
 constexpr int kMinBluesteinSide = 17;   // smallest side that is not a power of two: M >= 64
-constexpr int kMaxFrames = 8192;
+constexpr int kMaxFrames = 16384;
 
 // floor(n_bins * |q| / (pi sqrt 2)) with |q| = 2 pi sqrt((ky/H)^2 + (kx/W)^2):
 // the largest b with (b H W)^2 <= 2 n_bins^2 (ky^2 W^2 + kx^2 H^2), in exact integers.
@@ -175,7 +175,7 @@ ddm_status validate(const ddm_plan_desc* d) {
     if (d->precision == DDM_PREC_FP32_FP64FIX) {
         // built for the time transforms whose tiles arrive whole in shared memory
         const int Lf = 1 << ilog2(d->N);
-        if (Lf < 512) return DDM_ERR_UNSUPPORTED;
+        if (Lf < 512 || Lf > 8192) return DDM_ERR_UNSUPPORTED;
         if (d->fix_lags > 8) return DDM_ERR_UNSUPPORTED;
     }
     if (d->subtract_ref != 0 && d->subtract_ref != 1) return DDM_ERR_INVALID_ARG;
@@ -307,6 +307,16 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
         }
         for (int u = 0; u < 32; ++u) {
             const cx_cs cs = cx_cossin_frac(u, 64);
+            t.push_back(make_float2((float)cs.c, (float)-cs.s));
+        }
+        // two-level pass-1 twiddles of the L = 16384 kernel: exp(-2 pi i b / L), b < 64, and
+        // exp(-2 pi i 64 a / L), a < L / 64
+        for (int b = 0; b < 64; ++b) {
+            const cx_cs cs = cx_cossin_frac(b, L);
+            t.push_back(make_float2((float)cs.c, (float)-cs.s));
+        }
+        for (int a2 = 0; a2 < L / 64; ++a2) {
+            const cx_cs cs = cx_cossin_frac(64L * a2, L);
             t.push_back(make_float2((float)cs.c, (float)-cs.s));
         }
         st = upload(&p->tw_long, t);

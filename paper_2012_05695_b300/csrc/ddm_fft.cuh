@@ -383,17 +383,17 @@ __host__ __device__ constexpr int fft3_sigma(int j, int P, int R) { return j / R
 
 // Exchange placement for the pass-1 -> inner handover: element (k1, i) of transform ql at
 // (k1 * (T + PAD) + j) * QT + ql.  PAD makes the reads (several k1 per warp) use both halves
-// of the banks.  With R >= 8, j = i ^ ((i >> 4) mod 8) spreads writes whose lanes hold
-// indices 32 / R apart (a transform fed in another one's output order: eight-way on one
-// bank otherwise); below that j = i (two-way at R = 4 measured cheaper than the swizzle's
-// per-element index arithmetic).  (P * (T + PAD) * QT elements.)
+// of the banks.  With R >= 8, an XOR of j with higher bits of i spreads writes whose lanes
+// hold indices 32 / R apart (a transform fed in another one's output order: eight-way on
+// one bank otherwise); below that j = i (two-way at R = 4 measured cheaper than the
+// swizzle's per-element index arithmetic).  (P * (T + PAD) * QT elements.)
 template <int QT, int T, int PAD>
 struct AddrHandover {
     int ql;
-    static constexpr bool SWZ = T >= 256;
-    static_assert(T % 8 == 0, "the swizzle changes only the low three bits of i");
+    static_assert(T % 16 == 0, "the swizzle changes only the low bits of i");
     __device__ __forceinline__ int operator()(int k1, int i) const {
-        const int j = SWZ ? (i ^ ((i >> 4) & 7)) : i;
+        // T = 512 (R = 16, one transform per warp row): lanes 32 apart, j = i ^ ((i >> 5) mod 16)
+        const int j = T >= 512 ? (i ^ ((i >> 5) & 15)) : T == 256 ? (i ^ ((i >> 4) & 7)) : i;
         return (k1 * (T + PAD) + j) * QT + ql;
     }
 };

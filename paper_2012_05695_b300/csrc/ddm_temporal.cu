@@ -847,6 +847,243 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
 }
 
 // =====================================================================================
+// L = 16384 (N up to 16384, M = 32768): one wave vector per 512-thread CTA.  Its time
+// sequence (128 KB) and the transform's exchange (128 KB) cannot share shared memory, so
+// the sequence goes straight from global memory (L2) into registers, three times (odd
+// bins, even bins, power sums); shared memory holds the exchange, the parked |X_odd|^2
+// and small twiddle tables.  Pass-1 twiddles from two 2.5 KB tables (w^j = hi[j / 64]
+// lo[j mod 64]) instead of a 32 KB quarter wave.
+// =====================================================================================
+template <int L_>
+struct TwiddleTwoLevel {
+    static constexpr bool kEvenByProduct = true;
+    const float2* lo;   // exp(-2 pi i b / L), b < 64
+    const float2* hi;   // exp(-2 pi i 64 a / L), a < L / 64
+    __device__ __forceinline__ float2 operator()(int k1, int i) const {
+        const int j = (k1 * i) & (L_ - 1);
+        return cmul(hi[j >> 6], lo[j & 63]);
+    }
+};
+
+struct XLShape {
+    static constexpr int LOG2L = 14, L = 1 << LOG2L;
+    static constexpr int P = 32, T = L / P, R = T / P;
+    static constexpr int NT = T, NWG = NT / 32;
+    static constexpr int PAD = 0;                          // the handover's swizzle suffices
+    static constexpr size_t OFF_LO = 0;                                      // 64
+    static constexpr size_t OFF_HI = OFF_LO + 64 * sizeof(float2);           // L / 64
+    static constexpr size_t OFF_TWI = OFF_HI + (size_t)(L / 64) * sizeof(float2);  // T (inner pass)
+    static constexpr size_t OFF_W64 = OFF_TWI + (size_t)T * sizeof(float2);  // 32
+    static constexpr size_t OFF_RED = OFF_W64 + 32 * sizeof(float2);         // NWG float2 + 2 NWG float
+    static constexpr size_t OFF_XS = (OFF_RED + (size_t)NWG * 16 + 1023) & ~size_t(1023);
+    static constexpr size_t XS_ELEMS = (size_t)P * (T + PAD);                // handover; >= L
+    static constexpr size_t OFF_AB = OFF_XS + XS_ELEMS * sizeof(float2);
+    static constexpr size_t BYTES = OFF_AB + (size_t)L * sizeof(float);
+    static_assert(XS_ELEMS >= (size_t)L && (size_t)(L + L / 32) * sizeof(float) <= XS_ELEMS * sizeof(float2),
+                  "exchange holds the transform and the padded power sums");
+    static_assert(BYTES + 1024 <= 233472, "one CTA per SM");
+};
+
+struct XLTables {
+    const float2* lo;
+    const float2* hi;
+    const float2* inner;     // pass twiddles of the inner T-point transform
+    const float2* ci;        // exp(-i pi i / L), i < T
+    const float2* w64;       // exp(-i pi u / 32), u < 32
+};
+
+__global__ void __launch_bounds__(XLShape::NT, 1)
+temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs a, XLTables tb) {
+    using C = XLShape;
+    constexpr int L = C::L, P = C::P, T = C::T, R = C::R, NWG = C::NWG;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float2* lo = reinterpret_cast<float2*>(smem_raw + C::OFF_LO);
+    float2* hi = reinterpret_cast<float2*>(smem_raw + C::OFF_HI);
+    float2* twi = reinterpret_cast<float2*>(smem_raw + C::OFF_TWI);
+    float2* w64 = reinterpret_cast<float2*>(smem_raw + C::OFF_W64);
+    float2* red2 = reinterpret_cast<float2*>(smem_raw + C::OFF_RED);
+    float* wsum = reinterpret_cast<float*>(smem_raw + C::OFF_RED + NWG * sizeof(float2));
+    float2* xs = reinterpret_cast<float2*>(smem_raw + C::OFF_XS);
+    float* xf = reinterpret_cast<float*>(xs);
+    float* ab = reinterpret_cast<float*>(smem_raw + C::OFF_AB);
+
+    const int i = threadIdx.x;
+    const int lane = i & 31, wg = i >> 5;
+    for (int k = i; k < 64; k += C::NT) lo[k] = tb.lo[k];
+    for (int k = i; k < L / 64; k += C::NT) hi[k] = tb.hi[k];
+    for (int k = i; k < T; k += C::NT) twi[k] = tb.inner[k];
+    if (i < 32) w64[i] = tb.w64[i];
+    const float2 c_i = tb.ci[i];
+    const int s1 = fft3_sigma(i, P, R);                    // transform output order
+    // inverse output back to cyclic order through xs: index m at slot m ^ ((m >> 5) mod 16)
+    auto zslot = [](int m) { return m ^ ((m >> 5) & 15); };
+    static_assert(((T >> 5) & 15) == 0, "zslot(j + T u) = zslot(j) + T u");
+    const int zs1 = zslot(s1), zsi = zslot(i);
+    const TwiddleTwoLevel<L> tw1{lo, hi};
+    const int N = a.N, kd = a.kd;
+    const int64_t nq = a.n_q;
+    const int m_lo = N - kd;
+    const int m_tail = m_lo + ((i - m_lo) % T + T) % T;    // this thread's trailing lag, if < N
+    float chk = 0.f;
+
+    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+        const int64_t sq = a.q0 + tile;                    // stored wave vector
+        const float2* xg = spec + sq;                      // x(t) = xg[t * n_q]
+        __syncthreads();                                   // previous wave vector's reads done
+        // ---- time sequence (thread i holds t = i + T u) and its mean
+        float2 v[P];
+        float2 part = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int t = i + T * u;
+            v[u] = (t < N) ? __ldg(xg + (int64_t)t * nq) : make_float2(0.f, 0.f);
+            part = cadd(part, v[u]);
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
+            part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
+        }
+        if (lane == 0) red2[wg] = part;
+        __syncthreads();
+        float2 mean = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < NWG; ++w) mean = cadd(mean, red2[w]);
+        {
+            const float rn = 1.0f / (float)N;
+            mean = make_float2(mean.x * rn, mean.y * rn);
+        }
+        // ---- pass 0, odd bins: DFT of g(t) e^{-i pi t / L}, |.|^2 parked in ab;
+        //      pass 1, even bins: DFT of g (read again)
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+                const int t = i + T * u;
+                if (pass == 0)
+                    v[u] = (t < N) ? cmul(cmul(csub(v[u], mean), c_i), w64[u]) : make_float2(0.f, 0.f);
+                else
+                    v[u] = (t < N) ? csub(__ldg(xg + (int64_t)t * nq), mean) : make_float2(0.f, 0.f);
+                if ((u & 7) == 7) hoist_fence();
+            }
+            fft_cyclic3<L, false, 1, C::PAD>(v, i, i, 0, xs, tw1, twi, SyncBlock{});
+            if (pass == 0) {
+#pragma unroll
+                for (int u = 0; u < P; ++u) ab[u * T + i] = cabs2(v[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            v[u] = make_float2(cabs2(v[u]), ab[u * T + i]);
+            if ((u & 7) == 7) hoist_fence();
+        }
+        // ---- inverse of Z = |X_even|^2 + i |X_odd|^2 (input order s1), then Re C in cyclic
+        // order from the 2-for-1 split, into ab by lag
+        fft_cyclic3<L, true, 1, C::PAD, true>(v, s1, i, 0, xs, tw1, twi, SyncBlock{});
+#pragma unroll
+        for (int u = 0; u < P; ++u) xs[zs1 + T * u] = v[u];
+        __syncthreads();
+        {
+            const float scale = 0.25f / (float)L;
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+                const int m = i + T * u;
+                const float2 z = xs[zsi + T * u];
+                const float2 zr = xs[zslot((L - m) & (L - 1))];
+                const float2 w = cmul(c_i, w64[u]);        // e^{-i pi m / L}
+                ab[m] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
+                if ((u & 7) == 7) hoist_fence();
+            }
+        }
+        __syncthreads();                                   // xs becomes the power sums
+        // ---- |g - mean|^2 at padded positions t + t / 32, then the power sums of Eq. B1 as
+        // a split scan: frames below h = 32 hc (hc = ceil(N / 64) chunks of 32) hold the
+        // inclusive prefix sum, frames from h on the inclusive suffix sum, so that
+        // P1(m) = S(N - m) and P2(m) = S(N) - S(m) are each read either directly or as S(N)
+        // minus at most about half of it (no S(N) - S(m) cancellation at the largest lags,
+        // where it grows like N / (N - m)).  Thread i owns frames 32 i .. 32 i + 31.
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int t = i + T * u;
+            xf[t + (t >> 5)] = (t < N) ? cabs2(csub(__ldg(xg + (int64_t)t * nq), mean)) : 0.f;
+        }
+        __syncthreads();
+        const int hc = (N + 63) / 64, h = 32 * hc;
+        const bool fwd = i < hc;
+        float acc = 0.f;
+        if (fwd) {
+#pragma unroll
+            for (int jj = 0; jj < P; ++jj) acc += xf[i * (P + 1) + jj];
+        } else {
+#pragma unroll
+            for (int jj = P - 1; jj >= 0; --jj) acc += xf[i * (P + 1) + jj];
+        }
+        const float acc_f = fwd ? acc : 0.f, acc_b = fwd ? 0.f : acc;
+        float inc_f = acc_f, inc_b = acc_b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float yf = __shfl_up_sync(0xffffffffu, inc_f, o);
+            const float yb = __shfl_down_sync(0xffffffffu, inc_b, o);
+            if (lane >= o) inc_f += yf;
+            if (lane + o < 32) inc_b += yb;
+        }
+        if (lane == 31) wsum[wg] = inc_f;
+        if (lane == 0) wsum[NWG + wg] = inc_b;
+        __syncthreads();
+        float off = fwd ? inc_f - acc_f : inc_b - acc_b, total = 0.f;
+#pragma unroll
+        for (int w = 0; w < NWG; ++w) {
+            const float xf_w = wsum[w], xb_w = wsum[NWG + w];
+            if (fwd && w < wg) off += xf_w;
+            if (!fwd && w > wg) off += xb_w;
+            total += xf_w + xb_w;
+        }
+        if (fwd) {
+#pragma unroll
+            for (int jj = 0; jj < P; ++jj) {               // same order of additions as acc
+                off += xf[i * (P + 1) + jj];
+                xf[i * (P + 1) + jj] = off;
+            }
+        } else {
+#pragma unroll
+            for (int jj = P - 1; jj >= 0; --jj) {
+                off += xf[i * (P + 1) + jj];
+                xf[i * (P + 1) + jj] = off;
+            }
+        }
+        // ---- the trailing lags by direct differences (Eq. 1): at most kd pairs each
+        float tl = 0.f;
+        if (m_tail < N) {
+            for (int t = 0; t < N - m_tail; ++t)
+                tl += cabs2(csub(__ldg(xg + (int64_t)(t + m_tail) * nq), __ldg(xg + (int64_t)t * nq)));
+            tl *= __frcp_rn((float)(N - m_tail));
+            chk = fmaf(tl, 0.f, chk);
+        }
+        __syncthreads();
+        // ---- D(m) = (P1 + P2 - 2 Re C) / (N - m), m = i + T u, straight to global memory
+        float* drow = D + (int64_t)public_q((int)sq, a.H, a.Wh, a.crop) * N;
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            const int m = i + T * u;
+            if (m >= N) break;
+            float d = 0.f;
+            if (m > 0 && m < m_lo) {
+                // P1 = sum over t < N - m, P2 = sum over t >= m (Eq. B1)
+                const int ta = N - 1 - m;
+                const float p1 = ta < h ? xf[ta + (ta >> 5)] : total - xf[(ta + 1) + ((ta + 1) >> 5)];
+                const float p2 = m >= h ? xf[m + (m >> 5)] : total - xf[(m - 1) + ((m - 1) >> 5)];
+                d = (p1 + p2 - 2.f * ab[m]) * __frcp_rn((float)(N - m));
+                chk = fmaf(d, 0.f, chk);
+            } else if (m >= m_lo) {
+                d = tl;                                    // m == m_tail
+            }
+            drow[m] = d;
+        }
+    }
+    if (chk != chk) atomicOr(a.status, 1u);
+}
+
+// =====================================================================================
 // L <= 256: one group per CTA, per-thread loads
 // =====================================================================================
 template <int LOG2L>
@@ -1187,6 +1424,29 @@ ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaSt
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 
+ddm_status launch_xl(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
+    using C = XLShape;
+    if (!p->tw_tin || !p->tw_long || p->L != C::L) return DDM_ERR_INVALID_ARG;
+    TArgs a;
+    fill_args(a, p, D, 1);
+    auto k = temporal_sf_xl_kernel;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
+        cudaSuccess)
+        return DDM_ERR_CUDA;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return DDM_ERR_CUDA;
+    XLTables tb;                                  // tw_long: [L/4] quarter, [T] ci, [32] w64, [64] lo, [L/64] hi
+    tb.ci = p->tw_long + p->L / 4;
+    tb.w64 = tb.ci + p->L / 32;
+    tb.lo = tb.w64 + 32;
+    tb.hi = tb.lo + 64;
+    tb.inner = p->tw_tin;
+    const int64_t grid = a.n_tiles < p->n_sm ? a.n_tiles : p->n_sm;
+    k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(spec, D, a, tb);
+    return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
+}
+
 template <int LOG2L>
 ddm_status launch_small(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
     using C = TShape<LOG2L>;
@@ -1223,6 +1483,7 @@ ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cu
         case 11: return fix ? launch_long<11, true>(p, spec, D, s) : launch_long<11, false>(p, spec, D, s);
         case 12: return fix ? launch_long<12, true>(p, spec, D, s) : launch_long<12, false>(p, spec, D, s);
         case 13: return fix ? launch_long<13, true>(p, spec, D, s) : launch_long<13, false>(p, spec, D, s);
+        case 14: return fix ? DDM_ERR_UNSUPPORTED : launch_xl(p, spec, D, s);
         default: return DDM_ERR_UNSUPPORTED;
     }
 }

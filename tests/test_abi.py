@@ -56,7 +56,7 @@ def test_desc_init_defaults():
     ("W", 0, B.DDM_ERR_INVALID_ARG),
     ("H", 2048, B.DDM_ERR_UNSUPPORTED),
     ("N", 0, B.DDM_ERR_INVALID_ARG),
-    ("N", 9000, B.DDM_ERR_UNSUPPORTED),
+    ("N", 16385, B.DDM_ERR_UNSUPPORTED),
     ("dtype", 7, B.DDM_ERR_INVALID_ARG),
     ("precision", 9, B.DDM_ERR_INVALID_ARG),
     ("precision", 1, B.DDM_ERR_UNSUPPORTED),      # FP64 fixup needs N >= 257
@@ -120,6 +120,14 @@ def test_valid_plan_without_device_is_a_cuda_error():
 def test_low_frequency_window_needs_power_of_two_sides():
     d = _desc(600, 800, 4)
     d.kmax = 31
+    h = ctypes.c_void_p(123)
+    assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == B.DDM_ERR_UNSUPPORTED
+    assert not h.value
+
+
+def test_fp64_fixup_tier_stops_at_8192_frames():
+    d = _desc(8, 8, 9000)
+    d.precision = B.DDM_PREC_FP32_FP64FIX
     h = ctypes.c_void_p(123)
     assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == B.DDM_ERR_UNSUPPORTED
     assert not h.value

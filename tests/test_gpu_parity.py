@@ -83,7 +83,8 @@ def test_spatial_fft_without_reference_subtraction():
 
 # ------------------------------------------------------------------ step two alone
 @pytest.mark.parametrize("N", [1, 2, 3, 5, 17, 33, 64, 100, 128, 255, 256, 511, 1000, 1024,
-                               1025, 1500, 2048, 2049, 3000, 4096, 5000, 8192])
+                               1025, 1500, 2048, 2049, 3000, 4096, 5000, 8192, 8193,
+                               12000, 16384])
 def test_temporal_matches_oracle(N):
     """Oracle spectrum in, oracle D out: isolates the time-sequence stage."""
     import torch
@@ -112,6 +113,8 @@ def test_temporal_matches_oracle(N):
     (32, 16, 2000, "f32", {"q_begin": 64, "q_end": 200}),    # L = 2048, a wave-vector range
     (32, 32, 2500, "u16", {"kmax": 7}),                      # L = 4096 on the cropped store
     (16, 16, 6000, "u16", {}),                               # L = 8192, one 512-thread CTA per SM
+    (8, 16, 16384, "u16", {}),                               # L = 16384: one wave vector per CTA
+    (16, 16, 10000, "f32", {"q_begin": 64, "q_end": 140}),   # L = 16384 on a wave-vector range
 ])
 def test_long_sequences_end_to_end(H, W, N, dtype, kw):
     """N above 1024: the three-pass time transforms, from frames to D."""
