@@ -60,6 +60,8 @@ def parse_args():
     ap.add_argument("--no-fit-compare", action="store_true")
     ap.add_argument("--no-camera", action="store_true",
                     help="skip the 600x800x3000 (non-power-of-two sides) timing")
+    ap.add_argument("--no-long", action="store_true",
+                    help="skip the 512x512x16384 (longest stacks) timing")
     ap.add_argument("--kmax", type=int, default=63,
                     help="also time the low-frequency restriction |ky'|, kx <= kmax (0 = skip)")
     ap.add_argument("--shape", default=None,
@@ -314,6 +316,39 @@ def time_camera(ddm, dev, stream, seed, H=600, W=800, N=3000, n_bins=500, steps=
             "frames_per_s": N / (sum(ms) / 1e3), "device_status": status, "steps": steps}
 
 
+def time_long_stack(ddm, dev, stream, seed, H=512, W=512, N=16384, steps=3):
+    """The paper's longest stacks (N = 2^14, 16384-point time transforms): step one and
+    step two on device-drawn counts (timing only)."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    frames = torch.randint(1800, 2201, (N, H, W), generator=g, device=dev, dtype=torch.int32).to(torch.uint16)
+    plan = ddm.Plan(H, W, N, dtype="u16")
+    spec = torch.empty(2 * N * plan.n_q, dtype=torch.float32, device=dev)
+    D = torch.empty(plan.n_q * N, dtype=torch.float32, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for k in range(2 + steps):
+        e = ev[k - 2] if k >= 2 else None
+        if e:
+            e[0].record(stream)
+        plan.spatial_fft(frames, spec, stream)
+        if e:
+            e[1].record(stream)
+        plan.temporal_sf(spec, D, stream)
+        if e:
+            e[2].record(stream)
+    torch.cuda.synchronize()
+    ms = [sum(e[j].elapsed_time(e[j + 1]) for e in ev) / steps for j in range(2)]
+    status = plan.last_device_status()
+    plan.close()
+    del frames, spec, D
+    torch.cuda.empty_cache()
+    return {"workload": f"long_{H}x{W}x{N}_u16", "H": H, "W": W, "N": N,
+            "frames": "uniform counts 1800..2200 drawn on the device (timing only)",
+            "stages_ms": {"spatial_fft": ms[0], "temporal_sf": ms[1]},
+            "frames_per_s": N / (sum(ms) / 1e3), "device_status": status, "steps": steps}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -477,7 +512,7 @@ def run_ours(args):
     # ---- precision tiers on the same stack: the FP32+FP64-fixup temporal stage
     tiers = {"fp32": {"temporal_ms": tm_ms}}
     D_fix = None
-    fix_ok = N_FRAMES > 256                         # the tier is built for 257 <= N <= 8192
+    fix_ok = 256 < N_FRAMES <= 8192                 # the tier is built for 257 <= N <= 8192
     if rank == 0 and not fix_ok:
         tiers["fp32_fp64fix"] = {"unsupported": f"N = {N_FRAMES}: the FP64-fixup tier needs 257 <= N <= 8192"}
     if rank == 0 and fix_ok:
@@ -528,6 +563,9 @@ def run_ours(args):
     camera = None
     if rank == 0 and not args.no_camera:
         camera = time_camera(ddm, dev, stream, args.seed)
+    long_stack = None
+    if rank == 0 and not args.no_long:
+        long_stack = time_long_stack(ddm, dev, stream, args.seed)
 
     # ---- fit of the 362 radial curves: plain LM vs LM seeded by the trained MLP
     fit_cmp = None
@@ -605,6 +643,8 @@ def run_ours(args):
         out["low_q"] = low_q
     if camera:
         out["camera"] = camera
+    if long_stack:
+        out["long_stack"] = long_stack
     if fit_cmp:
         out["fit"] = fit_cmp
     if e2e:
