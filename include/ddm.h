@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define DDM_ABI_VERSION 3
+#define DDM_ABI_VERSION 4
 
 typedef enum ddm_status {
     DDM_OK = 0,
@@ -71,10 +71,10 @@ typedef enum ddm_spatial_path {
 
 typedef struct ddm_plan_desc {
     int H, W;          /* frame height and width in pixels, even, 2..1024: powers of two
-                          by radix-2 register FFTs; other even sides from 18 by
+                          by radix-2 register FFTs; other even sides (6 .. 1022) by
                           Bluestein's chirp-z transform (a cyclic convolution of length
-                          2^ceil(log2(2n - 1)) <= 2048); odd sides DDM_ERR_INVALID_ARG,
-                          non-powers of two below 17 DDM_ERR_UNSUPPORTED */
+                          max(32, 2^ceil(log2(2n - 1))) <= 2048); odd sides
+                          DDM_ERR_INVALID_ARG, sides above 1024 DDM_ERR_UNSUPPORTED */
     int N;             /* number of frames, 1 .. 16384 */
     int dtype;         /* ddm_dtype */
     int precision;     /* ddm_precision */
@@ -152,6 +152,14 @@ ddm_status ddm_plan_n_q(ddm_plan p, int64_t* n_q);
  * DDM_ERR_NUMERIC, or DDM_ERR_TIMEOUT if a tile copy did not complete within its bounded
  * wait); reading it resets it to DDM_OK.  Synchronise the stream first. */
 ddm_status ddm_plan_last_device_status(ddm_plan p, ddm_status* out);
+
+/* Test hook for the bounded device waits (no plan needed, current device, synchronous):
+ * launches one CTA that arms a tile barrier for bytes no copy will deliver and waits on it
+ * with the same bounded routine the time kernels use, giving up after cap_cycles SM clock
+ * cycles (clamped to 1e3 .. 4e9).  Returns DDM_ERR_TIMEOUT when the bound fired and was
+ * reported through a status word (the expected outcome), DDM_OK if the wait had completed
+ * (never, unless the bound is broken), DDM_ERR_CUDA on a launch or copy failure. */
+ddm_status ddm_selftest_bounded_wait(long long cap_cycles);
 
 /* ---- the hot path ---------------------------------------------------------------- */
 

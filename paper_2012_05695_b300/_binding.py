@@ -85,6 +85,7 @@ def lib():
         "ddm_plan_set_workspace": (st, [vp, vp, ctypes.c_size_t]),
         "ddm_plan_n_q": (st, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ddm_plan_last_device_status": (st, [vp, ctypes.POINTER(ctypes.c_int)]),
+        "ddm_selftest_bounded_wait": (st, [ctypes.c_longlong]),
         "ddm_spatial_fft": (st, [vp, vp, vp, vp]),
         "ddm_temporal_sf": (st, [vp, vp, vp, vp]),
         "ddm_structure_function": (st, [vp, vp, vp, vp]),
@@ -123,6 +124,12 @@ def status_string(s: int) -> str:
         return lib().ddm_status_string(int(s)).decode()
     except Exception:
         return "status %d" % int(s)
+
+
+def selftest_bounded_wait(cap_cycles: int) -> int:
+    """Run the library's bounded-wait test hook; returns the status (DDM_ERR_TIMEOUT
+    expected)."""
+    return int(lib().ddm_selftest_bounded_wait(int(cap_cycles)))
 
 
 def _check(status: int, where: str):

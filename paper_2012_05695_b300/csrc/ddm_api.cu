@@ -26,7 +26,6 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 constexpr int kRadialChunk = 64;   // wave vectors per radial partial sum
 
 constexpr int kMaxSide = 1024;
-constexpr int kMinBluesteinSide = 17;   // smallest side that is not a power of two: M >= 64
 constexpr int kMaxFrames = 16384;
 
 // floor(n_bins * |q| / (pi sqrt 2)) with |q| = 2 pi sqrt((ky/H)^2 + (kx/W)^2):
@@ -97,7 +96,7 @@ std::vector<float2> pass_twiddles(int L);
 // Bluestein tables for length n, built in double precision: the chirp's angle reduced
 // exactly (j^2 mod 2n in integers), the filter's DFT by a plain O(M^2) sum in double.
 ddm_status make_bluestein(ddm_bluestein* b, int n) {
-    int M = 1;
+    int M = 32;                                          // the register FFTs' smallest shape
     while (M < 2 * n - 1) M *= 2;
     b->n = n;
     b->M = M;
@@ -135,7 +134,7 @@ ddm_status make_bluestein(ddm_bluestein* b, int n) {
     }
     ddm_status st = upload(&b->chirp, chirp);
     if (st == DDM_OK) st = upload(&b->filt, filt);
-    if (st == DDM_OK) st = upload(&b->tw, pass_twiddles(M));
+    if (st == DDM_OK && M >= 64) st = upload(&b->tw, pass_twiddles(M));
     if (st == DDM_OK && M >= 2048) st = upload(&b->twin, pass_twiddles(M / 32));
     return st;
 }
@@ -164,9 +163,6 @@ ddm_status validate(const ddm_plan_desc* d) {
     if (!d) return DDM_ERR_INVALID_ARG;
     if (d->H < 2 || d->W < 2 || d->H % 2 != 0 || d->W % 2 != 0) return DDM_ERR_INVALID_ARG;
     if (d->H > kMaxSide || d->W > kMaxSide) return DDM_ERR_UNSUPPORTED;
-    // sides that are not powers of two: Bluestein transforms of length M <= 2048
-    for (int side : {d->H, d->W})
-        if (!is_pow2(side) && side < kMinBluesteinSide) return DDM_ERR_UNSUPPORTED;
     if (d->N < 1) return DDM_ERR_INVALID_ARG;
     if (d->N > kMaxFrames) return DDM_ERR_UNSUPPORTED;
     if (d->dtype != DDM_IN_U16 && d->dtype != DDM_IN_F32) return DDM_ERR_INVALID_ARG;
@@ -434,6 +430,26 @@ ddm_status ddm_plan_n_q(ddm_plan p, int64_t* n_q) {
     if (!check_plan(p) || !n_q) return DDM_ERR_INVALID_ARG;
     *n_q = p->n_q;
     return DDM_OK;
+}
+
+ddm_status ddm_selftest_bounded_wait(long long cap_cycles) {
+    if (cap_cycles < 1000) cap_cycles = 1000;
+    if (cap_cycles > 4000000000LL) cap_cycles = 4000000000LL;
+    unsigned* word = nullptr;
+    if (cudaMalloc(&word, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return DDM_ERR_CUDA;
+    }
+    unsigned h = 0;
+    bool ok = cudaMemset(word, 0, sizeof(unsigned)) == cudaSuccess &&
+              launch_wait_selftest(word, cap_cycles, nullptr) == cudaSuccess &&
+              cudaMemcpy(&h, word, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess;
+    cudaFree(word);
+    if (!ok) {
+        cudaGetLastError();
+        return DDM_ERR_CUDA;
+    }
+    return (h & 2u) ? DDM_ERR_TIMEOUT : DDM_OK;
 }
 
 ddm_status ddm_plan_last_device_status(ddm_plan p, ddm_status* out) {

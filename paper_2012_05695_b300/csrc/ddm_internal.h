@@ -67,6 +67,7 @@ size_t spectrum_frame_stride(const ddm_plan_s* p);   // complex elements per fra
 ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
                           cudaStream_t s);
 ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s);
+cudaError_t launch_wait_selftest(unsigned* status, long long cap_cycles, cudaStream_t s);
 cudaError_t launch_rows_bluestein(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
 cudaError_t launch_cols_bluestein(const ddm_plan_s* p, float2* spec, cudaStream_t s);
 ddm_status launch_radial(const ddm_plan_s* p, const float* D, float* Dr, int* counts, bool normalise,

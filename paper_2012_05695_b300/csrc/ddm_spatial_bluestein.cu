@@ -24,11 +24,12 @@ struct BShape {
     static constexpr bool THREE = M >= 2048;               // three-pass transform
     static constexpr int PAD = THREE ? ((QT == 2) ? 4 : 2) : 0;
     // exchange elements: the transforms' scratch, also the staging and the partner step
-    static constexpr size_t X_TWO = (size_t)(M + M / T) * QT;            // AddrPaddedInterleaved
+    static constexpr size_t X_TWO = T > 1 ? (size_t)(M + M / T) * QT     // AddrPaddedInterleaved
+                                          : (size_t)M * QT;              // (M = 32: no exchange)
     static constexpr size_t X_THREE = (size_t)P * (T + PAD) * QT > (size_t)M * QT
                                           ? (size_t)P * (T + PAD) * QT : (size_t)M * QT;
     static constexpr size_t XE = THREE ? X_THREE : X_TWO;
-    static_assert(M >= 64 && M <= 2048 && QT * T == NT, "Bluestein lengths 17 .. 1024");
+    static_assert(M >= 32 && M <= 2048 && QT * T == NT, "Bluestein lengths 3 .. 1024");
 };
 
 // The cyclic convolution at the heart of Bluestein's identity, on QT transforms held in
@@ -77,7 +78,7 @@ row_bluestein_kernel(const In* __restrict__ frames, float2* __restrict__ spec, i
     for (int k = tid; k < W; k += NT) chirp[k] = b.chirp[k];
     for (int k = tid; k < M; k += NT) {
         filt[k] = b.filt[k];
-        tw[k] = b.tw[k];
+        if constexpr (C::T > 1) tw[k] = b.tw[k];         // M = 32: one thread per transform
     }
     const int t = blockIdx.y;
     const int pair0 = blockIdx.x * QT;
@@ -152,7 +153,7 @@ col_bluestein_kernel(float2* __restrict__ spec, int H, int Wh, size_t frame_stri
     for (int k = tid; k < H; k += NT) chirp[k] = b.chirp[k];
     for (int k = tid; k < M; k += NT) {
         filt[k] = b.filt[k];
-        tw[k] = b.tw[k];
+        if constexpr (C::T > 1) tw[k] = b.tw[k];         // M = 32: one thread per transform
     }
     __syncthreads();
     const int ql = tid % QT, i = tid / QT;
@@ -238,6 +239,7 @@ cudaError_t cols_t(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
 template <typename In>
 cudaError_t rows_dispatch(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
     switch (p->blue_w.M) {
+        case 32: return rows_t<32, In>(p, frames, spec, s);
         case 64: return rows_t<64, In>(p, frames, spec, s);
         case 128: return rows_t<128, In>(p, frames, spec, s);
         case 256: return rows_t<256, In>(p, frames, spec, s);
@@ -257,6 +259,7 @@ cudaError_t launch_rows_bluestein(const ddm_plan_s* p, const void* frames, float
 
 cudaError_t launch_cols_bluestein(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
     switch (p->blue_h.M) {
+        case 32: return cols_t<32>(p, spec, s);
         case 64: return cols_t<64>(p, spec, s);
         case 128: return cols_t<128>(p, spec, s);
         case 256: return cols_t<256>(p, spec, s);

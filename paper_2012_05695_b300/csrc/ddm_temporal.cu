@@ -83,13 +83,31 @@ __device__ __forceinline__ void bulk_wait_read_all() {
 }
 // this thread's bulk copies are complete
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-// A bounded wait on a tile barrier: about two seconds of polling, then false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// A bounded wait on a tile barrier: about two seconds of polling (cap in SM clock cycles),
+// then false.
+constexpr long long kWaitCapCycles = 4000000000LL;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long cap = kWaitCapCycles) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > 4000000000LL) return false;
+        if (clock64() - t0 > cap) return false;
     }
     return true;
+}
+
+// Test hook for the bounded waits: one CTA arms a barrier for 16 bytes that no copy will
+// deliver, waits on it with the given bound (the same routine every tile wait uses), and
+// reports the give-up in the status word the way the time kernels do (bit 2).
+__global__ void wait_selftest_kernel(unsigned* status, long long cap) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect_tx(&bar, 16u);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, cap);
+    if (__syncthreads_or(ok ? 0 : 1) && threadIdx.x == 0) atomicOr(status, 2u);
 }
 // true in every thread of the group of `nthreads` on named barrier `id` if pred holds in any
 __device__ __forceinline__ bool group_any(bool pred, int id, int nthreads) {
@@ -1462,6 +1480,11 @@ ddm_status launch_small(const ddm_plan_s* p, const float2* spec, float* D, cudaS
 }
 
 }  // namespace
+
+cudaError_t launch_wait_selftest(unsigned* status, long long cap_cycles, cudaStream_t s) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(status, cap_cycles);
+    return cudaGetLastError();
+}
 
 ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
     const bool fix = p->d.precision == DDM_PREC_FP32_FP64FIX;

@@ -12,7 +12,7 @@ from conftest import cuda_available
 
 def test_library_is_in_tree_and_loads():
     L = ddm.lib()
-    assert L.ddm_abi_version() == 3
+    assert L.ddm_abi_version() == 4
     assert ddm.LIB_PATH.endswith("paper_2012_05695_b300/_lib/libddm_b300.so")
 
 
@@ -51,8 +51,8 @@ def test_desc_init_defaults():
 @pytest.mark.parametrize("field,value,status", [
     ("H", 3, B.DDM_ERR_INVALID_ARG),
     ("H", 21, B.DDM_ERR_INVALID_ARG),             # odd sides: rows are transformed in pairs
-    ("H", 6, B.DDM_ERR_UNSUPPORTED),              # not a power of two and below 17
-    ("W", 12, B.DDM_ERR_UNSUPPORTED),
+    ("W", 7, B.DDM_ERR_INVALID_ARG),
+    ("W", 1030, B.DDM_ERR_UNSUPPORTED),           # above 1024
     ("W", 0, B.DDM_ERR_INVALID_ARG),
     ("H", 2048, B.DDM_ERR_UNSUPPORTED),
     ("N", 0, B.DDM_ERR_INVALID_ARG),

@@ -23,6 +23,9 @@ def _frames(N, H, W, dtype, seed):
 
 
 @pytest.mark.parametrize("H,W,N,dtype", [
+    (8, 12, 3, "f32"),         # M = 32: one thread per transform, no exchange
+    (6, 10, 2, "u16"),
+    (14, 16, 3, "f32"),        # columns M = 32, power-of-two rows
     (18, 22, 3, "f32"),        # M = 64 both ways
     (100, 64, 4, "u16"),       # columns M = 256, power-of-two rows
     (64, 100, 3, "f32"),       # rows M = 256, power-of-two columns through Bluestein (M = 128)
@@ -67,6 +70,7 @@ def test_spatial_fft_non_power_of_two_without_reference_subtraction():
 
 
 @pytest.mark.parametrize("H,W,N,dtype", [
+    (8, 12, 3, "f32"), (6, 10, 1, "u16"), (12, 8, 50, "u16"),
     (18, 22, 40, "f32"), (48, 80, 64, "u16"), (100, 64, 33, "u16"), (64, 100, 20, "f32"),
     (250, 250, 100, "f32"), (600, 800, 16, "u16"),
 ])
