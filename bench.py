@@ -60,6 +60,7 @@ def parse_args():
     ap.add_argument("--no-fit-compare", action="store_true")
     ap.add_argument("--no-camera", action="store_true",
                     help="skip the 600x800x3000 (non-power-of-two sides) timing")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 tier timing")
     ap.add_argument("--no-long", action="store_true",
                     help="skip the 512x512x16384 (longest stacks) timing")
     ap.add_argument("--kmax", type=int, default=63,
@@ -529,6 +530,23 @@ def run_ours(args):
         torch.cuda.synchronize()
         tiers["fp32_fp64fix"] = {"temporal_ms": f0.elapsed_time(f1) / 10, "fix_lags": 8}
 
+    # ---- the FP64 tier on the same stack (the precision sweep's reference): both steps
+    D64 = None
+    if rank == 0 and N_FRAMES <= 4096 and not args.no_fp64:
+        plan64 = ddm.Plan(H, W, N_FRAMES, dtype="u16", precision=ddm.DDM_PREC_FP64)
+        D64 = torch.empty_like(D)
+        plan64.structure_function(frames, D64, stream)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(3):
+            plan64.structure_function(frames, D64, stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        tiers["fp64"] = {"structure_function_ms": f0.elapsed_time(f1) / 3,
+                         "device_status": plan64.last_device_status()}
+        plan64.close()
+
     # ---- the low-frequency restriction (Sec. 3) on the same stack: cropped spectrum store
     low_q = None
     if rank == 0 and args.kmax > 0 and args.kmax < min(H, W) // 2:
@@ -594,6 +612,10 @@ def run_ours(args):
         ref = D_or[..., 1:9]
         tiers["fp32"]["max_rel_err"] = max_err
         tiers["fp32"]["small_lag_err_rel_D"] = float(np.max(np.abs(Dg[..., 1:9] - ref) / ref))
+        if D64 is not None:
+            D6 = D64.view(H, W // 2 + 1, N_FRAMES)[:, cols, :].cpu().numpy()
+            tiers["fp64"]["max_rel_err"] = oracle.scaled_error(D6, D_or, s_q)
+            tiers["fp64"]["small_lag_err_rel_D"] = float(np.max(np.abs(D6[..., 1:9] - ref) / ref))
         if D_fix is not None:
             Df = D_fix.view(H, W // 2 + 1, N_FRAMES)[:, cols, :].cpu().numpy()
             tiers["fp32_fp64fix"]["max_rel_err"] = oracle.scaled_error(Df, D_or, s_q)

@@ -51,13 +51,20 @@ typedef enum ddm_status {
 
 typedef enum ddm_dtype { DDM_IN_U16 = 0, DDM_IN_F32 = 1 } ddm_dtype;
 
-/* Arithmetic of the structure-function path.  Both tiers transform in FP32. */
+/* Arithmetic of the structure-function path. */
 typedef enum ddm_precision {
     DDM_PREC_FP32 = 0,   /* FP32 transforms, prefix and suffix sums and combination */
-    DDM_PREC_FP32_FP64FIX = 1 /* as FP32, plus: lags 1..fix_lags recomputed by direct
+    DDM_PREC_FP32_FP64FIX = 1, /* as FP32, plus: lags 1..fix_lags recomputed by direct
                                  differences (Eq. 1), FP32 over each thread's 32 frames and
                                  FP64 across threads: no cancellation against the power
                                  sums.  This build: 257 <= N <= 8192, fix_lags <= 8 */
+    DDM_PREC_FP64 = 2    /* everything in FP64 on the GPU (the precision sweep's reference
+                            tier; D is still written as float32): spatial and time
+                            transforms, power sums and combination.  About 1/64 of the
+                            FP32 rate.  This build: power-of-two sides, N <= 4096, kmax = 0,
+                            the whole wave-vector range, ddm_structure_function only
+                            (ddm_spatial_fft / ddm_temporal_sf / the static entry return
+                            DDM_ERR_UNSUPPORTED: the spectrum workspace is complex128) */
 } ddm_precision;
 
 /* Kernels of step one.  Both give the same spectrum (to FP32 rounding). */

@@ -5,6 +5,6 @@ per wave vector, D(q, m) from running sums of |F|^2 and the autocorrelation of t
 zero-padded time sequence, behind the C ABI of include/ddm.h.  This package is the thin
 Python binding; all arithmetic runs in the CUDA library built from csrc/.
 """
-from ._binding import (DDM_IN_F32, DDM_IN_U16, DDM_PREC_FP32, DDM_PREC_FP32_FP64FIX,  # noqa: F401
+from ._binding import (DDM_IN_F32, DDM_IN_U16, DDM_PREC_FP32, DDM_PREC_FP32_FP64FIX, DDM_PREC_FP64,  # noqa: F401
                        DDMError, LIB_PATH, MLP, Plan, header_functions, lib, selftest_bounded_wait,
                        spectrum_index_map, status_string)

@@ -66,6 +66,8 @@ void free_plan(ddm_plan_s* p) {
     cudaFree(p->tw_col);
     cudaFree(p->tw_t);
     cudaFree(p->tw_tin);
+    cudaFree(p->tw64);
+    cudaFree(p->tw64_half);
     for (ddm_bluestein* b : {&p->blue_w, &p->blue_h}) {
         cudaFree(b->chirp);
         cudaFree(b->filt);
@@ -155,7 +157,8 @@ size_t stored_wave_vectors(const ddm_plan_desc& d) {
 
 size_t workspace_bytes(const ddm_plan_desc& d) {
     const size_t nq = stored_wave_vectors(d);
-    const size_t b = nq * (size_t)d.N * sizeof(float2);
+    const size_t elem = d.precision == DDM_PREC_FP64 ? 2 * sizeof(double) : sizeof(float2);
+    const size_t b = nq * (size_t)d.N * elem;
     return (b + 255) & ~(size_t)255;
 }
 
@@ -166,7 +169,8 @@ ddm_status validate(const ddm_plan_desc* d) {
     if (d->N < 1) return DDM_ERR_INVALID_ARG;
     if (d->N > kMaxFrames) return DDM_ERR_UNSUPPORTED;
     if (d->dtype != DDM_IN_U16 && d->dtype != DDM_IN_F32) return DDM_ERR_INVALID_ARG;
-    if (d->precision != DDM_PREC_FP32 && d->precision != DDM_PREC_FP32_FP64FIX)
+    if (d->precision != DDM_PREC_FP32 && d->precision != DDM_PREC_FP32_FP64FIX &&
+        d->precision != DDM_PREC_FP64)
         return DDM_ERR_INVALID_ARG;
     if (d->precision == DDM_PREC_FP32_FP64FIX) {
         // built for the time transforms whose tiles arrive whole in shared memory
@@ -193,6 +197,7 @@ ddm_status validate(const ddm_plan_desc* d) {
         if (d->q_begin < 0 || d->q_begin % 64 != 0 || d->q_end <= d->q_begin || d->q_end > nq)
             return DDM_ERR_INVALID_ARG;
     }
+    if (d->precision == DDM_PREC_FP64 && !fp64_supported(*d)) return DDM_ERR_UNSUPPORTED;
     if (d->max_workspace_bytes != 0 && workspace_bytes(*d) > d->max_workspace_bytes)
         return DDM_ERR_OOM;
     return DDM_OK;
@@ -388,6 +393,25 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
             st = DDM_ERR_OOM;
         }
     }
+    if (st == DDM_OK && desc->precision == DDM_PREC_FP64) {
+        // FP64 tier: exp(-2 pi i r / n_tab), r < n_tab / 2, n_tab = max(W, H, L); and
+        // exp(-i pi t / L), t < L
+        int n_tab = desc->W > desc->H ? desc->W : desc->H;
+        if (p->L > n_tab) n_tab = p->L;
+        p->fp64_ntab = n_tab;
+        std::vector<double2> t64(n_tab / 2 > 0 ? n_tab / 2 : 1), h64(p->L);
+        for (int r = 0; r < n_tab / 2; ++r) {
+            const cx_cs cs = cx_cossin_frac(r, n_tab);
+            t64[r] = make_double2(cs.c, -cs.s);
+        }
+        if (n_tab < 2) t64[0] = make_double2(1.0, 0.0);
+        for (int t = 0; t < p->L; ++t) {
+            const cx_cs cs = cx_cossin_frac(t, 2L * p->L);
+            h64[t] = make_double2(cs.c, -cs.s);
+        }
+        st = upload(&p->tw64, t64);
+        if (st == DDM_OK) st = upload(&p->tw64_half, h64);
+    }
     if (st == DDM_OK) st = make_fit_tables(p);
     if (st == DDM_OK) {
         if (cudaMalloc(&p->dev_status, sizeof(unsigned)) != cudaSuccess ||
@@ -466,12 +490,14 @@ ddm_status ddm_plan_last_device_status(ddm_plan p, ddm_status* out) {
 
 ddm_status ddm_spatial_fft(ddm_plan p, const void* frames, float* spectrum, void* stream) {
     if (!check_plan(p) || !frames || !spectrum) return DDM_ERR_INVALID_ARG;
+    if (p->d.precision == DDM_PREC_FP64) return DDM_ERR_UNSUPPORTED;
     if ((reinterpret_cast<uintptr_t>(spectrum) & 7) != 0) return DDM_ERR_INVALID_ARG;
     return launch_spatial(p, frames, reinterpret_cast<float2*>(spectrum), (cudaStream_t)stream);
 }
 
 ddm_status ddm_temporal_sf(ddm_plan p, const float* spectrum, float* D, void* stream) {
     if (!check_plan(p) || !spectrum || !D) return DDM_ERR_INVALID_ARG;
+    if (p->d.precision == DDM_PREC_FP64) return DDM_ERR_UNSUPPORTED;
     if ((reinterpret_cast<uintptr_t>(spectrum) & 7) != 0 || (reinterpret_cast<uintptr_t>(D) & 3) != 0)
         return DDM_ERR_INVALID_ARG;
     return launch_temporal(p, reinterpret_cast<const float2*>(spectrum), D, (cudaStream_t)stream);
@@ -482,6 +508,7 @@ ddm_status ddm_structure_function(ddm_plan p, const void* frames, float* D, void
     if ((reinterpret_cast<uintptr_t>(D) & 3) != 0) return DDM_ERR_INVALID_ARG;
     ddm_status st = ensure_workspace(p);
     if (st != DDM_OK) return st;
+    if (p->d.precision == DDM_PREC_FP64) return launch_fp64(p, frames, p->workspace, D, (cudaStream_t)stream);
     float2* spec = reinterpret_cast<float2*>(p->workspace);
     st = launch_spatial(p, frames, spec, (cudaStream_t)stream);
     if (st != DDM_OK) return st;

@@ -25,6 +25,9 @@ struct ddm_plan_s {
     int64_t q0, q1;     // stored wave vectors covered by step two and the radial stage
     int kc;             // low-frequency restriction: kmax (0 = full half plane)
     ddm_bluestein blue_w, blue_h;   // rows / columns of non-power-of-two length
+    double2* tw64 = nullptr;        // FP64 tier: exp(-2 pi i r / fp64_ntab), r < fp64_ntab / 2
+    double2* tw64_half = nullptr;   // FP64 tier: exp(-i pi t / L), t < L
+    int fp64_ntab = 0;
     float2* crop_inter; // kc > 0: row-pass output [N][H][kc + 1]
     int device;
     int n_sm;
@@ -67,6 +70,8 @@ size_t spectrum_frame_stride(const ddm_plan_s* p);   // complex elements per fra
 ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
                           cudaStream_t s);
 ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s);
+bool fp64_supported(const ddm_plan_desc& d);
+ddm_status launch_fp64(const ddm_plan_s* p, const void* frames, void* workspace, float* D, cudaStream_t s);
 cudaError_t launch_wait_selftest(unsigned* status, long long cap_cycles, cudaStream_t s);
 cudaError_t launch_rows_bluestein(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
 cudaError_t launch_cols_bluestein(const ddm_plan_s* p, float2* spec, cudaStream_t s);

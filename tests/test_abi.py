@@ -59,6 +59,7 @@ def test_desc_init_defaults():
     ("N", 16385, B.DDM_ERR_UNSUPPORTED),
     ("dtype", 7, B.DDM_ERR_INVALID_ARG),
     ("precision", 9, B.DDM_ERR_INVALID_ARG),
+    ("precision", 3, B.DDM_ERR_INVALID_ARG),
     ("precision", 1, B.DDM_ERR_UNSUPPORTED),      # FP64 fixup needs N >= 257
     ("M", 6, B.DDM_ERR_INVALID_ARG),          # M < 2N - 1 wraps around (App. B)
     ("M", 7, B.DDM_ERR_UNSUPPORTED),          # legal pad length, not the one built
@@ -130,4 +131,18 @@ def test_fp64_fixup_tier_stops_at_8192_frames():
     d.precision = B.DDM_PREC_FP32_FP64FIX
     h = ctypes.c_void_p(123)
     assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == B.DDM_ERR_UNSUPPORTED
+    assert not h.value
+
+
+@pytest.mark.parametrize("H,W,N,kmax,status", [
+    (8, 8, 5000, 0, B.DDM_ERR_UNSUPPORTED),        # FP64 tier: N <= 4096
+    (8, 12, 16, 0, B.DDM_ERR_UNSUPPORTED),         # FP64 tier: power-of-two sides
+    (16, 16, 16, 3, B.DDM_ERR_UNSUPPORTED),        # FP64 tier: the full half plane
+])
+def test_fp64_tier_limits(H, W, N, kmax, status):
+    d = _desc(H, W, N)
+    d.precision = B.DDM_PREC_FP64
+    d.kmax = kmax
+    h = ctypes.c_void_p(123)
+    assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == status
     assert not h.value
