@@ -77,11 +77,12 @@ typedef enum ddm_spatial_path {
 } ddm_spatial_path;
 
 typedef struct ddm_plan_desc {
-    int H, W;          /* frame height and width in pixels, even, 2..1024: powers of two
+    int H, W;          /* frame height and width in pixels, even: powers of two 2..2048
                           by radix-2 register FFTs; other even sides (6 .. 1022) by
                           Bluestein's chirp-z transform (a cyclic convolution of length
                           max(32, 2^ceil(log2(2n - 1))) <= 2048); odd sides
-                          DDM_ERR_INVALID_ARG, sides above 1024 DDM_ERR_UNSUPPORTED */
+                          DDM_ERR_INVALID_ARG, other sides above 1024
+                          DDM_ERR_UNSUPPORTED */
     int N;             /* number of frames, 1 .. 16384 */
     int dtype;         /* ddm_dtype */
     int precision;     /* ddm_precision */

@@ -25,7 +25,7 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 constexpr int kRadialChunk = 64;   // wave vectors per radial partial sum
 
-constexpr int kMaxSide = 1024;
+constexpr int kMaxSide = 2048;         // powers of two; other even sides up to 1022
 constexpr int kMaxFrames = 16384;
 
 // floor(n_bins * |q| / (pi sqrt 2)) with |q| = 2 pi sqrt((ky/H)^2 + (kx/W)^2):
@@ -141,6 +141,15 @@ ddm_status make_bluestein(ddm_bluestein* b, int n) {
     return st;
 }
 
+// A power-of-two side of 2048 points: the Bluestein kernels' three-pass transform alone.
+ddm_status make_direct(ddm_bluestein* b, int n) {
+    b->n = n;
+    b->M = n;
+    ddm_status st = upload(&b->tw, pass_twiddles(n));
+    if (st == DDM_OK) st = upload(&b->twin, pass_twiddles(n / 32));
+    return st;
+}
+
 std::vector<float2> pass_twiddles(int L) {
     std::vector<float2> t;
     if (L >= 64) {
@@ -166,6 +175,7 @@ ddm_status validate(const ddm_plan_desc* d) {
     if (!d) return DDM_ERR_INVALID_ARG;
     if (d->H < 2 || d->W < 2 || d->H % 2 != 0 || d->W % 2 != 0) return DDM_ERR_INVALID_ARG;
     if (d->H > kMaxSide || d->W > kMaxSide) return DDM_ERR_UNSUPPORTED;
+    if ((!is_pow2(d->H) && d->H > 1024) || (!is_pow2(d->W) && d->W > 1024)) return DDM_ERR_UNSUPPORTED;
     if (d->N < 1) return DDM_ERR_INVALID_ARG;
     if (d->N > kMaxFrames) return DDM_ERR_UNSUPPORTED;
     if (d->dtype != DDM_IN_U16 && d->dtype != DDM_IN_F32) return DDM_ERR_INVALID_ARG;
@@ -191,7 +201,8 @@ ddm_status validate(const ddm_plan_desc* d) {
     if (d->kmax < 0) return DDM_ERR_INVALID_ARG;
     if (d->kmax > 0 && (d->kmax % 2 == 0 || d->kmax >= d->H / 2 || d->kmax >= d->W / 2))
         return DDM_ERR_INVALID_ARG;
-    if (d->kmax > 0 && (!is_pow2(d->H) || !is_pow2(d->W))) return DDM_ERR_UNSUPPORTED;
+    if (d->kmax > 0 && (!is_pow2(d->H) || !is_pow2(d->W) || d->H > 1024 || d->W > 1024))
+        return DDM_ERR_UNSUPPORTED;
     if (d->q_begin != 0 || d->q_end != 0) {
         const int64_t nq = (int64_t)stored_wave_vectors(*d);
         if (d->q_begin < 0 || d->q_begin % 64 != 0 || d->q_end <= d->q_begin || d->q_end > nq)
@@ -287,12 +298,15 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
     ddm_status st = DDM_OK;
     // pass twiddles of the three transform lengths
     const bool pow2_w = is_pow2(desc->W), pow2_h = is_pow2(desc->H);
-    if (st == DDM_OK && pow2_w) st = upload(&p->tw_row, pass_twiddles(desc->W));
-    if (st == DDM_OK && pow2_h) st = upload(&p->tw_col, pass_twiddles(desc->H));
+    if (st == DDM_OK && pow2_w && desc->W <= 1024) st = upload(&p->tw_row, pass_twiddles(desc->W));
+    if (st == DDM_OK && pow2_h && desc->H <= 1024) st = upload(&p->tw_col, pass_twiddles(desc->H));
     // Bluestein tables: rows when W is not a power of two; columns when either side is not
-    // (the power-of-two column kernel takes whole blocks of 16 stored columns)
+    // (the power-of-two column kernel takes whole blocks of 16 stored columns).  Sides of
+    // 2048: the same kernels' 2048-point transform alone (no chirp).
     if (st == DDM_OK && !pow2_w) st = make_bluestein(&p->blue_w, desc->W);
-    if (st == DDM_OK && !(pow2_w && pow2_h)) st = make_bluestein(&p->blue_h, desc->H);
+    if (st == DDM_OK && desc->W == 2048) st = make_direct(&p->blue_w, 2048);
+    if (st == DDM_OK && desc->H == 2048) st = make_direct(&p->blue_h, 2048);
+    else if (st == DDM_OK && !(pow2_w && pow2_h)) st = make_bluestein(&p->blue_h, desc->H);
     if (st == DDM_OK) st = upload(&p->tw_t, pass_twiddles(p->L));
     if (st == DDM_OK && p->L >= 2048) st = upload(&p->tw_tin, pass_twiddles(p->L / 32));
     if (st == DDM_OK && p->L >= 2048) {

@@ -1,4 +1,5 @@
-// Step one (Sec. 2) for frame sides that are not powers of two (e.g. a 600 x 800 camera):
+// Step one (Sec. 2) for frame sides that are not powers of two (e.g. a 600 x 800 camera),
+// and for power-of-two sides of 2048 (the same 2048-point transform without the chirp):
 // the n-point DFTs of the rows and columns by Bluestein's chirp-z identity,
 //     X[k] = conj(c_k) sum_j (z_j conj(c_j)) c_{k-j},   c_j = exp(i pi j^2 / n),
 // a cyclic convolution of length M = 2^ceil(log2(2n - 1)) done with the power-of-two
@@ -35,13 +36,19 @@ struct BShape {
 // The cyclic convolution at the heart of Bluestein's identity, on QT transforms held in
 // the cyclic layout (thread i of transform ql holds a[i + T u]).  Returns the logical index
 // li of the result: the thread then holds y[li + T u].
-template <int M, typename Sync>
+// DIRECT (a power-of-two side of M = 2048 points): the forward transform alone, no chirp.
+template <int M, bool DIRECT, typename Sync>
 __device__ __forceinline__ int bluestein_core(float2 (&v)[32], int i, int ql, float2* xs,
                                               const ddm_bluestein& b, const float2* filt,
                                               const float2* tw, Sync sync) {
     using C = BShape<M>;
     constexpr int T = C::T, QT = C::QT;
-    if constexpr (!C::THREE) {
+    if constexpr (DIRECT) {
+        static_assert(C::THREE, "direct transforms only at M = 2048");
+        const TwiddleTable tw1{tw, T};
+        fft_cyclic3<M, false, QT, C::PAD>(v, i, i, ql, xs, tw1, b.twin, sync);
+        return fft3_sigma(i, 32, T / 32);
+    } else if constexpr (!C::THREE) {
         const AddrPaddedInterleaved<QT, T> addr{ql};
         fft_cyclic<M, false>(v, i, xs, addr, tw, sync);
 #pragma unroll
@@ -62,7 +69,7 @@ __device__ __forceinline__ int bluestein_core(float2 (&v)[32], int i, int ql, fl
 
 // ------------------------------------------------------------------ rows (W not 2^k)
 // grid: (ceil(H/2 / QT), N); block: 256.  CTA: QT row pairs of one frame.
-template <int M, typename In>
+template <int M, bool DIRECT, typename In>
 __global__ void __launch_bounds__(256, 2)
 row_bluestein_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H, int W,
                      size_t frame_stride, int subtract_ref, ddm_bluestein b) {
@@ -75,9 +82,10 @@ row_bluestein_kernel(const In* __restrict__ frames, float2* __restrict__ spec, i
     float2* tw = filt + M;                                 // M entries (pass twiddles)
 
     const int tid = threadIdx.x;
-    for (int k = tid; k < W; k += NT) chirp[k] = b.chirp[k];
+    if constexpr (!DIRECT)
+        for (int k = tid; k < W; k += NT) chirp[k] = b.chirp[k];
     for (int k = tid; k < M; k += NT) {
-        filt[k] = b.filt[k];
+        if constexpr (!DIRECT) filt[k] = b.filt[k];
         if constexpr (C::T > 1) tw[k] = b.tw[k];         // M = 32: one thread per transform
     }
     const int t = blockIdx.y;
@@ -107,15 +115,16 @@ row_bluestein_kernel(const In* __restrict__ frames, float2* __restrict__ spec, i
 #pragma unroll
     for (int u = 0; u < 32; ++u) {
         const int n = i + T * u;
-        v[u] = (active && n < W) ? cmul_conj(stage[ql * W + n], chirp[n]) : make_float2(0.f, 0.f);
+        const float2 z = (active && n < W) ? stage[ql * W + n] : make_float2(0.f, 0.f);
+        v[u] = (DIRECT || n >= W) ? z : cmul_conj(z, chirp[n]);
     }
     __syncthreads();                                       // staging read: the exchange reuses it
-    const int li = bluestein_core<M>(v, i, ql, xs, b, filt, tw, SyncBlock{});
+    const int li = bluestein_core<M, DIRECT>(v, i, ql, xs, b, filt, tw, SyncBlock{});
     // X[k] = y[k] conj(c_k), k < W, into [k][QT] for the two-real-rows unpacking
 #pragma unroll
     for (int u = 0; u < 32; ++u) {
         const int k = li + T * u;
-        if (k < W) xs[k * QT + ql] = cmul_conj(v[u], chirp[k]);
+        if (k < W) xs[k * QT + ql] = DIRECT ? v[u] : cmul_conj(v[u], chirp[k]);
     }
     __syncthreads();
     const int Wh = W / 2;
@@ -138,7 +147,7 @@ row_bluestein_kernel(const In* __restrict__ frames, float2* __restrict__ spec, i
 
 // --------------------------------------------------------------- columns (H not 2^k)
 // grid: (ceil(Wh / QT), N); block: 256.  In place, QT stored columns of one frame.
-template <int M>
+template <int M, bool DIRECT>
 __global__ void __launch_bounds__(256, 2)
 col_bluestein_kernel(float2* __restrict__ spec, int H, int Wh, size_t frame_stride, ddm_bluestein b) {
     using C = BShape<M>;
@@ -150,9 +159,10 @@ col_bluestein_kernel(float2* __restrict__ spec, int H, int Wh, size_t frame_stri
     float2* tw = filt + M;
 
     const int tid = threadIdx.x;
-    for (int k = tid; k < H; k += NT) chirp[k] = b.chirp[k];
+    if constexpr (!DIRECT)
+        for (int k = tid; k < H; k += NT) chirp[k] = b.chirp[k];
     for (int k = tid; k < M; k += NT) {
-        filt[k] = b.filt[k];
+        if constexpr (!DIRECT) filt[k] = b.filt[k];
         if constexpr (C::T > 1) tw[k] = b.tw[k];         // M = 32: one thread per transform
     }
     __syncthreads();
@@ -165,13 +175,16 @@ col_bluestein_kernel(float2* __restrict__ spec, int H, int Wh, size_t frame_stri
 #pragma unroll
     for (int u = 0; u < 32; ++u) {
         const int y = i + T * u;
-        v[u] = (valid && y < H) ? cmul_conj(base[(size_t)y * Wh + kx], chirp[y]) : make_float2(0.f, 0.f);
+        const float2 z = (valid && y < H) ? base[(size_t)y * Wh + kx] : make_float2(0.f, 0.f);
+        v[u] = (DIRECT || y >= H) ? z : cmul_conj(z, chirp[y]);
     }
-    const int li = bluestein_core<M>(v, i, ql, xs, b, filt, tw, SyncBlock{});
+    const int li = bluestein_core<M, DIRECT>(v, i, ql, xs, b, filt, tw, SyncBlock{});
+    if constexpr (!DIRECT) {
 #pragma unroll
-    for (int u = 0; u < 32; ++u) {
-        const int k = li + T * u;
-        if (k < H) v[u] = cmul_conj(v[u], chirp[k]);
+        for (int u = 0; u < 32; ++u) {
+            const int k = li + T * u;
+            if (k < H) v[u] = cmul_conj(v[u], chirp[k]);
+        }
     }
     if (blockIdx.x != 0) {
         if (valid) {
@@ -211,10 +224,10 @@ size_t bluestein_smem() {
     return sizeof(float2) * (BShape<M>::XE + 1024 + 2 * (size_t)M);
 }
 
-template <int M, typename In>
+template <int M, typename In, bool DIRECT = false>
 cudaError_t rows_t(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
     using C = BShape<M>;
-    auto k = row_bluestein_kernel<M, In>;
+    auto k = row_bluestein_kernel<M, DIRECT, In>;
     const size_t smem = bluestein_smem<M>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -224,10 +237,10 @@ cudaError_t rows_t(const ddm_plan_s* p, const void* frames, float2* spec, cudaSt
     return cudaGetLastError();
 }
 
-template <int M>
+template <int M, bool DIRECT = false>
 cudaError_t cols_t(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
     using C = BShape<M>;
-    auto k = col_bluestein_kernel<M>;
+    auto k = col_bluestein_kernel<M, DIRECT>;
     const size_t smem = bluestein_smem<M>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -238,6 +251,8 @@ cudaError_t cols_t(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
 
 template <typename In>
 cudaError_t rows_dispatch(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+    if (p->blue_w.M == p->blue_w.n) return p->blue_w.M == 2048 ? rows_t<2048, In, true>(p, frames, spec, s)
+                                                                : cudaErrorInvalidValue;
     switch (p->blue_w.M) {
         case 32: return rows_t<32, In>(p, frames, spec, s);
         case 64: return rows_t<64, In>(p, frames, spec, s);
@@ -258,6 +273,8 @@ cudaError_t launch_rows_bluestein(const ddm_plan_s* p, const void* frames, float
 }
 
 cudaError_t launch_cols_bluestein(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
+    if (p->blue_h.M == p->blue_h.n) return p->blue_h.M == 2048 ? cols_t<2048, true>(p, spec, s)
+                                                                : cudaErrorInvalidValue;
     switch (p->blue_h.M) {
         case 32: return cols_t<32>(p, spec, s);
         case 64: return cols_t<64>(p, spec, s);

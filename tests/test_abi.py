@@ -54,7 +54,7 @@ def test_desc_init_defaults():
     ("W", 7, B.DDM_ERR_INVALID_ARG),
     ("W", 1030, B.DDM_ERR_UNSUPPORTED),           # above 1024
     ("W", 0, B.DDM_ERR_INVALID_ARG),
-    ("H", 2048, B.DDM_ERR_UNSUPPORTED),
+    ("H", 4096, B.DDM_ERR_UNSUPPORTED),
     ("N", 0, B.DDM_ERR_INVALID_ARG),
     ("N", 16385, B.DDM_ERR_UNSUPPORTED),
     ("dtype", 7, B.DDM_ERR_INVALID_ARG),

@@ -35,6 +35,10 @@ def _frames(N, H, W, dtype, seed):
     (512, 600, 2, "u16"),      # columns of a power-of-two side at M = 1024
     (600, 800, 3, "u16"),      # the camera shape: M = 2048 both ways
     (1000, 1022, 2, "u16"),
+    (2048, 2048, 2, "u16"),    # 2048-pixel sides: the 2048-point transform without the chirp
+    (2048, 64, 2, "f32"),
+    (64, 2048, 3, "u16"),
+    (600, 2048, 2, "u16"),
 ])
 def test_spatial_fft_non_power_of_two_matches_oracle_dft(H, W, N, dtype):
     import torch
@@ -72,7 +76,7 @@ def test_spatial_fft_non_power_of_two_without_reference_subtraction():
 @pytest.mark.parametrize("H,W,N,dtype", [
     (8, 12, 3, "f32"), (6, 10, 1, "u16"), (12, 8, 50, "u16"),
     (18, 22, 40, "f32"), (48, 80, 64, "u16"), (100, 64, 33, "u16"), (64, 100, 20, "f32"),
-    (250, 250, 100, "f32"), (600, 800, 16, "u16"),
+    (250, 250, 100, "f32"), (600, 800, 16, "u16"), (2048, 64, 40, "u16"), (16, 2048, 33, "f32"),
 ])
 def test_structure_function_non_power_of_two_matches_oracle(H, W, N, dtype):
     frames = _frames(N, H, W, dtype, seed=11 * N + H)
