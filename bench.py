@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-camera", action="store_true",
                     help="skip the 600x800x3000 (non-power-of-two sides) timing")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 tier timing")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time the image-size sweep 128^2 .. 2048^2 at N = 16384 (4096 at 2048^2)")
     ap.add_argument("--no-long", action="store_true",
                     help="skip the 512x512x16384 (longest stacks) timing")
     ap.add_argument("--kmax", type=int, default=63,
@@ -287,7 +289,7 @@ def time_camera(ddm, dev, stream, seed, H=600, W=800, N=3000, n_bins=500, steps=
     import torch
     g = torch.Generator(device=dev)
     g.manual_seed(seed)
-    frames = torch.randint(1800, 2201, (N, H, W), generator=g, device=dev, dtype=torch.int32).to(torch.uint16)
+    frames = torch.randint(1800, 2201, (N, H, W), generator=g, device=dev, dtype=torch.int16).view(torch.uint16)
     plan = ddm.Plan(H, W, N, dtype="u16", n_bins=n_bins)
     spec = torch.empty(2 * N * plan.n_q, dtype=torch.float32, device=dev)
     D = torch.empty(plan.n_q * N, dtype=torch.float32, device=dev)
@@ -323,7 +325,7 @@ def time_long_stack(ddm, dev, stream, seed, H=512, W=512, N=16384, steps=3):
     import torch
     g = torch.Generator(device=dev)
     g.manual_seed(seed)
-    frames = torch.randint(1800, 2201, (N, H, W), generator=g, device=dev, dtype=torch.int32).to(torch.uint16)
+    frames = torch.randint(1800, 2201, (N, H, W), generator=g, device=dev, dtype=torch.int16).view(torch.uint16)
     plan = ddm.Plan(H, W, N, dtype="u16")
     spec = torch.empty(2 * N * plan.n_q, dtype=torch.float32, device=dev)
     D = torch.empty(plan.n_q * N, dtype=torch.float32, device=dev)
@@ -348,6 +350,19 @@ def time_long_stack(ddm, dev, stream, seed, H=512, W=512, N=16384, steps=3):
             "frames": "uniform counts 1800..2200 drawn on the device (timing only)",
             "stages_ms": {"spatial_fft": ms[0], "temporal_sf": ms[1]},
             "frames_per_s": N / (sum(ms) / 1e3), "device_status": status, "steps": steps}
+
+
+def image_size_sweep(ddm, dev, stream, seed):
+    """The paper's second workload (Fig. 3 shape): frame sides 128 .. 2048 at the longest
+    stacks that fit (N = 16384 up to 1024^2; 2048^2 at N = 4096: its spectrum at N = 16384
+    would be 275 GB).  Step one and step two on device-drawn counts (timing only)."""
+    out = []
+    for side, N in ((128, 16384), (256, 16384), (512, 16384), (1024, 16384), (2048, 4096)):
+        r = time_long_stack(ddm, dev, stream, seed, H=side, W=side, N=N, steps=2)
+        out.append({"side": side, "N": N, "spatial_ms": r["stages_ms"]["spatial_fft"],
+                    "temporal_ms": r["stages_ms"]["temporal_sf"], "frames_per_s": r["frames_per_s"],
+                    "device_status": r["device_status"]})
+    return out
 
 
 def run_reference(args):
@@ -584,6 +599,7 @@ def run_ours(args):
     long_stack = None
     if rank == 0 and not args.no_long:
         long_stack = time_long_stack(ddm, dev, stream, args.seed)
+    sweep = image_size_sweep(ddm, dev, stream, args.seed) if (rank == 0 and args.sweep) else None
 
     # ---- fit of the 362 radial curves: plain LM vs LM seeded by the trained MLP
     fit_cmp = None
@@ -667,6 +683,8 @@ def run_ours(args):
         out["camera"] = camera
     if long_stack:
         out["long_stack"] = long_stack
+    if sweep:
+        out["image_size_sweep"] = sweep
     if fit_cmp:
         out["fit"] = fit_cmp
     if e2e:
