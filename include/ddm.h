@@ -269,6 +269,14 @@ ddm_status ddm_mlp_destroy(ddm_mlp m);
 /* Host arrays of DDM_MLP_PARAMS floats; set resets the Adam state and step count. */
 ddm_status ddm_mlp_set_weights(ddm_mlp m, const float* host_w);
 ddm_status ddm_mlp_get_weights(ddm_mlp m, float* host_w);
+/* Training checkpoint: a host array of DDM_MLP_STATE_FLOATS floats holding the FP32 master
+ * weights, Adam's first and second moments (DDM_MLP_PARAMS each, in that order) and the
+ * Adam step count (an integer stored as a float, 0 .. 2^24).  get synchronises the device;
+ * set restores all of it, so training resumed from a checkpoint takes exactly the steps
+ * the uninterrupted run would have taken. */
+#define DDM_MLP_STATE_FLOATS (3 * DDM_MLP_PARAMS + 1)
+ddm_status ddm_mlp_get_state(ddm_mlp m, float* host_state);
+ddm_status ddm_mlp_set_state(ddm_mlp m, const float* host_state);
 /* x [B][64] device -> o [B][4] device (raw outputs, before the head). */
 ddm_status ddm_mlp_forward(ddm_mlp m, const float* x, int B, float* o, void* stream);
 /* Loss = mean over the batch of (o0 - t0)^2 + (o1 - t1)^2 + (beta - t2)^2 + (o3 - t3)^2,

@@ -43,6 +43,7 @@ DDM_FIT_MLP_ACCEPTED = 8
 DDM_FIT_FALLBACK = 16
 DDM_FIT_LAGS = 64
 DDM_MLP_PARAMS = 41860
+DDM_MLP_STATE_FLOATS = 3 * DDM_MLP_PARAMS + 1
 
 
 class DDMError(RuntimeError):
@@ -87,6 +88,8 @@ def lib():
         "ddm_plan_n_q": (st, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ddm_plan_last_device_status": (st, [vp, ctypes.POINTER(ctypes.c_int)]),
         "ddm_selftest_bounded_wait": (st, [ctypes.c_longlong]),
+        "ddm_mlp_get_state": (st, [vp, vp]),
+        "ddm_mlp_set_state": (st, [vp, vp]),
         "ddm_spatial_fft": (st, [vp, vp, vp, vp]),
         "ddm_temporal_sf": (st, [vp, vp, vp, vp]),
         "ddm_structure_function": (st, [vp, vp, vp, vp]),
@@ -336,6 +339,20 @@ class MLP:
         a = np.empty(DDM_MLP_PARAMS, np.float32)
         _check(lib().ddm_mlp_get_weights(self._h, a.ctypes.data_as(ctypes.c_void_p)), "ddm_mlp_get_weights")
         return a
+
+    def get_state(self):
+        """Training checkpoint: weights, Adam moments and step count (host float32 array)."""
+        import numpy as np
+        a = np.empty(DDM_MLP_STATE_FLOATS, np.float32)
+        _check(lib().ddm_mlp_get_state(self._h, a.ctypes.data_as(ctypes.c_void_p)), "ddm_mlp_get_state")
+        return a
+
+    def set_state(self, state):
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(state, dtype=np.float32))
+        if a.size != DDM_MLP_STATE_FLOATS:
+            raise ValueError("state must hold %d floats" % DDM_MLP_STATE_FLOATS)
+        _check(lib().ddm_mlp_set_state(self._h, a.ctypes.data_as(ctypes.c_void_p)), "ddm_mlp_set_state")
 
     def forward(self, x, B, o, stream=None):
         import torch

@@ -400,6 +400,31 @@ ddm_status ddm_mlp_get_weights(ddm_mlp m, float* host_w) {
                ? DDM_OK : DDM_ERR_CUDA;
 }
 
+ddm_status ddm_mlp_get_state(ddm_mlp m, float* host_state) {
+    if (!m || !host_state) return DDM_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(host_state, m->w, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(host_state + NPARAM, m->m, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(host_state + 2 * NPARAM, m->v, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return DDM_ERR_CUDA;
+    host_state[3 * NPARAM] = (float)m->step;
+    return DDM_OK;
+}
+
+ddm_status ddm_mlp_set_state(ddm_mlp m, const float* host_state) {
+    if (!m || !host_state) return DDM_ERR_INVALID_ARG;
+    const float st = host_state[3 * NPARAM];
+    if (!(st >= 0.f && st <= 16777216.f) || st != (float)(int)st) return DDM_ERR_INVALID_ARG;
+    if (cudaMemcpy(m->w, host_state, sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->m, host_state + NPARAM, sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->v, host_state + 2 * NPARAM, sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess)
+        return DDM_ERR_CUDA;
+    m->step = (int)st;
+    bf16_copy_kernel<<<(NPARAM + 255) / 256, 256>>>(m->w, m->wt);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return DDM_ERR_CUDA;
+    return DDM_OK;
+}
+
 ddm_status ddm_mlp_forward(ddm_mlp m, const float* x, int B, float* o, void* stream) {
     if (!m || !x || !o || B < 1 || B > m->max_batch) return DDM_ERR_INVALID_ARG;
     return mlp_forward_raw(m, x, B, o, (cudaStream_t)stream);

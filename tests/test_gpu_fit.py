@@ -189,3 +189,35 @@ def test_trained_mlp_seed_gains_over_heuristic_seed():
     assert im.mean() < 0.7 * il.mean()
     assert ok_m.mean() >= ok_l.mean() - 0.01
     assert np.median(ratio) <= 1.02
+
+
+def test_training_resumes_from_a_checkpoint_bitwise():
+    """Checkpoint after 3 Adam steps, restore into a fresh network, take 4 more steps in each:
+    the weights and the Adam state agree bit for bit with the uninterrupted run."""
+    import torch
+    w = synth.mlp_init(11)
+    rng = np.random.Generator(np.random.PCG64(11))
+    Bn, lr = 128, 2e-3
+    xs = [_cuda(rng.uniform(0, 1.2, Bn * 64).astype(np.float32)) for _ in range(7)]
+    ts = [_cuda(rng.uniform(0, 1, Bn * 4).astype(np.float32)) for _ in range(7)]
+    a = ddm.MLP(Bn)
+    a.set_weights(w)
+    for k in range(3):
+        a.train_step(xs[k], ts[k], Bn, lr)
+    state = a.get_state()
+    assert state[-1] == 3.0
+    b = ddm.MLP(Bn)
+    b.set_state(state)
+    for k in range(3, 7):
+        a.train_step(xs[k], ts[k], Bn, lr)
+        b.train_step(xs[k], ts[k], Bn, lr)
+    torch.cuda.synchronize()
+    sa, sb = a.get_state(), b.get_state()
+    assert sa[-1] == sb[-1] == 7.0
+    assert np.array_equal(sa, sb)
+    with pytest.raises(ValueError):
+        b.set_state(state[:-1])
+    bad = state.copy()
+    bad[-1] = 2.5                                   # step count must be an integer
+    with pytest.raises(ddm.DDMError):
+        b.set_state(bad)
