@@ -161,6 +161,14 @@ ddm_status ddm_plan_n_q(ddm_plan p, int64_t* n_q);
  * wait); reading it resets it to DDM_OK.  Synchronise the stream first. */
 ddm_status ddm_plan_last_device_status(ddm_plan p, ddm_status* out);
 
+/* Per-stage timing (the paper's per-task time breakdown, Sec. 2): with stats enabled,
+ * ddm_structure_function records CUDA events on its stream before step one, between the
+ * steps and after step two; ddm_plan_stats waits for the last call's events and returns the
+ * two stage times in milliseconds (the FP64 tier reports both steps as step one).
+ * DDM_ERR_INVALID_ARG if no call has been recorded since stats were enabled. */
+ddm_status ddm_plan_enable_stats(ddm_plan p, int on);
+ddm_status ddm_plan_stats(ddm_plan p, float* step_one_ms, float* step_two_ms);
+
 /* Test hook for the bounded device waits (no plan needed, current device, synchronous):
  * launches one CTA that arms a tile barrier for bytes no copy will deliver and waits on it
  * with the same bounded routine the time kernels use, giving up after cap_cycles SM clock

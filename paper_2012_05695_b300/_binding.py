@@ -88,6 +88,8 @@ def lib():
         "ddm_plan_n_q": (st, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ddm_plan_last_device_status": (st, [vp, ctypes.POINTER(ctypes.c_int)]),
         "ddm_selftest_bounded_wait": (st, [ctypes.c_longlong]),
+        "ddm_plan_enable_stats": (st, [vp, c_int]),
+        "ddm_plan_stats": (st, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
         "ddm_mlp_get_state": (st, [vp, vp]),
         "ddm_mlp_set_state": (st, [vp, vp]),
         "ddm_spatial_fft": (st, [vp, vp, vp, vp]),
@@ -290,6 +292,15 @@ class Plan:
                              _dev_ptr(params, "params", torch.float32, 4 * n_curves),
                              opt(cost, "cost", torch.float32), opt(iters, "iters", torch.int32),
                              opt(flags, "flags", torch.int32), _stream_ptr(stream)), "ddm_fit")
+
+    def enable_stats(self, on: bool = True):
+        _check(lib().ddm_plan_enable_stats(self._h, 1 if on else 0), "ddm_plan_enable_stats")
+
+    def stats(self):
+        """(step one ms, step two ms) of the last structure_function call."""
+        a, b = ctypes.c_float(), ctypes.c_float()
+        _check(lib().ddm_plan_stats(self._h, ctypes.byref(a), ctypes.byref(b)), "ddm_plan_stats")
+        return a.value, b.value
 
     def last_device_status(self) -> int:
         s = ctypes.c_int()

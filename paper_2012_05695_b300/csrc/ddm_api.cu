@@ -62,6 +62,8 @@ ddm_status upload(T** dst, const std::vector<T>& host) {
 
 void free_plan(ddm_plan_s* p) {
     if (!p) return;
+    for (cudaEvent_t& e : p->stats_ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(p->tw_row);
     cudaFree(p->tw_col);
     cudaFree(p->tw_t);
@@ -470,6 +472,35 @@ ddm_status ddm_plan_n_q(ddm_plan p, int64_t* n_q) {
     return DDM_OK;
 }
 
+ddm_status ddm_plan_enable_stats(ddm_plan p, int on) {
+    if (!check_plan(p)) return DDM_ERR_INVALID_ARG;
+    for (cudaEvent_t& e : p->stats_ev) {
+        if (on && !e && cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+            return DDM_ERR_CUDA;
+        }
+        if (!on && e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    }
+    p->stats_recorded = false;
+    return DDM_OK;
+}
+
+ddm_status ddm_plan_stats(ddm_plan p, float* step_one_ms, float* step_two_ms) {
+    if (!check_plan(p) || !step_one_ms || !step_two_ms) return DDM_ERR_INVALID_ARG;
+    if (!p->stats_recorded) return DDM_ERR_INVALID_ARG;
+    if (cudaEventSynchronize(p->stats_ev[2]) != cudaSuccess ||
+        cudaEventElapsedTime(step_one_ms, p->stats_ev[0], p->stats_ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(step_two_ms, p->stats_ev[1], p->stats_ev[2]) != cudaSuccess) {
+        cudaGetLastError();
+        return DDM_ERR_CUDA;
+    }
+    return DDM_OK;
+}
+
 ddm_status ddm_selftest_bounded_wait(long long cap_cycles) {
     if (cap_cycles < 1000) cap_cycles = 1000;
     if (cap_cycles > 4000000000LL) cap_cycles = 4000000000LL;
@@ -522,11 +553,26 @@ ddm_status ddm_structure_function(ddm_plan p, const void* frames, float* D, void
     if ((reinterpret_cast<uintptr_t>(D) & 3) != 0) return DDM_ERR_INVALID_ARG;
     ddm_status st = ensure_workspace(p);
     if (st != DDM_OK) return st;
-    if (p->d.precision == DDM_PREC_FP64) return launch_fp64(p, frames, p->workspace, D, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool stats = p->stats_ev[0] != nullptr;
+    if (stats && cudaEventRecord(p->stats_ev[0], s) != cudaSuccess) return DDM_ERR_CUDA;
+    if (p->d.precision == DDM_PREC_FP64) {
+        // one launch sequence: step one and step two are not separated in the stats
+        st = launch_fp64(p, frames, p->workspace, D, s);
+        if (st == DDM_OK && stats)
+            st = (cudaEventRecord(p->stats_ev[1], s) == cudaSuccess &&
+                  cudaEventRecord(p->stats_ev[2], s) == cudaSuccess) ? DDM_OK : DDM_ERR_CUDA;
+        p->stats_recorded = stats && st == DDM_OK;
+        return st;
+    }
     float2* spec = reinterpret_cast<float2*>(p->workspace);
-    st = launch_spatial(p, frames, spec, (cudaStream_t)stream);
+    st = launch_spatial(p, frames, spec, s);
     if (st != DDM_OK) return st;
-    return launch_temporal(p, spec, D, (cudaStream_t)stream);
+    if (stats && cudaEventRecord(p->stats_ev[1], s) != cudaSuccess) return DDM_ERR_CUDA;
+    st = launch_temporal(p, spec, D, s);
+    if (st == DDM_OK && stats && cudaEventRecord(p->stats_ev[2], s) != cudaSuccess) return DDM_ERR_CUDA;
+    p->stats_recorded = stats && st == DDM_OK;
+    return st;
 }
 
 ddm_status ddm_azimuthal_average(ddm_plan p, const float* D, float* Dr, int* counts,

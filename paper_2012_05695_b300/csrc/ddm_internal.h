@@ -56,6 +56,8 @@ struct ddm_plan_s {
     float* fit_scratch; // fit: features, plateaus, MLP outputs (grown on demand)
     size_t fit_scratch_bytes;
     unsigned* dev_status;   // kernel-reported status word
+    cudaEvent_t stats_ev[3] = {nullptr, nullptr, nullptr};   // step-one / step-two timing
+    bool stats_recorded = false;
     void* workspace;
     size_t ws_bytes;
     bool ws_owned;

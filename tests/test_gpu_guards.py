@@ -109,3 +109,26 @@ def test_bounded_wait_gives_up_with_timeout(cap):
     assert ddm.selftest_bounded_wait(cap) == ddm._binding.DDM_ERR_TIMEOUT
     x = torch.ones(1024, device="cuda")
     assert float(x.sum().item()) == 1024.0
+
+
+def test_plan_stats_time_both_steps():
+    import torch
+    H, W, N = 128, 128, 512
+    frames = to_device(_frames(N, H, W, "u16", 3))
+    plan = ddm.Plan(H, W, N, dtype="u16")
+    D = torch.empty(plan.n_q * N, device="cuda")
+    with pytest.raises(ddm.DDMError):
+        plan.enable_stats(True)
+        plan.stats()                                  # nothing recorded yet
+    plan.structure_function(frames, D)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    plan.structure_function(frames, D)
+    e.record()
+    one, two = plan.stats()
+    torch.cuda.synchronize()
+    total = s.elapsed_time(e)
+    assert one > 0 and two > 0
+    assert one + two <= total * 1.05 + 0.05
+    assert one + two >= total * 0.5
+    plan.enable_stats(False)
