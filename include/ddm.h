@@ -143,8 +143,12 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc);
  * work enqueued with the plan is still running. */
 ddm_status ddm_plan_destroy(ddm_plan p);
 
-/* Bytes of device workspace ddm_structure_function needs (the spectrum store,
- * n_q * N complex64, 256-byte aligned). */
+/* Bytes of device workspace ddm_structure_function needs: the spectrum store (n_q * N
+ * complex64, complex128 for DDM_PREC_FP64, 256-byte aligned), plus, for time transforms of
+ * L >= 2048 points on many wave vectors (n_q >= 200000, or >= 100000 at L = 16384) when
+ * max_workspace_bytes leaves room, a blocked copy of the spectrum (16 wave vectors
+ * contiguous over time) that the time kernels read.  ddm_temporal_sf uses the workspace
+ * for that copy too (allocating it if none is attached). */
 ddm_status ddm_plan_workspace_size(ddm_plan p, size_t* bytes);
 
 /* Attach a caller-owned device workspace of at least ddm_plan_workspace_size() bytes,

@@ -28,6 +28,10 @@ struct ddm_plan_s {
     double2* tw64 = nullptr;        // FP64 tier: exp(-2 pi i r / fp64_ntab), r < fp64_ntab / 2
     double2* tw64_half = nullptr;   // FP64 tier: exp(-i pi t / L), t < L
     int fp64_ntab = 0;
+    bool blocked = false;           // L >= 2048, large n_q: time kernels read a blocked copy of
+                                    // [q0, q1) (16 wave vectors contiguous over time) made in the
+                                    // workspace at byte offset blk_offset
+    size_t blk_offset = 0;
     float2* crop_inter; // kc > 0: row-pass output [N][H][kc + 1]
     int device;
     int n_sm;

@@ -68,6 +68,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y),
         "r"(smem_u32(bar)) : "memory");
 }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z),
+        "r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -138,6 +145,8 @@ struct TArgs {
     int64_t n_tiles;  // tiles of [q0, q1) (of one group, L >= 512; of one CTA, L <= 256)
     int vec4;         // D rows 16-byte aligned (N % 4 == 0 and D aligned)
     int fix;          // FP64-fixup tier: lags 1..fix by direct differences (0 = off)
+    int blocked;      // L >= 2048: the spectrum arrives as 16-wave-vector blocks [b][t][16]
+                      // of the range [q0, q1) (block b = wave vectors q0 + 16 b ..)
     const float2* tw;
     const float2* tw2;
     const float* inv;
@@ -634,9 +643,15 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
         if (tid == 0) {
             fence_proxy_async();
             mbar_expect_tx(&tile_bar, (uint32_t)(C::NBOX * C::BOX_T * QG * sizeof(float2)));
+            const int64_t rel = t * QG;                    // first wave vector, relative to q0
 #pragma unroll
-            for (int b = 0; b < C::NBOX; ++b)
-                tma_load_2d(xs + b * C::BOX_T * QG, &tmap, (int)(2 * (q0 + t * QG)), b * C::BOX_T, &tile_bar);
+            for (int b = 0; b < C::NBOX; ++b) {
+                if (a.blocked)                             // [block][t][16]: x in the block, t, block
+                    tma_load_3d(xs + b * C::BOX_T * QG, &tmap, (int)(2 * (rel & 15)), b * C::BOX_T,
+                                (int)(rel >> 4), &tile_bar);
+                else
+                    tma_load_2d(xs + b * C::BOX_T * QG, &tmap, (int)(2 * (q0 + rel)), b * C::BOX_T, &tile_bar);
+            }
         }
     };
     auto wait = [&]() -> bool {
@@ -939,14 +954,15 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
     const int zs1 = zslot(s1), zsi = zslot(i);
     const TwiddleTwoLevel<L> tw1{lo, hi};
     const int N = a.N, kd = a.kd;
-    const int64_t nq = a.n_q;
     const int m_lo = N - kd;
     const int m_tail = m_lo + ((i - m_lo) % T + T) % T;    // this thread's trailing lag, if < N
     float chk = 0.f;
 
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         const int64_t sq = a.q0 + tile;                    // stored wave vector
-        const float2* xg = spec + sq;                      // x(t) = xg[t * n_q]
+        // x(t) = xg[t * nq]: the [t][q] spectrum, or its 16-wave-vector blocks [b][t][16]
+        const float2* xg = a.blocked ? spec + (tile >> 4) * (int64_t)N * 16 + (tile & 15) : spec + sq;
+        const int64_t nq = a.blocked ? 16 : a.n_q;
         __syncthreads();                                   // previous wave vector's reads done
         // ---- time sequence (thread i holds t = i + T u) and its mean
         float2 v[P];
@@ -1364,6 +1380,50 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
+// Corner turn of the stored wave vectors [q0, q1) into blocks of 16 contiguous over time:
+// blk[(b N + t) 16 + c] = spec[t n_q + q0 + 16 b + c], zero past q1.  One block of 256 frames
+// per CTA; reads and writes are 128-byte rows.
+__global__ void __launch_bounds__(256)
+blocked_copy_kernel(const float2* __restrict__ spec, float2* __restrict__ blk, int N, int64_t n_q,
+                    int64_t q0, int64_t q1) {
+    const int64_t b = blockIdx.x;
+    const int t0 = blockIdx.y * 256;
+    const int64_t qb = q0 + 16 * b;
+    for (int idx = threadIdx.x; idx < 256 * 16; idx += 256) {
+        const int t = t0 + (idx >> 4), c = idx & 15;
+        if (t >= N) break;
+        const int64_t q = qb + c;
+        blk[(b * N + t) * 16 + c] = q < q1 ? __ldg(spec + (int64_t)t * n_q + q) : make_float2(0.f, 0.f);
+    }
+}
+
+// 3D view of the blocked copy as float32 [nb][N][32]; boxes of 2 qg floats x 256 rows x 1
+// block.
+bool make_blocked_map(CUtensorMap* map, const float2* blk, int64_t nb, int N, int qg) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {32, (cuuint64_t)N, (cuuint64_t)nb};
+    const cuuint64_t strides[2] = {32 * sizeof(float), (cuuint64_t)N * 32 * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * qg), 256, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(blk), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The blocked copy of [q0, q1) in the plan workspace, or nullptr when the plan does not use it
+// (or has no workspace yet: the kernels then read the [t][q] spectrum).
+float2* blocked_copy(const ddm_plan_s* p, const float2* spec, cudaStream_t s, bool* ok) {
+    *ok = true;
+    if (!p->blocked || !p->workspace) return nullptr;
+    float2* blk = reinterpret_cast<float2*>(static_cast<char*>(p->workspace) + p->blk_offset);
+    const int64_t nb = (p->q1 - p->q0 + 15) / 16;
+    dim3 grid((unsigned)nb, (unsigned)((p->d.N + 255) / 256));
+    blocked_copy_kernel<<<grid, 256, 0, s>>>(spec, blk, p->d.N, p->n_q, p->q0, p->q1);
+    *ok = cudaGetLastError() == cudaSuccess;
+    return blk;
+}
+
 // 2D view of the spectrum as float32 [N][2 n_q]; boxes of 2 qg floats (qg complex) x 256
 // rows; rows >= N and columns >= 2 n_q read as zero.
 bool make_spectrum_map(CUtensorMap* map, const float2* spec, int64_t n_q, int N, int qg) {
@@ -1385,6 +1445,7 @@ void fill_args(TArgs& a, const ddm_plan_s* p, float* D, int qt) {
     a.Wh = p->Wh;
     a.crop = p->kc > 0;
     a.vec4 = (p->d.N % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
+    a.blocked = 0;
     a.fix = (p->d.precision == DDM_PREC_FP32_FP64FIX) ? p->fix_lags : 0;
     a.n_q = p->n_q;
     a.q0 = p->q0;
@@ -1419,11 +1480,17 @@ template <int LOG2L, bool FIXUP>
 ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
     using C = LShape<LOG2L>;
     if ((reinterpret_cast<uintptr_t>(spec) & 15) != 0 || !p->tw_tin || !p->tw_long) return DDM_ERR_INVALID_ARG;
+    bool ok = true;
+    const float2* blk = blocked_copy(p, spec, s, &ok);
+    if (!ok) return DDM_ERR_CUDA;
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof(tmap));
-    if (!make_spectrum_map(&tmap, spec, p->n_q, p->d.N, C::QG)) return DDM_ERR_CUDA;
+    if (blk ? !make_blocked_map(&tmap, blk, (p->q1 - p->q0 + 15) / 16, p->d.N, C::QG)
+            : !make_spectrum_map(&tmap, spec, p->n_q, p->d.N, C::QG))
+        return DDM_ERR_CUDA;
     TArgs a;
     fill_args(a, p, D, C::QG);
+    a.blocked = blk != nullptr;
     auto k = temporal_sf_long_kernel<LOG2L, FIXUP>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
         cudaSuccess)
@@ -1445,8 +1512,13 @@ ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaSt
 ddm_status launch_xl(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
     using C = XLShape;
     if (!p->tw_tin || !p->tw_long || p->L != C::L) return DDM_ERR_INVALID_ARG;
+    bool ok = true;
+    const float2* blk = blocked_copy(p, spec, s, &ok);
+    if (!ok) return DDM_ERR_CUDA;
+    if (blk) spec = blk;
     TArgs a;
     fill_args(a, p, D, 1);
+    a.blocked = blk != nullptr;
     auto k = temporal_sf_xl_kernel;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
         cudaSuccess)

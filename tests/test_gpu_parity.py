@@ -340,3 +340,38 @@ def test_fp64_fixup_tier_blobs_512x512x1024_sampled():
     ref = D_ref[..., 1:9]
     err = np.max(np.abs(D[:, cols, 1:9] - ref) / ref)
     assert err <= 2e-5, err
+
+
+@pytest.mark.parametrize("S,N,kw", [
+    (640, 2048, {}),
+    (640, 4096, {"precision": ddm.DDM_PREC_FP32_FP64FIX}),
+    (640, 3000, {"q_begin": 1024, "q_end": 200000}),
+    (512, 16384, {}),
+])
+def test_temporal_blocked_copy_matches_oracle(S, N, kw):
+    """n_q = 205440 (640 x 640) at L = 2048 .. 4096 and 131584 (512 x 512) at L = 16384: the
+    long time kernels read a blocked copy of the spectrum (16 wave vectors contiguous over
+    time).  Random spectrum drawn on the device, checked on sampled wave vectors at block
+    edges, inside blocks and at the range ends."""
+    import torch
+    H = W = S
+    plan = ddm.Plan(H, W, N, dtype="f32", **kw)
+    nq = plan.n_q
+    g = torch.Generator(device="cuda")
+    g.manual_seed(N)
+    spec = torch.randn(2 * N * nq, generator=g, device="cuda") + 0.5
+    D = torch.full((nq * N,), float("nan"), device="cuda")
+    plan.temporal_sf(spec, D)
+    torch.cuda.synchronize()
+    assert plan.last_device_status() == 0
+    q0, q1 = kw.get("q_begin", 0), kw.get("q_end", nq)
+    cand = [q0, q0 + 1, q0 + 15, q0 + 16, q0 + 17, q0 + 31, q0 + 1000, (q0 + q1) // 2, q1 - 17, q1 - 2, q1 - 1]
+    s = np.array(sorted(set(c for c in cand if q0 <= c < q1)))
+    F = spec.view(N, nq, 2)[:, torch.from_numpy(s).cuda(), :].cpu().numpy().astype(np.float64)
+    F = F[..., 0] + 1j * F[..., 1]                      # [N, len(s)]
+    D_ref = oracle.sf_direct(F)                          # [len(s), N]
+    sky, skx = (np.asarray(a) for a in ddm.spectrum_index_map(H, W))
+    rows = sky[s] * (W // 2 + 1) + skx[s]
+    Dg = D.view(nq, N)[torch.from_numpy(rows).cuda()].cpu().numpy()
+    assert np.all(Dg[:, 0] == 0)
+    assert oracle.scaled_error(Dg, D_ref, oracle.plateau_scale(F)) <= TOL
