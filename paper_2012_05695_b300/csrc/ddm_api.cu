@@ -73,6 +73,8 @@ void free_plan(ddm_plan_s* p) {
     cudaFree(p->tw_col);
     cudaFree(p->tw_t);
     cudaFree(p->tw_tin);
+    cudaFree(p->mix_w.tw);
+    cudaFree(p->mix_h.tw);
     cudaFree(p->tw64);
     cudaFree(p->tw64_half);
     for (ddm_bluestein* b : {&p->blue_w, &p->blue_h}) {
@@ -146,6 +148,23 @@ ddm_status make_bluestein(ddm_bluestein* b, int n) {
     if (st == DDM_OK && M >= 64) st = upload(&b->tw, pass_twiddles(M));
     if (st == DDM_OK && M >= 2048) st = upload(&b->twin, pass_twiddles(M / 32));
     return st;
+}
+
+// A side of a mixed-radix shape n = P T: the pass twiddles, built in double precision.
+ddm_status make_mixed(ddm_mixed* m, int n) {
+    int P = 0, T = 0;
+    mixed_shape(n, &P, &T);
+    if (P == 0) return DDM_ERR_UNSUPPORTED;
+    m->n = n;
+    m->P = P;
+    m->T = T;
+    std::vector<float2> tw((size_t)n);
+    for (int k1 = 0; k1 < P; ++k1)
+        for (int i = 0; i < T; ++i) {
+            const cx_cs cs = cx_cossin_frac((long)((long)i * k1 % n), n);
+            tw[(size_t)k1 * T + i] = make_float2((float)cs.c, (float)-cs.s);
+        }
+    return upload(&m->tw, tw);
 }
 
 // A power-of-two side of 2048 points: the Bluestein kernels' three-pass transform alone.
@@ -336,10 +355,20 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
     // Bluestein tables: rows when W is not a power of two; columns when either side is not
     // (the power-of-two column kernel takes whole blocks of 16 stored columns).  Sides of
     // 2048: the same kernels' 2048-point transform alone (no chirp).
-    if (st == DDM_OK && !pow2_w) st = make_bluestein(&p->blue_w, desc->W);
+    // mixed-radix kernels first for the sides they are built for (480, 600, 640, 720, 800, 960)
+    int mP = 0, mT = 0;
+    mixed_shape(desc->W, &mP, &mT);
+    const bool mix_w = mP > 0;
+    mixed_shape(desc->H, &mP, &mT);
+    const bool mix_h = mP > 0;
+    if (st == DDM_OK && mix_w) st = make_mixed(&p->mix_w, desc->W);
+    else if (st == DDM_OK && !pow2_w) st = make_bluestein(&p->blue_w, desc->W);
     if (st == DDM_OK && desc->W == 2048) st = make_direct(&p->blue_w, 2048);
     if (st == DDM_OK && desc->H == 2048) st = make_direct(&p->blue_h, 2048);
-    else if (st == DDM_OK && !(pow2_w && pow2_h)) st = make_bluestein(&p->blue_h, desc->H);
+    else if (st == DDM_OK && !(pow2_w && pow2_h)) {
+        if (mix_h) st = make_mixed(&p->mix_h, desc->H);
+        else st = make_bluestein(&p->blue_h, desc->H);
+    }
     if (st == DDM_OK) st = upload(&p->tw_t, pass_twiddles(p->L));
     if (st == DDM_OK && p->L >= 2048) st = upload(&p->tw_tin, pass_twiddles(p->L / 32));
     if (st == DDM_OK && p->L >= 2048) {

@@ -198,6 +198,83 @@ __device__ __forceinline__ void dft_reg(float2* v) {
     }
 }
 
+// ------------------------------------------------------------------ mixed radix (2, 3, 5)
+// DFTs of 3 and 5 points in place.  s i z below is -i z (forward) or +i z (inverse).
+template <bool INV>
+__device__ __forceinline__ float2 times_si(float2 z) {
+    return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+}
+template <bool INV>
+__device__ __forceinline__ void dft3(float2& a, float2& b, float2& c) {
+    constexpr float h = (float)cx_cossin_frac(1, 3).s;           // sin(2 pi / 3)
+    const float2 t1 = cadd(b, c), d = csub(b, c);
+    const float2 t2 = make_float2(fmaf(-0.5f, t1.x, a.x), fmaf(-0.5f, t1.y, a.y));
+    const float2 m = times_si<INV>(make_float2(h * d.x, h * d.y));
+    a = cadd(a, t1);
+    b = cadd(t2, m);
+    c = csub(t2, m);
+}
+template <bool INV>
+__device__ __forceinline__ void dft5(float2& a, float2& b, float2& c, float2& d, float2& e) {
+    constexpr float c1 = (float)cx_cossin_frac(1, 5).c, c2 = (float)cx_cossin_frac(2, 5).c;
+    constexpr float s1 = (float)cx_cossin_frac(1, 5).s, s2 = (float)cx_cossin_frac(2, 5).s;
+    const float2 t1 = cadd(b, e), t2 = cadd(c, d), t3 = csub(b, e), t4 = csub(c, d);
+    const float2 r1 = make_float2(fmaf(c2, t2.x, fmaf(c1, t1.x, a.x)), fmaf(c2, t2.y, fmaf(c1, t1.y, a.y)));
+    const float2 r2 = make_float2(fmaf(c1, t2.x, fmaf(c2, t1.x, a.x)), fmaf(c1, t2.y, fmaf(c2, t1.y, a.y)));
+    const float2 m1 = times_si<INV>(make_float2(fmaf(s2, t4.x, s1 * t3.x), fmaf(s2, t4.y, s1 * t3.y)));
+    const float2 m2 = times_si<INV>(make_float2(fmaf(-s1, t4.x, s2 * t3.x), fmaf(-s1, t4.y, s2 * t3.y)));
+    a = cadd(a, cadd(t1, t2));
+    b = cadd(r1, m1);
+    e = csub(r1, m1);
+    c = cadd(r2, m2);
+    d = csub(r2, m2);
+}
+
+// Unnormalised DFT of N = 2^a 3^b 5^c points in registers, natural order in and out:
+// decimation in time by the prime p (5, then 3, then the power-of-two dft_reg), the p
+// sub-sequences v[p j + r] transformed, then for every k < N/p the twiddles w_N^{r k}
+// (compile-time constants) and a p-point DFT give X[k + (N/p) q], q < p.
+template <int N, bool INV>
+__device__ __forceinline__ void dft_mix(float2* v);
+
+template <int N, int P, int K, bool INV>
+__device__ __forceinline__ void mix_combine_k(float2* v, float2 (*sub)[N / P]) {
+    constexpr int M = N / P;
+    if constexpr (P == 5) {
+        float2 a = sub[0][K], b = twiddle_const<N, K, INV>(sub[1][K]), c = twiddle_const<N, 2 * K, INV>(sub[2][K]);
+        float2 d = twiddle_const<N, 3 * K, INV>(sub[3][K]), e = twiddle_const<N, 4 * K, INV>(sub[4][K]);
+        dft5<INV>(a, b, c, d, e);
+        v[K] = a; v[K + M] = b; v[K + 2 * M] = c; v[K + 3 * M] = d; v[K + 4 * M] = e;
+    } else if constexpr (P == 3) {
+        float2 a = sub[0][K], b = twiddle_const<N, K, INV>(sub[1][K]), c = twiddle_const<N, 2 * K, INV>(sub[2][K]);
+        dft3<INV>(a, b, c);
+        v[K] = a; v[K + M] = b; v[K + 2 * M] = c;
+    }
+}
+template <int N, int P, bool INV, int... K>
+__device__ __forceinline__ void mix_combine(float2* v, float2 (*sub)[N / P], std::integer_sequence<int, K...>) {
+    (mix_combine_k<N, P, K, INV>(v, sub), ...);
+}
+
+template <int N, bool INV>
+__device__ __forceinline__ void dft_mix(float2* v) {
+    if constexpr ((N & (N - 1)) == 0) {
+        dft_reg<N, INV>(v);
+    } else {
+        constexpr int P = (N % 5 == 0) ? 5 : 3;
+        static_assert(N % P == 0, "dft_mix: lengths 2^a 3^b 5^c");
+        constexpr int M = N / P;
+        float2 sub[P][M];
+#pragma unroll
+        for (int r = 0; r < P; ++r)
+#pragma unroll
+            for (int j = 0; j < M; ++j) sub[r][j] = v[P * j + r];
+#pragma unroll
+        for (int r = 0; r < P; ++r) dft_mix<M, INV>(sub[r]);
+        mix_combine<N, P, INV>(v, sub, std::make_integer_sequence<int, M>{});
+    }
+}
+
 // ------------------------------------------------------------------ two-pass FFT
 template <int L>
 struct FftShape {

@@ -17,6 +17,13 @@ struct ddm_bluestein {
     float2* twin = nullptr;
 };
 
+// Mixed-radix transform of a side n = P T (P, T of the form 2^a 3^b 5^c): pass twiddles
+// tw[k1 T + i] = exp(-2 pi i i k1 / n), k1 < P, i < T.
+struct ddm_mixed {
+    int n = 0, P = 0, T = 0;
+    float2* tw = nullptr;
+};
+
 struct ddm_plan_s {
     ddm_plan_desc d;
     int L;              // transform length in time: smallest power of two >= N (M = 2L)
@@ -25,6 +32,7 @@ struct ddm_plan_s {
     int64_t q0, q1;     // stored wave vectors covered by step two and the radial stage
     int kc;             // low-frequency restriction: kmax (0 = full half plane)
     ddm_bluestein blue_w, blue_h;   // rows / columns of non-power-of-two length
+    ddm_mixed mix_w, mix_h;         // rows / columns of a mixed-radix side (before Bluestein)
     double2* tw64 = nullptr;        // FP64 tier: exp(-2 pi i r / fp64_ntab), r < fp64_ntab / 2
     double2* tw64_half = nullptr;   // FP64 tier: exp(-i pi t / L), t < L
     int fp64_ntab = 0;
@@ -78,6 +86,9 @@ ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
 ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s);
 bool fp64_supported(const ddm_plan_desc& d);
 ddm_status launch_fp64(const ddm_plan_s* p, const void* frames, void* workspace, float* D, cudaStream_t s);
+void mixed_shape(int n, int* P, int* T);
+cudaError_t launch_rows_mixed(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
+cudaError_t launch_cols_mixed(const ddm_plan_s* p, float2* spec, cudaStream_t s);
 cudaError_t launch_wait_selftest(unsigned* status, long long cap_cycles, cudaStream_t s);
 cudaError_t launch_rows_bluestein(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
 cudaError_t launch_cols_bluestein(const ddm_plan_s* p, float2* spec, cudaStream_t s);

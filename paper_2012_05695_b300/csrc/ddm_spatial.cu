@@ -320,12 +320,14 @@ ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
         if (launch_rows_bulk(p, frames, spec, s) != cudaSuccess) return DDM_ERR_CUDA;
         return dispatch_cols_crop(p, spec, s) == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
     }
-    if (p->blue_w.M > 0 || p->blue_h.M > 0) {
-        // a side that is not a power of two, or of 2048: Bluestein (or 2048-point) rows or
-        // the power-of-two row pass, then Bluestein (or 2048-point) columns or the
-        // power-of-two column pass
+    if (p->blue_w.M > 0 || p->blue_h.M > 0 || p->mix_w.n > 0 || p->mix_h.n > 0) {
+        // a side that is not a power of two, or of 2048: mixed-radix, Bluestein (or
+        // 2048-point) rows or the power-of-two row pass, then mixed-radix, Bluestein (or
+        // 2048-point) columns or the power-of-two column pass
         cudaError_t e;
-        if (p->blue_w.M > 0)
+        if (p->mix_w.n > 0)
+            e = launch_rows_mixed(p, frames, spec, s);
+        else if (p->blue_w.M > 0)
             e = launch_rows_bluestein(p, frames, spec, s);
         else if (rows_bulk_supported(p, frames))
             e = launch_rows_bulk(p, frames, spec, s);
@@ -333,7 +335,8 @@ ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
             e = (p->d.dtype == DDM_IN_U16) ? dispatch_rows<uint16_t>(p, frames, spec, s)
                                            : dispatch_rows<float>(p, frames, spec, s);
         if (e != cudaSuccess) return DDM_ERR_CUDA;
-        e = p->blue_h.M > 0 ? launch_cols_bluestein(p, spec, s) : dispatch_cols(p, spec, s);
+        e = p->mix_h.n > 0 ? launch_cols_mixed(p, spec, s)
+            : p->blue_h.M > 0 ? launch_cols_bluestein(p, spec, s) : dispatch_cols(p, spec, s);
         return e == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
     }
     if (p->d.spatial_path == DDM_SPATIAL_FUSED && fused_spatial_supported(p) &&

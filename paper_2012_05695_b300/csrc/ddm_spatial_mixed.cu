@@ -1,0 +1,243 @@
+// Step one (Sec. 2) for frame sides n = P T with P, T of the form 2^a 3^b 5^c (common camera
+// sides: 480, 600, 640, 720, 800, 960): a two-pass mixed-radix transform instead of
+// Bluestein's, about 6x less arithmetic at n = 800.  T threads per transform, P points per
+// thread in the cyclic layout (thread i holds x[i + T u], u < P):
+//   pass 1: the P-point DFT over u (dft_mix), the twiddle w_n^{i k1} (host table, double
+//           precision), one shared-memory exchange;
+//   pass 2: thread j < P takes k1 = j and does the T-point DFT over i; it then holds
+//           X[j + P k2], k2 < T (threads j >= P idle in this pass).
+// The row and column kernels around it are those of the Bluestein path (two real rows per
+// complex row transform with the Nyquist value in slot 0; columns in place, the packed DC /
+// Nyquist column unpacked by the block that holds it).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ddm_fft.cuh"
+#include "ddm_internal.h"
+
+namespace ddm {
+namespace {
+
+template <int P_, int T_>
+struct MShape {
+    static constexpr int P = P_, T = T_, N = P * T;
+    static constexpr int NT = 256;
+    static constexpr int QT = NT / T;                       // transforms per CTA
+    static constexpr int ROW = T + 1;                       // exchange row of one k1 (padded)
+    static constexpr size_t XCH = (size_t)P * ROW * QT;     // (k1 ROW + i) QT + ql
+    static constexpr int WS = N + 1;                        // staged row stride (odd: no conflicts)
+    static constexpr size_t STG = (size_t)QT * WS;
+    static constexpr size_t OUT = (size_t)N * QT;           // X[k] of transform ql at k QT + ql
+    static constexpr size_t XE = XCH > STG ? (XCH > OUT ? XCH : OUT) : (STG > OUT ? STG : OUT);
+    static constexpr size_t BYTES = sizeof(float2) * (XE + (size_t)N);
+    static_assert(P <= 40 && T <= 32 && QT >= 1, "mixed-radix shapes");
+};
+
+// QT interleaved transforms; thread (ql, i) with i < T.  live: the thread is one of the
+// T QT threads that carry a transform (the CTA may have a few spare threads).  Returns with
+// thread (ql, j), j < P, holding X[j + P k2] in w[k2].
+template <int P, int T>
+__device__ __forceinline__ void fft_mixed(float2 (&v)[P], float2 (&w)[T], int i, int ql, bool live,
+                                          float2* xs, const float2* tw) {
+    using C = MShape<P, T>;
+    dft_mix<P, false>(v);
+    if (live) {
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) {
+            const float2 a = k1 == 0 ? v[k1] : cmul(v[k1], tw[k1 * T + i]);
+            xs[(k1 * C::ROW + i) * C::QT + ql] = a;
+        }
+    }
+    __syncthreads();
+    if (live && i < P) {
+#pragma unroll
+        for (int ip = 0; ip < T; ++ip) w[ip] = xs[(i * C::ROW + ip) * C::QT + ql];
+        dft_mix<T, false>(w);
+    }
+    __syncthreads();                                        // exchange read: xs is free
+}
+
+// ---------------------------------------------------------------- rows (W = P T)
+// grid: (ceil(H/2 / QT), N); block: 256.  CTA: QT row pairs of one frame.
+template <int P, int T, typename In>
+__global__ void __launch_bounds__(256)
+row_mixed_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H, size_t frame_stride,
+                 int subtract_ref, const float2* __restrict__ tw_g) {
+    using C = MShape<P, T>;
+    constexpr int W = C::N, QT = C::QT, NT = C::NT, WS = C::WS;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float2* xs = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = xs + C::XE;
+    const int tid = threadIdx.x;
+    for (int k = tid; k < W; k += NT) tw[k] = tw_g[k];
+    const int t = blockIdx.y;
+    const int pair0 = blockIdx.x * QT;
+    const int npairs = min(QT, H / 2 - pair0);
+    const In* src = frames + ((size_t)t * H + 2 * pair0) * W;
+    const In* ref = frames + (size_t)(2 * pair0) * W;
+    for (int e = tid; e < npairs * W; e += NT) {
+        const int q = e / W, x = e - q * W;
+        const size_t ia = (size_t)(2 * q) * W + x, ib = ia + W;
+        float a, b;
+        if constexpr (sizeof(In) == 2) {
+            a = (float)((int)src[ia] - (subtract_ref ? (int)ref[ia] : 0));
+            b = (float)((int)src[ib] - (subtract_ref ? (int)ref[ib] : 0));
+        } else {
+            a = subtract_ref ? (float)src[ia] - (float)ref[ia] : (float)src[ia];
+            b = subtract_ref ? (float)src[ib] - (float)ref[ib] : (float)src[ib];
+        }
+        xs[q * WS + x] = make_float2(a, b);
+    }
+    __syncthreads();
+    const int ql = tid % QT, i = tid / QT;
+    const bool live = i < T;
+    const bool active = live && ql < npairs;
+    float2 v[P], w[T];
+#pragma unroll
+    for (int u = 0; u < P; ++u) v[u] = active ? xs[ql * WS + i + T * u] : make_float2(0.f, 0.f);
+    __syncthreads();                                        // staging read: xs becomes the exchange
+    fft_mixed<P, T>(v, w, i, ql, live, xs, tw);
+    if (live && i < P) {
+#pragma unroll
+        for (int k2 = 0; k2 < T; ++k2) xs[(i + P * k2) * QT + ql] = w[k2];
+    }
+    __syncthreads();
+    const int Wh = W / 2;
+    for (int e = tid; e < npairs * Wh; e += NT) {
+        const int q = e / Wh, k = e - q * Wh;
+        float2* outa = spec + (size_t)t * frame_stride + (size_t)(2 * (pair0 + q)) * Wh;
+        float2* outb = outa + Wh;
+        const float2 z = xs[k * QT + q];
+        if (k == 0) {
+            const float2 zn = xs[Wh * QT + q];
+            outa[0] = make_float2(z.x, zn.x);
+            outb[0] = make_float2(z.y, zn.y);
+        } else {
+            const float2 zr = xs[(W - k) * QT + q];
+            outa[k] = make_float2(0.5f * (z.x + zr.x), 0.5f * (z.y - zr.y));
+            outb[k] = make_float2(0.5f * (z.y + zr.y), 0.5f * (zr.x - z.x));
+        }
+    }
+}
+
+// ------------------------------------------------------------- columns (H = P T)
+// grid: (ceil(Wh / QT), N); block: 256.  In place, QT stored columns of one frame.
+template <int P, int T>
+__global__ void __launch_bounds__(256)
+col_mixed_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride, const float2* __restrict__ tw_g) {
+    using C = MShape<P, T>;
+    constexpr int H = C::N, QT = C::QT, NT = C::NT;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float2* xs = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = xs + C::XE;
+    const int tid = threadIdx.x;
+    for (int k = tid; k < H; k += NT) tw[k] = tw_g[k];
+    __syncthreads();
+    const int ql = tid % QT, i = tid / QT;
+    const bool live = i < T;
+    const int kx = blockIdx.x * QT + ql;
+    const bool valid = live && kx < Wh;
+    float2* base = spec + (size_t)blockIdx.y * frame_stride;
+    float2 v[P], w[T];
+#pragma unroll
+    for (int u = 0; u < P; ++u) v[u] = valid ? base[(size_t)(i + T * u) * Wh + kx] : make_float2(0.f, 0.f);
+    fft_mixed<P, T>(v, w, i, ql, live, xs, tw);
+    const bool holds = live && i < P;                       // holds X[i + P k2], k2 < T
+    if (blockIdx.x != 0) {
+        if (holds && kx < Wh) {
+#pragma unroll
+            for (int k2 = 0; k2 < T; ++k2) base[(size_t)(i + P * k2) * Wh + kx] = w[k2];
+        }
+        return;
+    }
+    // the block holding kx = 0 unpacks the packed DC / Nyquist column (partner ky <-> H - ky)
+    if (holds) {
+#pragma unroll
+        for (int k2 = 0; k2 < T; ++k2) xs[(i + P * k2) * QT + ql] = w[k2];
+    }
+    __syncthreads();
+    if (!holds || kx >= Wh) return;
+#pragma unroll
+    for (int k2 = 0; k2 < T; ++k2) {
+        const int ky = i + P * k2;
+        if (ql != 0) {
+            base[(size_t)ky * Wh + kx] = w[k2];
+        } else {
+            const float2 c = w[k2];
+            const float2 cr = xs[(ky == 0 ? 0 : H - ky) * QT];
+            base[(size_t)ky * Wh] = make_float2(0.5f * (c.x + cr.x), 0.5f * (c.y - cr.y));
+            base[(size_t)H * Wh + ky] = make_float2(0.5f * (c.y + cr.y), 0.5f * (cr.x - c.x));
+        }
+    }
+}
+
+template <int P, int T, typename In>
+cudaError_t rows_t(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+    using C = MShape<P, T>;
+    auto k = row_mixed_kernel<P, T, In>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p->d.H / 2 + C::QT - 1) / C::QT, p->d.N);
+    k<<<grid, C::NT, C::BYTES, s>>>((const In*)frames, spec, p->d.H, (size_t)p->n_q, p->d.subtract_ref,
+                                     p->mix_w.tw);
+    return cudaGetLastError();
+}
+
+template <int P, int T>
+cudaError_t cols_t(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
+    using C = MShape<P, T>;
+    auto k = col_mixed_kernel<P, T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p->Wh + C::QT - 1) / C::QT, p->d.N);
+    k<<<grid, C::NT, C::BYTES, s>>>(spec, p->Wh, (size_t)p->n_q, p->mix_h.tw);
+    return cudaGetLastError();
+}
+
+// the shapes built: side -> (P, T)
+template <typename In>
+cudaError_t rows_dispatch(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+    switch (p->d.W) {
+        case 480: return rows_t<15, 32, In>(p, frames, spec, s);
+        case 600: return rows_t<24, 25, In>(p, frames, spec, s);
+        case 640: return rows_t<20, 32, In>(p, frames, spec, s);
+        case 720: return rows_t<24, 30, In>(p, frames, spec, s);
+        case 800: return rows_t<25, 32, In>(p, frames, spec, s);
+        case 960: return rows_t<30, 32, In>(p, frames, spec, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+// (P, T) of a side built with the mixed-radix kernels, or (0, 0)
+void mixed_shape(int n, int* P, int* T) {
+    switch (n) {
+        case 480: *P = 15; *T = 32; return;
+        case 600: *P = 24; *T = 25; return;
+        case 640: *P = 20; *T = 32; return;
+        case 720: *P = 24; *T = 30; return;
+        case 800: *P = 25; *T = 32; return;
+        case 960: *P = 30; *T = 32; return;
+        default: *P = 0; *T = 0; return;
+    }
+}
+
+cudaError_t launch_rows_mixed(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+    return p->d.dtype == DDM_IN_U16 ? rows_dispatch<uint16_t>(p, frames, spec, s)
+                                    : rows_dispatch<float>(p, frames, spec, s);
+}
+
+cudaError_t launch_cols_mixed(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
+    switch (p->d.H) {
+        case 480: return cols_t<15, 32>(p, spec, s);
+        case 600: return cols_t<24, 25>(p, spec, s);
+        case 640: return cols_t<20, 32>(p, spec, s);
+        case 720: return cols_t<24, 30>(p, spec, s);
+        case 800: return cols_t<25, 32>(p, spec, s);
+        case 960: return cols_t<30, 32>(p, spec, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ddm

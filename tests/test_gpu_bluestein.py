@@ -1,5 +1,6 @@
-"""Frame sides that are not powers of two (step one of Sec. 2 by Bluestein's chirp-z
-transform) against the FP64 oracle, through the C ABI.
+"""Frame sides that are not powers of two (step one of Sec. 2 by the mixed-radix kernels for
+480, 600, 640, 720, 800, 960 and by Bluestein's chirp-z transform otherwise) and sides of
+2048, against the FP64 oracle, through the C ABI.
 
 Shapes cover every convolution length the kernels are built for (M = 64 .. 2048), a
 power-of-two side beside a non-power-of-two one in both orders, ragged row-pair and
@@ -35,6 +36,11 @@ def _frames(N, H, W, dtype, seed):
     (512, 600, 2, "u16"),      # columns of a power-of-two side at M = 1024
     (600, 800, 3, "u16"),      # the camera shape: M = 2048 both ways
     (1000, 1022, 2, "u16"),
+    (480, 640, 2, "f32"),      # mixed-radix sides (P T = 15 32, 20 32)
+    (720, 960, 2, "u16"),      # (24 30, 30 32)
+    (800, 600, 2, "f32"),      # (25 32 columns, 24 25 rows)
+    (600, 512, 2, "u16"),      # mixed columns beside power-of-two rows
+    (64, 960, 3, "f32"),       # mixed rows beside Bluestein columns (M = 128)
     (2048, 2048, 2, "u16"),    # 2048-pixel sides: the 2048-point transform without the chirp
     (2048, 64, 2, "f32"),
     (64, 2048, 3, "u16"),
@@ -77,6 +83,7 @@ def test_spatial_fft_non_power_of_two_without_reference_subtraction():
     (8, 12, 3, "f32"), (6, 10, 1, "u16"), (12, 8, 50, "u16"),
     (18, 22, 40, "f32"), (48, 80, 64, "u16"), (100, 64, 33, "u16"), (64, 100, 20, "f32"),
     (250, 250, 100, "f32"), (600, 800, 16, "u16"), (2048, 64, 40, "u16"), (16, 2048, 33, "f32"),
+    (480, 640, 12, "f32"), (720, 96, 30, "u16"),
 ])
 def test_structure_function_non_power_of_two_matches_oracle(H, W, N, dtype):
     frames = _frames(N, H, W, dtype, seed=11 * N + H)
