@@ -314,7 +314,7 @@ def time_camera(ddm, dev, stream, seed, H=600, W=800, N=3000, n_bins=500, steps=
     plan.close()
     return {"workload": f"camera_{H}x{W}x{N}_u16", "H": H, "W": W, "N": N, "n_bins": n_bins,
             "frames": "uniform counts 1800..2200 drawn on the device (timing only)",
-            "spatial": "Bluestein rows and columns, convolution length 2048",
+            "spatial": "mixed-radix rows (800 = 25 x 32) and columns (600 = 24 x 25)",
             "stages_ms": {"spatial_fft": ms[0], "temporal_sf": ms[1], "azimuthal_average": ms[2]},
             "frames_per_s": N / (sum(ms) / 1e3), "device_status": status, "steps": steps}
 
