@@ -1,6 +1,6 @@
 // Step one (Sec. 2) for frame sides n = P T with P, T of the form 2^a 3^b 5^c (common camera
-// sides: 480, 600, 640, 720, 800, 960): a two-pass mixed-radix transform instead of
-// Bluestein's, about 6x less arithmetic at n = 800.  T threads per transform, P points per
+// sides: 384, 480, 540, 600, 640, 720, 768, 800, 900, 960, 1000): a two-pass mixed-radix
+// transform instead of Bluestein's, about 6x less arithmetic at n = 800.  T threads per transform, P points per
 // thread in the cyclic layout (thread i holds x[i + T u], u < P):
 //   pass 1: the P-point DFT over u (dft_mix), the twiddle w_n^{i k1} (host table, double
 //           precision), one shared-memory exchange;
@@ -30,7 +30,8 @@ struct MShape {
     static constexpr size_t OUT = (size_t)N * QT;           // X[k] of transform ql at k QT + ql
     static constexpr size_t XE = XCH > STG ? (XCH > OUT ? XCH : OUT) : (STG > OUT ? STG : OUT);
     static constexpr size_t BYTES = sizeof(float2) * (XE + (size_t)N);
-    static_assert(P <= 40 && T <= 32 && QT >= 1, "mixed-radix shapes");
+    static_assert(P <= 32 && T <= 40 && QT >= 1, "mixed-radix shapes");
+    static_assert(P <= T, "pass 2 gives each k1 < P its own thread: P <= T");
 };
 
 // QT interleaved transforms; thread (ql, i) with i < T.  live: the thread is one of the
@@ -198,12 +199,17 @@ cudaError_t cols_t(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
 template <typename In>
 cudaError_t rows_dispatch(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
     switch (p->d.W) {
+        case 384: return rows_t<12, 32, In>(p, frames, spec, s);
         case 480: return rows_t<15, 32, In>(p, frames, spec, s);
+        case 540: return rows_t<18, 30, In>(p, frames, spec, s);
         case 600: return rows_t<24, 25, In>(p, frames, spec, s);
         case 640: return rows_t<20, 32, In>(p, frames, spec, s);
         case 720: return rows_t<24, 30, In>(p, frames, spec, s);
+        case 768: return rows_t<24, 32, In>(p, frames, spec, s);
         case 800: return rows_t<25, 32, In>(p, frames, spec, s);
+        case 900: return rows_t<30, 30, In>(p, frames, spec, s);
         case 960: return rows_t<30, 32, In>(p, frames, spec, s);
+        case 1000: return rows_t<25, 40, In>(p, frames, spec, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -213,12 +219,17 @@ cudaError_t rows_dispatch(const ddm_plan_s* p, const void* frames, float2* spec,
 // (P, T) of a side built with the mixed-radix kernels, or (0, 0)
 void mixed_shape(int n, int* P, int* T) {
     switch (n) {
+        case 384: *P = 12; *T = 32; return;
         case 480: *P = 15; *T = 32; return;
+        case 540: *P = 18; *T = 30; return;
         case 600: *P = 24; *T = 25; return;
         case 640: *P = 20; *T = 32; return;
         case 720: *P = 24; *T = 30; return;
+        case 768: *P = 24; *T = 32; return;
         case 800: *P = 25; *T = 32; return;
+        case 900: *P = 30; *T = 30; return;
         case 960: *P = 30; *T = 32; return;
+        case 1000: *P = 25; *T = 40; return;
         default: *P = 0; *T = 0; return;
     }
 }
@@ -230,12 +241,17 @@ cudaError_t launch_rows_mixed(const ddm_plan_s* p, const void* frames, float2* s
 
 cudaError_t launch_cols_mixed(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
     switch (p->d.H) {
+        case 384: return cols_t<12, 32>(p, spec, s);
         case 480: return cols_t<15, 32>(p, spec, s);
+        case 540: return cols_t<18, 30>(p, spec, s);
         case 600: return cols_t<24, 25>(p, spec, s);
         case 640: return cols_t<20, 32>(p, spec, s);
         case 720: return cols_t<24, 30>(p, spec, s);
+        case 768: return cols_t<24, 32>(p, spec, s);
         case 800: return cols_t<25, 32>(p, spec, s);
+        case 900: return cols_t<30, 30>(p, spec, s);
         case 960: return cols_t<30, 32>(p, spec, s);
+        case 1000: return cols_t<25, 40>(p, spec, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,6 +1,6 @@
 """Frame sides that are not powers of two (step one of Sec. 2 by the mixed-radix kernels for
-480, 600, 640, 720, 800, 960 and by Bluestein's chirp-z transform otherwise) and sides of
-2048, against the FP64 oracle, through the C ABI.
+384, 480, 540, 600, 640, 720, 768, 800, 900, 960, 1000 and by Bluestein's chirp-z transform
+otherwise) and sides of 2048, against the FP64 oracle, through the C ABI.
 
 Shapes cover every convolution length the kernels are built for (M = 64 .. 2048), a
 power-of-two side beside a non-power-of-two one in both orders, ragged row-pair and
@@ -41,6 +41,8 @@ def _frames(N, H, W, dtype, seed):
     (800, 600, 2, "f32"),      # (25 32 columns, 24 25 rows)
     (600, 512, 2, "u16"),      # mixed columns beside power-of-two rows
     (64, 960, 3, "f32"),       # mixed rows beside Bluestein columns (M = 128)
+    (384, 768, 2, "u16"),      # (12 32, 24 32)
+    (540, 900, 2, "f32"),      # (18 30, 30 30)
     (2048, 2048, 2, "u16"),    # 2048-pixel sides: the 2048-point transform without the chirp
     (2048, 64, 2, "f32"),
     (64, 2048, 3, "u16"),
