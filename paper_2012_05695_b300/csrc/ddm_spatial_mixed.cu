@@ -18,16 +18,27 @@
 namespace ddm {
 namespace {
 
+// exchange row stride: the smallest r >= T with r QT = QT (mod 16), so that in pass 2 the
+// QT-lane groups of consecutive k1 tile the 16 bank pairs (8-byte elements)
+constexpr int mixed_row(int T, int QT) {
+    int r = T;
+    while ((r * QT - QT) % 16 != 0) ++r;
+    return r;
+}
+
 template <int P_, int T_>
 struct MShape {
     static constexpr int P = P_, T = T_, N = P * T;
     static constexpr int NT = 256;
     static constexpr int QT = NT / T;                       // transforms per CTA
-    static constexpr int ROW = T + 1;                       // exchange row of one k1 (padded)
+    static constexpr int ROW = mixed_row(T, QT);            // exchange row of one k1
     static constexpr size_t XCH = (size_t)P * ROW * QT;     // (k1 ROW + i) QT + ql
-    static constexpr int WS = N + 1;                        // staged row stride (odd: no conflicts)
+    // row stride of the staged input and of the output X (transform ql at ql WS + k): 4 mod 16
+    // float2, so that the lanes of a warp (a few transforms x a few consecutive indices) fall
+    // on distinct bank pairs
+    static constexpr int WS = N + ((4 - N % 16) + 16) % 16;
     static constexpr size_t STG = (size_t)QT * WS;
-    static constexpr size_t OUT = (size_t)N * QT;           // X[k] of transform ql at k QT + ql
+    static constexpr size_t OUT = STG;
     static constexpr size_t XE = XCH > STG ? (XCH > OUT ? XCH : OUT) : (STG > OUT ? STG : OUT);
     static constexpr size_t BYTES = sizeof(float2) * (XE + (size_t)N);
     static_assert(P <= 32 && T <= 40 && QT >= 1, "mixed-radix shapes");
@@ -76,16 +87,17 @@ row_mixed_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H
     const int npairs = min(QT, H / 2 - pair0);
     const In* src = frames + ((size_t)t * H + 2 * pair0) * W;
     const In* ref = frames + (size_t)(2 * pair0) * W;
-    for (int e = tid; e < npairs * W; e += NT) {
+#pragma unroll 4
+    for (int e = tid; e < npairs * W; e += NT) {            // 4 iterations of loads in flight
         const int q = e / W, x = e - q * W;
         const size_t ia = (size_t)(2 * q) * W + x, ib = ia + W;
         float a, b;
         if constexpr (sizeof(In) == 2) {
-            a = (float)((int)src[ia] - (subtract_ref ? (int)ref[ia] : 0));
-            b = (float)((int)src[ib] - (subtract_ref ? (int)ref[ib] : 0));
+            a = (float)((int)__ldg(src + ia) - (subtract_ref ? (int)__ldg(ref + ia) : 0));
+            b = (float)((int)__ldg(src + ib) - (subtract_ref ? (int)__ldg(ref + ib) : 0));
         } else {
-            a = subtract_ref ? (float)src[ia] - (float)ref[ia] : (float)src[ia];
-            b = subtract_ref ? (float)src[ib] - (float)ref[ib] : (float)src[ib];
+            a = subtract_ref ? __ldg(src + ia) - __ldg(ref + ia) : __ldg(src + ia);
+            b = subtract_ref ? __ldg(src + ib) - __ldg(ref + ib) : __ldg(src + ib);
         }
         xs[q * WS + x] = make_float2(a, b);
     }
@@ -100,7 +112,7 @@ row_mixed_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H
     fft_mixed<P, T>(v, w, i, ql, live, xs, tw);
     if (live && i < P) {
 #pragma unroll
-        for (int k2 = 0; k2 < T; ++k2) xs[(i + P * k2) * QT + ql] = w[k2];
+        for (int k2 = 0; k2 < T; ++k2) xs[ql * WS + i + P * k2] = w[k2];
     }
     __syncthreads();
     const int Wh = W / 2;
@@ -108,13 +120,13 @@ row_mixed_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H
         const int q = e / Wh, k = e - q * Wh;
         float2* outa = spec + (size_t)t * frame_stride + (size_t)(2 * (pair0 + q)) * Wh;
         float2* outb = outa + Wh;
-        const float2 z = xs[k * QT + q];
+        const float2 z = xs[q * WS + k];
         if (k == 0) {
-            const float2 zn = xs[Wh * QT + q];
+            const float2 zn = xs[q * WS + Wh];
             outa[0] = make_float2(z.x, zn.x);
             outb[0] = make_float2(z.y, zn.y);
         } else {
-            const float2 zr = xs[(W - k) * QT + q];
+            const float2 zr = xs[q * WS + W - k];
             outa[k] = make_float2(0.5f * (z.x + zr.x), 0.5f * (z.y - zr.y));
             outb[k] = make_float2(0.5f * (z.y + zr.y), 0.5f * (zr.x - z.x));
         }
