@@ -30,6 +30,11 @@ struct BShape {
     static constexpr size_t X_THREE = (size_t)P * (T + PAD) * QT > (size_t)M * QT
                                           ? (size_t)P * (T + PAD) * QT : (size_t)M * QT;
     static constexpr size_t XE = THREE ? X_THREE : X_TWO;
+    // row stride of the staged rows and of the output X of transform ql (at ql WS + k):
+    // WS = 32 / QT (mod 16) float2 (odd when QT >= 32), so that a warp's QT x (32 / QT) lanes
+    // fall on distinct bank pairs
+    static constexpr int WS_MOD = QT >= 32 ? 1 : 32 / QT;
+    static constexpr int ws(int W) { return W + ((WS_MOD - W % 16) % 16 + 16) % 16; }
     static_assert(M >= 32 && M <= 2048 && QT * T == NT, "Bluestein lengths 3 .. 1024");
 };
 
@@ -94,7 +99,9 @@ row_bluestein_kernel(const In* __restrict__ frames, float2* __restrict__ spec, i
     // the CTA's rows, frame 0 subtracted in integers, staged as floats [pair][W] complex
     const In* src = frames + ((size_t)t * H + 2 * pair0) * W;
     const In* ref = frames + (size_t)(2 * pair0) * W;
-    float2* stage = xs;                                    // QT * W complex <= exchange size
+    float2* stage = xs;                                    // QT * WS complex <= exchange size
+    const int WS = C::ws(W);
+#pragma unroll 4
     for (int e = tid; e < npairs * W; e += NT) {
         const int q = e / W, x = e - q * W;
         const size_t ia = (size_t)(2 * q) * W + x, ib = ia + W;
@@ -106,7 +113,7 @@ row_bluestein_kernel(const In* __restrict__ frames, float2* __restrict__ spec, i
             a = subtract_ref ? (float)src[ia] - (float)ref[ia] : (float)src[ia];
             bb = subtract_ref ? (float)src[ib] - (float)ref[ib] : (float)src[ib];
         }
-        stage[q * W + x] = make_float2(a, bb);
+        stage[q * WS + x] = make_float2(a, bb);
     }
     __syncthreads();
     const int ql = tid % QT, i = tid / QT;
@@ -115,16 +122,16 @@ row_bluestein_kernel(const In* __restrict__ frames, float2* __restrict__ spec, i
 #pragma unroll
     for (int u = 0; u < 32; ++u) {
         const int n = i + T * u;
-        const float2 z = (active && n < W) ? stage[ql * W + n] : make_float2(0.f, 0.f);
+        const float2 z = (active && n < W) ? stage[ql * WS + n] : make_float2(0.f, 0.f);
         v[u] = (DIRECT || n >= W) ? z : cmul_conj(z, chirp[n]);
     }
     __syncthreads();                                       // staging read: the exchange reuses it
     const int li = bluestein_core<M, DIRECT>(v, i, ql, xs, b, filt, tw, SyncBlock{});
-    // X[k] = y[k] conj(c_k), k < W, into [k][QT] for the two-real-rows unpacking
+    // X[k] = y[k] conj(c_k), k < W, into row ql for the two-real-rows unpacking
 #pragma unroll
     for (int u = 0; u < 32; ++u) {
         const int k = li + T * u;
-        if (k < W) xs[k * QT + ql] = DIRECT ? v[u] : cmul_conj(v[u], chirp[k]);
+        if (k < W) xs[ql * WS + k] = DIRECT ? v[u] : cmul_conj(v[u], chirp[k]);
     }
     __syncthreads();
     const int Wh = W / 2;
@@ -132,13 +139,13 @@ row_bluestein_kernel(const In* __restrict__ frames, float2* __restrict__ spec, i
         const int q = e / Wh, k = e - q * Wh;
         float2* outa = spec + (size_t)t * frame_stride + (size_t)(2 * (pair0 + q)) * Wh;
         float2* outb = outa + Wh;
-        const float2 z = xs[k * QT + q];
+        const float2 z = xs[q * WS + k];
         if (k == 0) {
-            const float2 zn = xs[Wh * QT + q];
+            const float2 zn = xs[q * WS + Wh];
             outa[0] = make_float2(z.x, zn.x);
             outb[0] = make_float2(z.y, zn.y);
         } else {
-            const float2 zr = xs[(W - k) * QT + q];
+            const float2 zr = xs[q * WS + W - k];
             outa[k] = make_float2(0.5f * (z.x + zr.x), 0.5f * (z.y - zr.y));
             outb[k] = make_float2(0.5f * (z.y + zr.y), 0.5f * (zr.x - z.x));
         }
