@@ -240,7 +240,8 @@ typedef enum ddm_fit_mode {
     DDM_FIT_LM = 0,        /* Levenberg-Marquardt from a heuristic seed */
     DDM_FIT_MLP = 1,       /* MLP prediction only */
     DDM_FIT_MLP_LM = 2     /* MLP seed; kept if its RMS residual / A <= 1e-2, else LM from
-                              it, and LM from the heuristic seed if that diverges */
+                              the lower-cost of the MLP and the heuristic seed (and from the
+                              heuristic seed if LM from the MLP seed diverges) */
 } ddm_fit_mode;
 
 /* ddm_fit flags per curve */
@@ -249,6 +250,8 @@ typedef enum ddm_fit_mode {
 #define DDM_FIT_NONFINITE 4
 #define DDM_FIT_MLP_ACCEPTED 8
 #define DDM_FIT_FALLBACK 16
+#define DDM_FIT_SEED_HEURISTIC 32   /* MLP_LM: LM started from the heuristic seed, whose cost
+                                       was below the network's */
 
 typedef struct ddm_mlp_s* ddm_mlp;
 

@@ -41,6 +41,7 @@ DDM_FIT_MAXITER = 2
 DDM_FIT_NONFINITE = 4
 DDM_FIT_MLP_ACCEPTED = 8
 DDM_FIT_FALLBACK = 16
+DDM_FIT_SEED_HEURISTIC = 32
 DDM_FIT_LAGS = 64
 DDM_MLP_PARAMS = 41860
 DDM_MLP_STATE_FLOATS = 3 * DDM_MLP_PARAMS + 1

@@ -318,13 +318,23 @@ __global__ void __launch_bounds__(32 * kTrials) lm_kernel(const float* __restric
         } else if (isfinite(cost) && sqrtf(cost / (float)kLags) <= 1e-2f * fabsf(A)) {
             flags = DDM_FIT_CONVERGED | DDM_FIT_MLP_ACCEPTED;
         } else {
+            // LM from the lower-cost seed: the network's or the heuristic one (a network
+            // trained on another distribution then costs nothing, a good one saves iterations)
             float q[4] = {p[0], p[1], p[2], p[3]};
+            float h[4];
+            heuristic_seed(cv, lane, h);
+            const bool from_heuristic = !(cost <= cost_at(cv, h));
+            if (from_heuristic) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) q[a] = h[a];
+            }
             it = lm(cv, q, cost, flags, sh);
-            if (flags & DDM_FIT_NONFINITE) {
+            if ((flags & DDM_FIT_NONFINITE) && !from_heuristic) {
                 heuristic_seed(cv, lane, q);
                 it += lm(cv, q, cost, flags, sh);
                 flags |= DDM_FIT_FALLBACK;
             }
+            if (from_heuristic) flags |= DDM_FIT_SEED_HEURISTIC;
 #pragma unroll
             for (int a = 0; a < 4; ++a) p[a] = q[a];
         }
