@@ -295,32 +295,37 @@ def time_camera(ddm, dev, stream, seed, H=600, W=800, N=3000, n_bins=500, steps=
     g.manual_seed(seed)
     frames = torch.randint(1800, 2201, (N, H, W), generator=g, device=dev, dtype=torch.int16).view(torch.uint16)
     plan = ddm.Plan(H, W, N, dtype="u16", n_bins=n_bins)
-    spec = torch.empty(2 * N * plan.n_q, dtype=torch.float32, device=dev)
     D = torch.empty(plan.n_q * N, dtype=torch.float32, device=dev)
     Dr = torch.empty(n_bins * N, dtype=torch.float32, device=dev)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    # both steps through ddm_structure_function (its own workspace: step one writes the
+    # blocked copy the time kernels read), stage times from the plan's CUDA events
+    plan.enable_stats(True)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    one = two = 0.0
     for k in range(3 + steps):
         e = ev[k - 3] if k >= 3 else None
         if e:
             e[0].record(stream)
-        plan.spatial_fft(frames, spec, stream)
+        plan.structure_function(frames, D, stream)
         if e:
             e[1].record(stream)
-        plan.temporal_sf(spec, D, stream)
-        if e:
-            e[2].record(stream)
         plan.azimuthal_average(D, Dr, None, stream)
         if e:
-            e[3].record(stream)
+            e[2].record(stream)
+            a, b = plan.stats()
+            one += a
+            two += b
     torch.cuda.synchronize()
-    ms = [sum(e[j].elapsed_time(e[j + 1]) for e in ev) / steps for j in range(3)]
+    sf_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
+    ms = [one / steps, two / steps, sum(e[1].elapsed_time(e[2]) for e in ev) / steps]
     status = plan.last_device_status()
     plan.close()
     return {"workload": f"camera_{H}x{W}x{N}_u16", "H": H, "W": W, "N": N, "n_bins": n_bins,
+            "structure_function_ms": sf_ms,
             "frames": "uniform counts 1800..2200 drawn on the device (timing only)",
             "spatial": "mixed-radix rows (800 = 25 x 32) and columns (600 = 24 x 25)",
             "stages_ms": {"spatial_fft": ms[0], "temporal_sf": ms[1], "azimuthal_average": ms[2]},
-            "frames_per_s": N / (sum(ms) / 1e3), "device_status": status, "steps": steps}
+            "frames_per_s": N / ((sf_ms + ms[2]) / 1e3), "device_status": status, "steps": steps}
 
 
 def time_long_stack(ddm, dev, stream, seed, H=512, W=512, N=16384, steps=3):
@@ -331,24 +336,25 @@ def time_long_stack(ddm, dev, stream, seed, H=512, W=512, N=16384, steps=3):
     g.manual_seed(seed)
     frames = torch.randint(1800, 2201, (N, H, W), generator=g, device=dev, dtype=torch.int16).view(torch.uint16)
     plan = ddm.Plan(H, W, N, dtype="u16")
-    spec = torch.empty(2 * N * plan.n_q, dtype=torch.float32, device=dev)
     D = torch.empty(plan.n_q * N, dtype=torch.float32, device=dev)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    plan.enable_stats(True)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+    one = two = 0.0
     for k in range(2 + steps):
         e = ev[k - 2] if k >= 2 else None
         if e:
             e[0].record(stream)
-        plan.spatial_fft(frames, spec, stream)
+        plan.structure_function(frames, D, stream)
         if e:
             e[1].record(stream)
-        plan.temporal_sf(spec, D, stream)
-        if e:
-            e[2].record(stream)
+            a, b = plan.stats()
+            one += a
+            two += b
     torch.cuda.synchronize()
-    ms = [sum(e[j].elapsed_time(e[j + 1]) for e in ev) / steps for j in range(2)]
+    ms = [one / steps, two / steps]
     status = plan.last_device_status()
     plan.close()
-    del frames, spec, D
+    del frames, D
     torch.cuda.empty_cache()
     return {"workload": f"long_{H}x{W}x{N}_u16", "H": H, "W": W, "N": N,
             "frames": "uniform counts 1800..2200 drawn on the device (timing only)",

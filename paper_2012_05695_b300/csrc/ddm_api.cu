@@ -630,10 +630,23 @@ ddm_status ddm_structure_function(ddm_plan p, const void* frames, float* D, void
         return st;
     }
     float2* spec = reinterpret_cast<float2*>(p->workspace);
-    st = launch_spatial(p, frames, spec, s);
+    // plans whose long time kernels read a blocked copy: step one's column pass writes it
+    // directly (no corner-turn pass); the last block's entries past q1 are zeroed for the
+    // tiles that read them
+    float2* blk = nullptr;
+    if (p->blocked) {
+        blk = reinterpret_cast<float2*>(static_cast<char*>(p->workspace) + p->blk_offset);
+        const int64_t n = p->q1 - p->q0, nb = (n + 15) / 16;
+        if (n % 16 != 0 &&
+            cudaMemsetAsync(blk + (size_t)(nb - 1) * p->d.N * 16, 0, sizeof(float2) * (size_t)p->d.N * 16, s) !=
+                cudaSuccess)
+            return DDM_ERR_CUDA;
+    }
+    bool wrote_blocked = false;
+    st = launch_spatial(p, frames, spec, s, blk, &wrote_blocked);
     if (st != DDM_OK) return st;
     if (stats && cudaEventRecord(p->stats_ev[1], s) != cudaSuccess) return DDM_ERR_CUDA;
-    st = launch_temporal(p, spec, D, s);
+    st = launch_temporal(p, spec, D, s, wrote_blocked);
     if (st == DDM_OK && stats && cudaEventRecord(p->stats_ev[2], s) != cudaSuccess) return DDM_ERR_CUDA;
     p->stats_recorded = stats && st == DDM_OK;
     return st;

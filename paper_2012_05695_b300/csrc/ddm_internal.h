@@ -81,17 +81,41 @@ namespace ddm {
 // ([ky][kx]); the last H entries are the kx = W/2 column ([ky]).
 size_t spectrum_frame_stride(const ddm_plan_s* p);   // complex elements per frame
 
-ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
-                          cudaStream_t s);
-ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s);
+// blk_out: write the column pass's output straight into the plan's blocked copy (when the
+// chosen kernels can; *wrote_blocked tells) instead of in place
+ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s,
+                          float2* blk_out = nullptr, bool* wrote_blocked = nullptr);
+// pre_blocked: the plan's blocked copy already holds the spectrum (no corner-turn pass)
+ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s,
+                           bool pre_blocked = false);
+// Where a column pass writes the spectrum entry (frame t, stored wave vector q): in place in
+// the [t][q] spectrum (blk == nullptr), or into the blocked copy [b][t][16] of the range
+// [q0, q1) that the long time kernels read (entries outside the range are not written).
+struct SpecOut {
+    float2* blk;
+    int N;
+    int64_t q0, q1;
+#ifdef __CUDACC__
+    __device__ __forceinline__ void put(float2* frame, int t, int64_t q, float2 v) const {
+        if (!blk) {
+            frame[q] = v;
+            return;
+        }
+        const int64_t r = q - q0;
+        if (r < 0 || q >= q1) return;
+        blk[((r >> 4) * N + t) * 16 + (r & 15)] = v;
+    }
+#endif
+};
+
 bool fp64_supported(const ddm_plan_desc& d);
 ddm_status launch_fp64(const ddm_plan_s* p, const void* frames, void* workspace, float* D, cudaStream_t s);
 void mixed_shape(int n, int* P, int* T);
 cudaError_t launch_rows_mixed(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
-cudaError_t launch_cols_mixed(const ddm_plan_s* p, float2* spec, cudaStream_t s);
+cudaError_t launch_cols_mixed(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out);
 cudaError_t launch_wait_selftest(unsigned* status, long long cap_cycles, cudaStream_t s);
 cudaError_t launch_rows_bluestein(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
-cudaError_t launch_cols_bluestein(const ddm_plan_s* p, float2* spec, cudaStream_t s);
+cudaError_t launch_cols_bluestein(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out);
 ddm_status launch_radial(const ddm_plan_s* p, const float* D, float* Dr, int* counts, bool normalise,
                          cudaStream_t s);
 

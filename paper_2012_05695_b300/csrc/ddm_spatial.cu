@@ -110,7 +110,7 @@ row_r2c_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
 template <int H, int QC>
 __global__ void __launch_bounds__(QC * FftShape<H>::T, (QC * FftShape<H>::T) >= 512 ? 1 : (QC * FftShape<H>::T) >= 256 ? 2 : 4)
 col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
-               const float2* __restrict__ tw_g) {
+               const float2* __restrict__ tw_g, SpecOut out) {
     using S = FftShape<H>;
     constexpr int P = S::P, T = S::T, NT = QC * T;
     extern __shared__ float2 smem[];
@@ -138,8 +138,13 @@ col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
 
     base = opaque_ptr(base);
     if (blockIdx.x != 0) {
+        if (!out.blk) {
 #pragma unroll
-        for (int u = 0; u < P; ++u) base[off0 + (uint32_t)u * step] = v[u];
+            for (int u = 0; u < P; ++u) base[off0 + (uint32_t)u * step] = v[u];
+        } else {
+#pragma unroll
+            for (int u = 0; u < P; ++u) out.put(base, t, off0 + (uint32_t)u * step, v[u]);
+        }
         return;
     }
     // block 0 holds the packed DC/Nyquist column in ql = 0: unpack it
@@ -150,13 +155,13 @@ col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
     for (int u = 0; u < P; ++u) {
         const int ky = i + T * u;
         if (ql != 0) {
-            base[(size_t)ky * Wh + kx] = v[u];
+            out.put(base, t, (int64_t)ky * Wh + kx, v[u]);
         } else {
             const float2 c = v[u];
             const float2 cr = xs[addr((H - ky) & (H - 1))];
             // F0 = (C[ky] + conj C[-ky]) / 2 ; FN = (C[ky] - conj C[-ky]) / (2i)
-            base[(size_t)ky * Wh] = make_float2(0.5f * (c.x + cr.x), 0.5f * (c.y - cr.y));
-            base[(size_t)H * Wh + ky] = make_float2(0.5f * (c.y + cr.y), 0.5f * (cr.x - c.x));
+            out.put(base, t, (int64_t)ky * Wh, make_float2(0.5f * (c.x + cr.x), 0.5f * (c.y - cr.y)));
+            out.put(base, t, (int64_t)H * Wh + ky, make_float2(0.5f * (c.y + cr.y), 0.5f * (cr.x - c.x)));
         }
     }
 }
@@ -247,7 +252,7 @@ cudaError_t launch_rows(const ddm_plan_s* p, const void* frames, float2* spec, c
 }
 
 template <int H>
-cudaError_t launch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
+cudaError_t launch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out) {
     using S = FftShape<H>;
     const int Wh = p->Wh, N = p->d.N;
     const size_t frame_stride = spectrum_frame_stride(p);
@@ -257,7 +262,7 @@ cudaError_t launch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
         const size_t smem = sizeof(float2) * ((S::T > 1 ? H : 0) + (size_t)H * QC);
         auto k = col_c2c_kernel<H, QC>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, QC * S::T, smem, s>>>(spec, Wh, frame_stride, p->tw_col);
+        k<<<grid, QC * S::T, smem, s>>>(spec, Wh, frame_stride, p->tw_col, out);
         return cudaGetLastError();
     };
     if (Wh >= 16) return go(std::integral_constant<int, 16>{});
@@ -284,18 +289,18 @@ cudaError_t dispatch_rows(const ddm_plan_s* p, const void* frames, float2* spec,
     }
 }
 
-cudaError_t dispatch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
+cudaError_t dispatch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out = {}) {
     switch (p->d.H) {
-        case 2: return launch_cols<2>(p, spec, s);
-        case 4: return launch_cols<4>(p, spec, s);
-        case 8: return launch_cols<8>(p, spec, s);
-        case 16: return launch_cols<16>(p, spec, s);
-        case 32: return launch_cols<32>(p, spec, s);
-        case 64: return launch_cols<64>(p, spec, s);
-        case 128: return launch_cols<128>(p, spec, s);
-        case 256: return launch_cols<256>(p, spec, s);
-        case 512: return launch_cols<512>(p, spec, s);
-        case 1024: return launch_cols<1024>(p, spec, s);
+        case 2: return launch_cols<2>(p, spec, s, out);
+        case 4: return launch_cols<4>(p, spec, s, out);
+        case 8: return launch_cols<8>(p, spec, s, out);
+        case 16: return launch_cols<16>(p, spec, s, out);
+        case 32: return launch_cols<32>(p, spec, s, out);
+        case 64: return launch_cols<64>(p, spec, s, out);
+        case 128: return launch_cols<128>(p, spec, s, out);
+        case 256: return launch_cols<256>(p, spec, s, out);
+        case 512: return launch_cols<512>(p, spec, s, out);
+        case 1024: return launch_cols<1024>(p, spec, s, out);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -312,7 +317,10 @@ cudaError_t launch_rows_bulk(const ddm_plan_s* p, const void* frames, float2* sp
 // Path: Bluestein transforms where a side is not a power of two; DDM_SPATIAL_FUSED (cluster
 // kernel) where supported and asked for; otherwise the
 // row pass (bulk-staged where rows allow it) followed by the column pass.
-ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
+ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s,
+                          float2* blk_out, bool* wrote_blocked) {
+    if (wrote_blocked) *wrote_blocked = false;
+    const SpecOut out{blk_out, p->d.N, p->q0, p->q1};
     if (p->kc > 0) {
         // low-frequency restriction: bulk-staged row pass into the intermediate, then the
         // cropping column pass
@@ -335,8 +343,9 @@ ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
             e = (p->d.dtype == DDM_IN_U16) ? dispatch_rows<uint16_t>(p, frames, spec, s)
                                            : dispatch_rows<float>(p, frames, spec, s);
         if (e != cudaSuccess) return DDM_ERR_CUDA;
-        e = p->mix_h.n > 0 ? launch_cols_mixed(p, spec, s)
-            : p->blue_h.M > 0 ? launch_cols_bluestein(p, spec, s) : dispatch_cols(p, spec, s);
+        e = p->mix_h.n > 0 ? launch_cols_mixed(p, spec, s, out)
+            : p->blue_h.M > 0 ? launch_cols_bluestein(p, spec, s, out) : dispatch_cols(p, spec, s, out);
+        if (e == cudaSuccess && wrote_blocked) *wrote_blocked = blk_out != nullptr;
         return e == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
     }
     if (p->d.spatial_path == DDM_SPATIAL_FUSED && fused_spatial_supported(p) &&
@@ -349,7 +358,8 @@ ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
         e = (p->d.dtype == DDM_IN_U16) ? dispatch_rows<uint16_t>(p, frames, spec, s)
                                        : dispatch_rows<float>(p, frames, spec, s);
     if (e != cudaSuccess) return DDM_ERR_CUDA;
-    e = dispatch_cols(p, spec, s);
+    e = dispatch_cols(p, spec, s, out);
+    if (e == cudaSuccess && wrote_blocked) *wrote_blocked = blk_out != nullptr;
     return e == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 

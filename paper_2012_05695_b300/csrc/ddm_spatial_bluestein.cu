@@ -156,7 +156,8 @@ row_bluestein_kernel(const In* __restrict__ frames, float2* __restrict__ spec, i
 // grid: (ceil(Wh / QT), N); block: 256.  In place, QT stored columns of one frame.
 template <int M, bool DIRECT>
 __global__ void __launch_bounds__(256, 2)
-col_bluestein_kernel(float2* __restrict__ spec, int H, int Wh, size_t frame_stride, ddm_bluestein b) {
+col_bluestein_kernel(float2* __restrict__ spec, int H, int Wh, size_t frame_stride, ddm_bluestein b,
+                     SpecOut out) {
     using C = BShape<M>;
     constexpr int T = C::T, QT = C::QT, NT = C::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -198,7 +199,7 @@ col_bluestein_kernel(float2* __restrict__ spec, int H, int Wh, size_t frame_stri
 #pragma unroll
             for (int u = 0; u < 32; ++u) {
                 const int ky = li + T * u;
-                if (ky < H) base[(size_t)ky * Wh + kx] = v[u];
+                if (ky < H) out.put(base, t, (int64_t)ky * Wh + kx, v[u]);
             }
         }
         return;
@@ -216,12 +217,12 @@ col_bluestein_kernel(float2* __restrict__ spec, int H, int Wh, size_t frame_stri
         const int ky = li + T * u;
         if (ky >= H) continue;
         if (ql != 0) {
-            base[(size_t)ky * Wh + kx] = v[u];
+            out.put(base, t, (int64_t)ky * Wh + kx, v[u]);
         } else {
             const float2 c = v[u];
             const float2 cr = xs[(ky == 0 ? 0 : H - ky) * QT];
-            base[(size_t)ky * Wh] = make_float2(0.5f * (c.x + cr.x), 0.5f * (c.y - cr.y));
-            base[(size_t)H * Wh + ky] = make_float2(0.5f * (c.y + cr.y), 0.5f * (cr.x - c.x));
+            out.put(base, t, (int64_t)ky * Wh, make_float2(0.5f * (c.x + cr.x), 0.5f * (c.y - cr.y)));
+            out.put(base, t, (int64_t)H * Wh + ky, make_float2(0.5f * (c.y + cr.y), 0.5f * (cr.x - c.x)));
         }
     }
 }
@@ -245,14 +246,14 @@ cudaError_t rows_t(const ddm_plan_s* p, const void* frames, float2* spec, cudaSt
 }
 
 template <int M, bool DIRECT = false>
-cudaError_t cols_t(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
+cudaError_t cols_t(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out) {
     using C = BShape<M>;
     auto k = col_bluestein_kernel<M, DIRECT>;
     const size_t smem = bluestein_smem<M>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((p->Wh + C::QT - 1) / C::QT, p->d.N);
-    k<<<grid, C::NT, smem, s>>>(spec, p->d.H, p->Wh, (size_t)p->n_q, p->blue_h);
+    k<<<grid, C::NT, smem, s>>>(spec, p->d.H, p->Wh, (size_t)p->n_q, p->blue_h, out);
     return cudaGetLastError();
 }
 
@@ -279,17 +280,17 @@ cudaError_t launch_rows_bluestein(const ddm_plan_s* p, const void* frames, float
                                     : rows_dispatch<float>(p, frames, spec, s);
 }
 
-cudaError_t launch_cols_bluestein(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
-    if (p->blue_h.M == p->blue_h.n) return p->blue_h.M == 2048 ? cols_t<2048, true>(p, spec, s)
+cudaError_t launch_cols_bluestein(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out) {
+    if (p->blue_h.M == p->blue_h.n) return p->blue_h.M == 2048 ? cols_t<2048, true>(p, spec, s, out)
                                                                 : cudaErrorInvalidValue;
     switch (p->blue_h.M) {
-        case 32: return cols_t<32>(p, spec, s);
-        case 64: return cols_t<64>(p, spec, s);
-        case 128: return cols_t<128>(p, spec, s);
-        case 256: return cols_t<256>(p, spec, s);
-        case 512: return cols_t<512>(p, spec, s);
-        case 1024: return cols_t<1024>(p, spec, s);
-        case 2048: return cols_t<2048>(p, spec, s);
+        case 32: return cols_t<32>(p, spec, s, out);
+        case 64: return cols_t<64>(p, spec, s, out);
+        case 128: return cols_t<128>(p, spec, s, out);
+        case 256: return cols_t<256>(p, spec, s, out);
+        case 512: return cols_t<512>(p, spec, s, out);
+        case 1024: return cols_t<1024>(p, spec, s, out);
+        case 2048: return cols_t<2048>(p, spec, s, out);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -137,7 +137,8 @@ row_mixed_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H
 // grid: (ceil(Wh / QT), N); block: 256.  In place, QT stored columns of one frame.
 template <int P, int T>
 __global__ void __launch_bounds__(256)
-col_mixed_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride, const float2* __restrict__ tw_g) {
+col_mixed_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride, const float2* __restrict__ tw_g,
+                 SpecOut out) {
     using C = MShape<P, T>;
     constexpr int H = C::N, QT = C::QT, NT = C::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -156,10 +157,11 @@ col_mixed_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride, const f
     for (int u = 0; u < P; ++u) v[u] = valid ? base[(size_t)(i + T * u) * Wh + kx] : make_float2(0.f, 0.f);
     fft_mixed<P, T>(v, w, i, ql, live, xs, tw);
     const bool holds = live && i < P;                       // holds X[i + P k2], k2 < T
+    const int t = blockIdx.y;
     if (blockIdx.x != 0) {
         if (holds && kx < Wh) {
 #pragma unroll
-            for (int k2 = 0; k2 < T; ++k2) base[(size_t)(i + P * k2) * Wh + kx] = w[k2];
+            for (int k2 = 0; k2 < T; ++k2) out.put(base, t, (int64_t)(i + P * k2) * Wh + kx, w[k2]);
         }
         return;
     }
@@ -174,12 +176,12 @@ col_mixed_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride, const f
     for (int k2 = 0; k2 < T; ++k2) {
         const int ky = i + P * k2;
         if (ql != 0) {
-            base[(size_t)ky * Wh + kx] = w[k2];
+            out.put(base, t, (int64_t)ky * Wh + kx, w[k2]);
         } else {
             const float2 c = w[k2];
             const float2 cr = xs[(ky == 0 ? 0 : H - ky) * QT];
-            base[(size_t)ky * Wh] = make_float2(0.5f * (c.x + cr.x), 0.5f * (c.y - cr.y));
-            base[(size_t)H * Wh + ky] = make_float2(0.5f * (c.y + cr.y), 0.5f * (cr.x - c.x));
+            out.put(base, t, (int64_t)ky * Wh, make_float2(0.5f * (c.x + cr.x), 0.5f * (c.y - cr.y)));
+            out.put(base, t, (int64_t)H * Wh + ky, make_float2(0.5f * (c.y + cr.y), 0.5f * (cr.x - c.x)));
         }
     }
 }
@@ -197,13 +199,13 @@ cudaError_t rows_t(const ddm_plan_s* p, const void* frames, float2* spec, cudaSt
 }
 
 template <int P, int T>
-cudaError_t cols_t(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
+cudaError_t cols_t(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out) {
     using C = MShape<P, T>;
     auto k = col_mixed_kernel<P, T>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
     if (e != cudaSuccess) return e;
     dim3 grid((p->Wh + C::QT - 1) / C::QT, p->d.N);
-    k<<<grid, C::NT, C::BYTES, s>>>(spec, p->Wh, (size_t)p->n_q, p->mix_h.tw);
+    k<<<grid, C::NT, C::BYTES, s>>>(spec, p->Wh, (size_t)p->n_q, p->mix_h.tw, out);
     return cudaGetLastError();
 }
 
@@ -251,19 +253,19 @@ cudaError_t launch_rows_mixed(const ddm_plan_s* p, const void* frames, float2* s
                                     : rows_dispatch<float>(p, frames, spec, s);
 }
 
-cudaError_t launch_cols_mixed(const ddm_plan_s* p, float2* spec, cudaStream_t s) {
+cudaError_t launch_cols_mixed(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out) {
     switch (p->d.H) {
-        case 384: return cols_t<12, 32>(p, spec, s);
-        case 480: return cols_t<15, 32>(p, spec, s);
-        case 540: return cols_t<18, 30>(p, spec, s);
-        case 600: return cols_t<24, 25>(p, spec, s);
-        case 640: return cols_t<20, 32>(p, spec, s);
-        case 720: return cols_t<24, 30>(p, spec, s);
-        case 768: return cols_t<24, 32>(p, spec, s);
-        case 800: return cols_t<25, 32>(p, spec, s);
-        case 900: return cols_t<30, 30>(p, spec, s);
-        case 960: return cols_t<30, 32>(p, spec, s);
-        case 1000: return cols_t<25, 40>(p, spec, s);
+        case 384: return cols_t<12, 32>(p, spec, s, out);
+        case 480: return cols_t<15, 32>(p, spec, s, out);
+        case 540: return cols_t<18, 30>(p, spec, s, out);
+        case 600: return cols_t<24, 25>(p, spec, s, out);
+        case 640: return cols_t<20, 32>(p, spec, s, out);
+        case 720: return cols_t<24, 30>(p, spec, s, out);
+        case 768: return cols_t<24, 32>(p, spec, s, out);
+        case 800: return cols_t<25, 32>(p, spec, s, out);
+        case 900: return cols_t<30, 30>(p, spec, s, out);
+        case 960: return cols_t<30, 32>(p, spec, s, out);
+        case 1000: return cols_t<25, 40>(p, spec, s, out);
         default: return cudaErrorInvalidValue;
     }
 }

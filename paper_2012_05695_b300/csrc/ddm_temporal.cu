@@ -1411,12 +1411,14 @@ bool make_blocked_map(CUtensorMap* map, const float2* blk, int64_t nb, int N, in
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The blocked copy of [q0, q1) in the plan workspace, or nullptr when the plan does not use it
-// (or has no workspace yet: the kernels then read the [t][q] spectrum).
-float2* blocked_copy(const ddm_plan_s* p, const float2* spec, cudaStream_t s, bool* ok) {
+// The blocked copy of [q0, q1) in the plan workspace (made here unless step one wrote it:
+// pre), or nullptr when the plan does not use it (or has no workspace yet: the kernels then
+// read the [t][q] spectrum).
+float2* blocked_copy(const ddm_plan_s* p, const float2* spec, cudaStream_t s, bool pre, bool* ok) {
     *ok = true;
     if (!p->blocked || !p->workspace) return nullptr;
     float2* blk = reinterpret_cast<float2*>(static_cast<char*>(p->workspace) + p->blk_offset);
+    if (pre) return blk;                               // step one wrote the blocks already
     const int64_t nb = (p->q1 - p->q0 + 15) / 16;
     dim3 grid((unsigned)nb, (unsigned)((p->d.N + 255) / 256));
     blocked_copy_kernel<<<grid, 256, 0, s>>>(spec, blk, p->d.N, p->n_q, p->q0, p->q1);
@@ -1477,11 +1479,11 @@ ddm_status launch_grouped(const ddm_plan_s* p, const float2* spec, float* D, cud
 }
 
 template <int LOG2L, bool FIXUP>
-ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
+ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s, bool pre_blocked) {
     using C = LShape<LOG2L>;
     if ((reinterpret_cast<uintptr_t>(spec) & 15) != 0 || !p->tw_tin || !p->tw_long) return DDM_ERR_INVALID_ARG;
     bool ok = true;
-    const float2* blk = blocked_copy(p, spec, s, &ok);
+    const float2* blk = blocked_copy(p, spec, s, pre_blocked, &ok);
     if (!ok) return DDM_ERR_CUDA;
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof(tmap));
@@ -1509,11 +1511,11 @@ ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaSt
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 
-ddm_status launch_xl(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
+ddm_status launch_xl(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s, bool pre_blocked) {
     using C = XLShape;
     if (!p->tw_tin || !p->tw_long || p->L != C::L) return DDM_ERR_INVALID_ARG;
     bool ok = true;
-    const float2* blk = blocked_copy(p, spec, s, &ok);
+    const float2* blk = blocked_copy(p, spec, s, pre_blocked, &ok);
     if (!ok) return DDM_ERR_CUDA;
     if (blk) spec = blk;
     TArgs a;
@@ -1558,7 +1560,7 @@ cudaError_t launch_wait_selftest(unsigned* status, long long cap_cycles, cudaStr
     return cudaGetLastError();
 }
 
-ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
+ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s, bool pre_blocked) {
     const bool fix = p->d.precision == DDM_PREC_FP32_FP64FIX;
     switch (ilog2(p->L)) {
         case 0: return launch_small<0>(p, spec, D, s);
@@ -1575,10 +1577,10 @@ ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cu
         // rows, lockstep) 1.13 ms, 2 groups 1.05 ms, 4 groups (32-byte rows) 1.15 ms.
         case 9: return fix ? launch_grouped<9, true, 4>(p, spec, D, s) : launch_grouped<9, false, 4>(p, spec, D, s);
         case 10: return fix ? launch_grouped<10, true, 2>(p, spec, D, s) : launch_grouped<10, false, 2>(p, spec, D, s);
-        case 11: return fix ? launch_long<11, true>(p, spec, D, s) : launch_long<11, false>(p, spec, D, s);
-        case 12: return fix ? launch_long<12, true>(p, spec, D, s) : launch_long<12, false>(p, spec, D, s);
-        case 13: return fix ? launch_long<13, true>(p, spec, D, s) : launch_long<13, false>(p, spec, D, s);
-        case 14: return fix ? DDM_ERR_UNSUPPORTED : launch_xl(p, spec, D, s);
+        case 11: return fix ? launch_long<11, true>(p, spec, D, s, pre_blocked) : launch_long<11, false>(p, spec, D, s, pre_blocked);
+        case 12: return fix ? launch_long<12, true>(p, spec, D, s, pre_blocked) : launch_long<12, false>(p, spec, D, s, pre_blocked);
+        case 13: return fix ? launch_long<13, true>(p, spec, D, s, pre_blocked) : launch_long<13, false>(p, spec, D, s, pre_blocked);
+        case 14: return fix ? DDM_ERR_UNSUPPORTED : launch_xl(p, spec, D, s, pre_blocked);
         default: return DDM_ERR_UNSUPPORTED;
     }
 }

@@ -375,3 +375,45 @@ def test_temporal_blocked_copy_matches_oracle(S, N, kw):
     Dg = D.view(nq, N)[torch.from_numpy(rows).cuda()].cpu().numpy()
     assert np.all(Dg[:, 0] == 0)
     assert oracle.scaled_error(Dg, D_ref, oracle.plateau_scale(F)) <= TOL
+
+
+@pytest.mark.parametrize("H,W,N,dtype,kw", [
+    (512, 1024, 2048, "u16", {}),                                  # power-of-two columns
+    (1022, 400, 2048, "f32", {}),                                  # Bluestein rows and columns
+    (512, 1024, 2048, "u16", {"q_begin": 64, "q_end": 200007}),    # range ending mid-block
+])
+def test_structure_function_blocked_write_matches_oracle(H, W, N, dtype, kw):
+    """n_q >= 200000 at L = 2048: step one's column pass writes the time kernels' blocked
+    copy directly (no corner-turn pass).  Random frames; the oracle on sampled (ky, kx)."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(H + W + N))
+    if dtype == "u16":
+        frames = rng.integers(1800, 2201, size=(N, H, W), dtype=np.uint16)
+    else:
+        frames = rng.uniform(-1.0, 1.0, size=(N, H, W)).astype(np.float32)
+    plan = ddm.Plan(H, W, N, dtype=dtype, **kw)
+    D = torch.full((plan.n_q * N,), float("nan"), device="cuda")
+    plan.structure_function(to_device(frames), D)
+    torch.cuda.synchronize()
+    assert plan.last_device_status() == 0
+    Wq = W // 2 + 1
+    kx_sel = [0, 1, 7, W // 2]
+    ky_sel = [0, 1, H // 2 - 1, H // 2, H - 1]
+    F = oracle.dft2(frames, kx_sel)[:, ky_sel, :]                  # [N, 5, 4]
+    D_ref = oracle.sf_direct(F)                                    # [5, 4, N]
+    s_q = oracle.plateau_scale(F)
+    Dg = D.view(plan.n_q, N).cpu().numpy()
+    sky, skx = (np.asarray(a) for a in ddm.spectrum_index_map(H, W))
+    stored = {(int(a), int(b)): s for s, (a, b) in enumerate(zip(sky, skx))}
+    q0, q1 = kw.get("q_begin", 0), kw.get("q_end", plan.n_q)
+    checked = 0
+    for a, ky in enumerate(ky_sel):
+        for b, kx in enumerate(kx_sel):
+            if not (q0 <= stored[(ky, kx)] < q1):
+                continue
+            row = Dg[ky * Wq + kx]
+            assert row[0] == 0
+            err = np.max(np.abs(row - D_ref[a, b])) / s_q[a, b]
+            assert err <= TOL, (ky, kx, err)
+            checked += 1
+    assert checked >= 5
