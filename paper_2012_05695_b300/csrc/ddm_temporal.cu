@@ -794,22 +794,29 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             xf[(t + (t >> 5)) * QG + ql] = e[u];
         }
         __syncthreads();
-        // ---- inclusive prefix sums: thread i owns frames 32 i .. 32 i + 31
+        // ---- inclusive prefix sums: thread i owns frames 32 i .. 32 i + 31; the offsets of
+        // the chunks by a shuffle scan within the warp (lanes of one wave vector are QG apart)
+        // and the warps' totals
         float rowv[P];
-        {
-            float acc = 0.f;
+        float acc = 0.f;
 #pragma unroll
-            for (int jj = 0; jj < P; ++jj) {
-                acc += xf[(i * (P + 1) + jj) * QG + ql];
-                rowv[jj] = acc;
-            }
-            red[i * QG + ql] = acc;
+        for (int jj = 0; jj < P; ++jj) {
+            acc += xf[(i * (P + 1) + jj) * QG + ql];
+            rowv[jj] = acc;
         }
+        float incl = acc;
+#pragma unroll
+        for (int o = QG; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane >= 32 - QG) red[wg * QG + ql] = incl;     // the warp's last chunk of ql
         __syncthreads();
-        float total = 0.f, off = 0.f;
-        for (int c = 0; c < T; ++c) {
-            const float x = red[c * QG + ql];
-            if (c < i) off += x;
+        float total = 0.f, off = incl - acc;
+#pragma unroll
+        for (int w = 0; w < NWG; ++w) {
+            const float x = red[w * QG + ql];
+            if (w < wg) off += x;
             total += x;
         }
 #pragma unroll
