@@ -432,6 +432,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
         sync();
         // ---- inclusive prefix sums S(t): thread i owns the rows r = i + T g of T frames
         float rowv[G][T];
+        float racc[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int r = i + T * g;
@@ -441,20 +442,41 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
                 acc += xf[(r * (T + 1) + jj) * QG + ql];
                 rowv[g][jj] = acc;
             }
-            red[r * QG + ql] = acc;
+            racc[g] = acc;
+            if constexpr (G > 1) red[r * QG + ql] = acc;
         }
-        sync();
         float total = 0.f;
         float off[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) off[g] = 0.f;
+        if constexpr (G == 1) {
+            // one row per thread (rows in thread order): a shuffle scan within the warp (lanes
+            // of one wave vector QG apart) and the warps' totals
+            float incl = racc[0];
 #pragma unroll
-        for (int rp = 0; rp < P; ++rp) {
-            const float x = red[rp * QG + ql];
+            for (int o = QG; o < 32; o <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane >= 32 - QG) red[wg * QG + ql] = incl;
+            sync();
+            off[0] = incl - racc[0];
 #pragma unroll
-            for (int g = 0; g < G; ++g)
-                if (rp < i + T * g) off[g] += x;
-            total += x;
+            for (int w = 0; w < NWG; ++w) {
+                const float x = red[w * QG + ql];
+                if (w < wg) off[0] += x;
+                total += x;
+            }
+        } else {
+            sync();
+#pragma unroll
+            for (int rp = 0; rp < P; ++rp) {
+                const float x = red[rp * QG + ql];
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (rp < i + T * g) off[g] += x;
+                total += x;
+            }
         }
 #pragma unroll
         for (int g = 0; g < G; ++g) {
