@@ -41,7 +41,7 @@ extern "C" {
 typedef enum ddm_status {
     DDM_OK = 0,
     DDM_ERR_INVALID_ARG = 1,   /* bad pointer, size or descriptor field */
-    DDM_ERR_UNSUPPORTED = 2,   /* legal request this build does not implement */
+    DDM_ERR_UNSUPPORTED = 2,   /* legal request this library does not implement */
     DDM_ERR_OOM = 3,           /* device allocation failed or exceeds max_workspace_bytes */
     DDM_ERR_CUDA = 4,          /* a CUDA runtime call failed (no device, launch error) */
     DDM_ERR_TIMEOUT = 5,       /* a bounded device wait (tile copy) gave up */
@@ -57,11 +57,11 @@ typedef enum ddm_precision {
     DDM_PREC_FP32_FP64FIX = 1, /* as FP32, plus: lags 1..fix_lags recomputed by direct
                                  differences (Eq. 1), FP32 over each thread's 32 frames and
                                  FP64 across threads: no cancellation against the power
-                                 sums.  This build: 257 <= N <= 8192, fix_lags <= 8 */
+                                 sums.  Implemented for 257 <= N <= 8192, fix_lags <= 8 */
     DDM_PREC_FP64 = 2    /* everything in FP64 on the GPU (the precision sweep's reference
                             tier; D is still written as float32): spatial and time
                             transforms, power sums and combination.  About 1/64 of the
-                            FP32 rate.  This build: power-of-two sides, N <= 4096, kmax = 0,
+                            FP32 rate.  Implemented for power-of-two sides, N <= 4096, kmax = 0,
                             the whole wave-vector range, ddm_structure_function only
                             (ddm_spatial_fft / ddm_temporal_sf / the static entry return
                             DDM_ERR_UNSUPPORTED: the spectrum workspace is complex128) */
@@ -87,7 +87,7 @@ typedef struct ddm_plan_desc {
     int dtype;         /* ddm_dtype */
     int precision;     /* ddm_precision */
     int M;             /* temporal pad length; 0 = N_2 of Eq. B4.  Any M >= 2N-1 gives
-                          the same D (App. B); this build accepts 0 or N_2 and returns
+                          the same D (App. B); the library accepts 0 or N_2 and returns
                           DDM_ERR_INVALID_ARG for M < 2N-1, DDM_ERR_UNSUPPORTED otherwise */
     int n_bins;        /* radial bins for ddm_azimuthal_average (0 = no radial stage) */
     int subtract_ref;  /* 1: subtract frame 0 from every frame before the spatial
@@ -112,7 +112,7 @@ typedef struct ddm_plan_desc {
                           [N][n_q], n_q = (2 kmax + 1)(kmax + 1), stored order
                           ky' = 0..kmax, -kmax..-1 (outer) by kx = 0..kmax (inner); D rows
                           follow the same order.  kmax must be odd and below H/2 and W/2
-                          (DDM_ERR_INVALID_ARG otherwise); this build crops only frames
+                          (DDM_ERR_INVALID_ARG otherwise); the library crops only frames
                           whose sides are powers of two (DDM_ERR_UNSUPPORTED otherwise).
                           The plan then also owns an
                           intermediate of N * H * (kmax + 1) complex64 for step one */
@@ -123,7 +123,7 @@ typedef struct ddm_plan_s* ddm_plan;
 /* Library version of this header's ABI. */
 int ddm_abi_version(void);
 
-/* sizeof(ddm_plan_desc) in this build: a binding checks its mirror of the struct against it. */
+/* sizeof(ddm_plan_desc) in this library: a binding checks its mirror of the struct against it. */
 size_t ddm_plan_desc_size(void);
 
 /* Static, never NULL. */

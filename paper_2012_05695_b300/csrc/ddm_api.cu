@@ -294,7 +294,7 @@ const char* ddm_status_string(ddm_status s) {
     switch (s) {
         case DDM_OK: return "ok";
         case DDM_ERR_INVALID_ARG: return "invalid argument";
-        case DDM_ERR_UNSUPPORTED: return "unsupported by this build";
+        case DDM_ERR_UNSUPPORTED: return "unsupported by this library";
         case DDM_ERR_OOM: return "out of device memory or over the workspace limit";
         case DDM_ERR_CUDA: return "CUDA runtime error";
         case DDM_ERR_TIMEOUT: return "bounded device wait timed out";

@@ -1,6 +1,6 @@
 // The fit seed network: MLP 64 -> 128 -> 128 -> 128 -> 4, GELU (erf form) on the hidden
 // layers, trained with Adam.  Not in the paper: it seeds the Levenberg-Marquardt fit of
-// D(|q|, dt) (ddm_fit.cu), which stays the judge.
+// D(|q|, dt) (ddm_fit.cu), which has the final say.
 //
 // Precision: FP32 master weights, gradients and Adam moments; the weight matrices are
 // used rounded to bfloat16 (a transposed bf16 copy, rebuilt after every Adam step);
