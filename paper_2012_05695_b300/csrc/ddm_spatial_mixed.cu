@@ -71,7 +71,23 @@ __device__ __forceinline__ void fft_mixed(float2 (&v)[P], float2 (&w)[T], int i,
 
 // ---------------------------------------------------------------- rows (W = P T)
 // grid: (ceil(H/2 / QT), N); block: 256.  CTA: QT row pairs of one frame.
-template <int P, int T, typename In>
+// four consecutive pixels by one 8-byte (uint16) or 16-byte (float) load
+__device__ __forceinline__ void load4(const uint16_t* p, float (&f)[4]) {
+    const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+    f[0] = (float)(r.x & 0xffffu);
+    f[1] = (float)(r.x >> 16);
+    f[2] = (float)(r.y & 0xffffu);
+    f[3] = (float)(r.y >> 16);
+}
+__device__ __forceinline__ void load4(const float* p, float (&f)[4]) {
+    const float4 r = __ldg(reinterpret_cast<const float4*>(p));
+    f[0] = r.x;
+    f[1] = r.y;
+    f[2] = r.z;
+    f[3] = r.w;
+}
+
+template <int P, int T, typename In, bool VEC>
 __global__ void __launch_bounds__(256)
 row_mixed_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H, size_t frame_stride,
                  int subtract_ref, const float2* __restrict__ tw_g) {
@@ -87,19 +103,52 @@ row_mixed_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H
     const int npairs = min(QT, H / 2 - pair0);
     const In* src = frames + ((size_t)t * H + 2 * pair0) * W;
     const In* ref = frames + (size_t)(2 * pair0) * W;
+    if constexpr (VEC) {
+        // four pixels of rows 2q and 2q + 1 per thread and iteration: a warp moves 256 B (uint16)
+        // or 512 B (float) of each row per load, enough bytes in flight to cover HBM latency.  The
+        // 32 B of four staged pairs go out as two 16 B halves; a quad whose 32 B chunk lies at an
+        // odd multiple of 128 B writes its upper half first, so that each store by a warp meets all
+        // 32 banks.  The differences of integers below 2^16 are exact in float, as on the scalar path.
+        static_assert(W % 4 == 0 && WS % 4 == 0, "vector staging: W and WS multiples of 4");
+        constexpr int W4 = W / 4;
 #pragma unroll 4
-    for (int e = tid; e < npairs * W; e += NT) {            // 4 iterations of loads in flight
-        const int q = e / W, x = e - q * W;
-        const size_t ia = (size_t)(2 * q) * W + x, ib = ia + W;
-        float a, b;
-        if constexpr (sizeof(In) == 2) {
-            a = (float)((int)__ldg(src + ia) - (subtract_ref ? (int)__ldg(ref + ia) : 0));
-            b = (float)((int)__ldg(src + ib) - (subtract_ref ? (int)__ldg(ref + ib) : 0));
-        } else {
-            a = subtract_ref ? __ldg(src + ia) - __ldg(ref + ia) : __ldg(src + ia);
-            b = subtract_ref ? __ldg(src + ib) - __ldg(ref + ib) : __ldg(src + ib);
+        for (int e = tid; e < npairs * W4; e += NT) {
+            const int q = e / W4, x4 = e - q * W4, x = 4 * x4;
+            const size_t ia = (size_t)(2 * q) * W + x, ib = ia + W;
+            float a[4], b[4];
+            load4(src + ia, a);
+            load4(src + ib, b);
+            if (subtract_ref) {
+                float ra[4], rb[4];
+                load4(ref + ia, ra);
+                load4(ref + ib, rb);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    a[j] -= ra[j];
+                    b[j] -= rb[j];
+                }
+            }
+            const float4 lo = make_float4(a[0], b[0], a[1], b[1]), hi = make_float4(a[2], b[2], a[3], b[3]);
+            float4* dst = reinterpret_cast<float4*>(xs + q * WS + x);
+            const int h = ((q * (WS / 4) + x4) >> 2) & 1;
+            dst[h] = h ? hi : lo;
+            dst[1 - h] = h ? lo : hi;
         }
-        xs[q * WS + x] = make_float2(a, b);
+    } else {
+#pragma unroll 4
+        for (int e = tid; e < npairs * W; e += NT) {        // 4 iterations of loads in flight
+            const int q = e / W, x = e - q * W;
+            const size_t ia = (size_t)(2 * q) * W + x, ib = ia + W;
+            float a, b;
+            if constexpr (sizeof(In) == 2) {
+                a = (float)((int)__ldg(src + ia) - (subtract_ref ? (int)__ldg(ref + ia) : 0));
+                b = (float)((int)__ldg(src + ib) - (subtract_ref ? (int)__ldg(ref + ib) : 0));
+            } else {
+                a = subtract_ref ? __ldg(src + ia) - __ldg(ref + ia) : __ldg(src + ia);
+                b = subtract_ref ? __ldg(src + ib) - __ldg(ref + ib) : __ldg(src + ib);
+            }
+            xs[q * WS + x] = make_float2(a, b);
+        }
     }
     __syncthreads();
     const int ql = tid % QT, i = tid / QT;
@@ -189,7 +238,9 @@ col_mixed_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride, const f
 template <int P, int T, typename In>
 cudaError_t rows_t(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
     using C = MShape<P, T>;
-    auto k = row_mixed_kernel<P, T, In>;
+    // vector staging needs the frames 4-pixel aligned (every row offset is: W is a multiple of 4)
+    const bool vec = reinterpret_cast<uintptr_t>(frames) % (4 * sizeof(In)) == 0;
+    auto k = vec ? row_mixed_kernel<P, T, In, true> : row_mixed_kernel<P, T, In, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
     if (e != cudaSuccess) return e;
     dim3 grid((p->d.H / 2 + C::QT - 1) / C::QT, p->d.N);
