@@ -212,6 +212,53 @@ def oracle_sample(frames, cols, nthreads):
     return time.perf_counter() - t0, D, s_q
 
 
+def time_mlp_forward(mlp, x, sizes, reps=50):
+    """Device time of the MLP forward (tensor cores), per batch size: a CUDA graph of `reps`
+    calls replayed under CUDA events, so that the Python call path is not timed.  Roofline:
+    the network's algorithmic FLOPs (one pass, 2 B (64*128 + 2*128*128 + 128*4)) over the
+    measured bf16 tensor peak."""
+    import torch
+    peak = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    s = torch.cuda.Stream()
+    res = {}
+    for Bn in sizes:
+        xb = x[:Bn * 64]
+        o = torch.empty(Bn * 4, device="cuda")
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                mlp.forward(xb, Bn, o, s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+            for _ in range(reps):
+                mlp.forward(xb, Bn, o, s)
+        ts = []
+        with torch.cuda.stream(s):          # replay() launches on the current stream
+            for _ in range(3):
+                g.replay()
+            torch.cuda.synchronize()
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                g.replay()
+                e1.record(s)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e3 / reps)
+        us = statistics.median(ts)
+        flops = 2.0 * Bn * (64 * 128 + 2 * 128 * 128 + 128 * 4)
+        tf = flops / (us * 1e-6) / 1e12
+        res[str(Bn)] = {"us": us, "ctas": (Bn + 127) // 128, "tflops": tf,
+                        "frac_of_bf16_peak": (tf / peak) if peak else None}
+    res["peak_bf16_tflops"] = peak
+    res["bound"] = "latency: one 128-sample CTA per SM runs three dependent MMA batches"
+    assert mlp.last_device_status() == 0
+    return res
+
+
 def compare_fits(ddm, plan, Dr, stream):
     """Train the seed network on synthetic curves (library kernels), then fit the stack's
     radial curves with plain LM and with the MLP seed; times and iteration counts."""
@@ -265,7 +312,8 @@ def compare_fits(ddm, plan, Dr, stream):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     out = {"train_steps": steps, "train_batch": batch, "train_s": train_s,
-           "train_loss": float(loss.item()), "curves": N_BINS}
+           "train_loss": float(loss.item()), "curves": N_BINS,
+           "mlp_forward": time_mlp_forward(mlp, x, (N_BINS, batch))}
     for name, mode, net in (("lm", B_.DDM_FIT_LM, None), ("mlp_lm", B_.DDM_FIT_MLP_LM, mlp)):
         prm = torch.empty(N_BINS * 4, device="cuda")
         cst = torch.empty(N_BINS, device="cuda")

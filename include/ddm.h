@@ -292,8 +292,16 @@ ddm_status ddm_mlp_get_weights(ddm_mlp m, float* host_w);
 #define DDM_MLP_STATE_FLOATS (3 * DDM_MLP_PARAMS + 1)
 ddm_status ddm_mlp_get_state(ddm_mlp m, float* host_state);
 ddm_status ddm_mlp_set_state(ddm_mlp m, const float* host_state);
-/* x [B][64] device -> o [B][4] device (raw outputs, before the head). */
+/* x [B][64] device -> o [B][4] device (raw outputs, before the head); any alignment.  The
+ * hidden layers run on the tensor cores (tcgen05.mma, bf16 operands, FP32 accumulation in
+ * tensor memory), one CTA per 128 samples; each FP32 activation enters as three bf16 terms
+ * that sum to it exactly, so the result is the FP32-activation network's up to FP32 rounding.  The MMA
+ * waits are bounded (about 2 s); one that gives up leaves o unwritten for that CTA's samples
+ * and is reported by ddm_mlp_last_device_status(). */
 ddm_status ddm_mlp_forward(ddm_mlp m, const float* x, int B, float* o, void* stream);
+/* DDM_ERR_TIMEOUT in *out if a bounded wait of a forward pass gave up since the last call,
+ * else DDM_OK; synchronises the device and clears the word. */
+ddm_status ddm_mlp_last_device_status(ddm_mlp m, ddm_status* out);
 /* Loss = mean over the batch of (o0 - t0)^2 + (o1 - t1)^2 + (beta - t2)^2 + (o3 - t3)^2,
  * t [B][4] device targets (ln(A/p8), ln tau, beta, B/A).  grad [DDM_MLP_PARAMS] device and
  * loss [1] device are written (loss may be NULL).  Summation order is fixed. */

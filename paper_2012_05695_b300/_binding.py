@@ -106,6 +106,7 @@ def lib():
         "ddm_mlp_set_weights": (st, [vp, vp]),
         "ddm_mlp_get_weights": (st, [vp, vp]),
         "ddm_mlp_forward": (st, [vp, vp, c_int, vp, vp]),
+        "ddm_mlp_last_device_status": (st, [vp, ctypes.POINTER(ctypes.c_int)]),
         "ddm_mlp_grad": (st, [vp, vp, vp, c_int, vp, vp, vp]),
         "ddm_mlp_train_step": (st, [vp, vp, vp, c_int, ctypes.c_float, vp, vp]),
     }
@@ -371,6 +372,13 @@ class MLP:
         _check(lib().ddm_mlp_forward(self._h, _dev_ptr(x, "x", torch.float32, B * DDM_FIT_LAGS), int(B),
                                      _dev_ptr(o, "o", torch.float32, B * 4), _stream_ptr(stream)),
                "ddm_mlp_forward")
+
+    def last_device_status(self) -> int:
+        """DDM_ERR_TIMEOUT if a bounded MMA wait of a forward pass gave up since the last
+        call, else DDM_OK (synchronises; clears the word)."""
+        out = ctypes.c_int()
+        _check(lib().ddm_mlp_last_device_status(self._h, ctypes.byref(out)), "ddm_mlp_last_device_status")
+        return int(out.value)
 
     def grad(self, x, t, B, grad, loss=None, stream=None):
         import torch

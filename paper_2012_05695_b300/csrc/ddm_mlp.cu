@@ -6,11 +6,16 @@
 // used rounded to bfloat16 (a transposed bf16 copy, rebuilt after every Adam step);
 // biases, activations and every accumulation are FP32.
 //
-// One CTA handles a chunk of kSB samples with all bf16 weights resident in shared memory
-// (83 KB): forward, and for training the backward pass and the chunk's weight-gradient
-// partials.  A second kernel sums the partials over chunks in chunk order (fixed order:
-// bitwise reproducible), a third applies Adam.  The network is tiny (0.34 GFLOP per batch
-// of 4096): CUDA cores, not tensor cores.
+// Inference (ddm_mlp_forward, the fit's seeds) runs the three hidden layers on the
+// 5th-generation tensor cores: tcgen05.mma (kind::f16, bf16 operands, FP32 accumulators in
+// tensor memory), one CTA per 128 samples.  Each FP32 activation enters as three bf16 terms
+// whose sum is exactly the activation (8 + 8 + 8 significand bits), so that every product is
+// exact and the result is the FP32-activation network's to within FP32 accumulation order.
+//
+// Training: one CTA handles a chunk of kSB samples with all bf16 weights resident in shared
+// memory (83 KB): forward, backward pass and the chunk's weight-gradient partials on CUDA
+// cores.  A second kernel sums the partials over chunks in chunk order (fixed order: bitwise
+// reproducible), a third applies Adam.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -43,6 +48,250 @@ constexpr float kInvSqrt2Pi = 0.39894228040143268f;
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * kInvSqrt2)); }
 __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.f + erff(z * kInvSqrt2)) + z * expf(-0.5f * z * z) * kInvSqrt2Pi;
+}
+
+// ---------------------------------------------------------------- tensor-core forward
+// Operand images in shared memory: K-major, no swizzle.  A "core matrix" is 8 rows x 16 bytes
+// (8 bf16 of one row per 16-byte line); the K/8 core matrices of one 8-row group lie 128 B
+// apart (the descriptor's leading byte offset) and consecutive row groups K * 16 B apart (its
+// stride byte offset).  Element (r, k) of an image with K columns:
+__host__ __device__ constexpr int img_at(int r, int k, int K) {
+    return (r >> 3) * (K * 8) + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+constexpr int kTM = 128;                                   // samples per CTA = MMA M = TMEM lanes
+constexpr int kTcThreads = 512;                            // 4 lane quarters x 4 column groups
+constexpr int kColGroups = kTcThreads / kTM;               // 32-column slices of an accumulator row
+constexpr int IMG1 = 0, IMG2 = IMG1 + kHid * kIn, IMG3 = IMG2 + kHid * kHid;
+constexpr int NIMG = IMG3 + kHid * kHid;                   // W1, W2, W3 as [out][in] images
+// instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B bf16 (bits
+// 7-9 and 10-12 = 1), both K-major, N = 128 (bits 17-22 = N / 8), M = 128 (bits 24-28 = M / 16)
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kHid >> 3) << 17) |
+                                ((uint32_t)(kTM >> 4) << 24);
+constexpr uint32_t kTmemCols = 128;                        // one 128 x 128 FP32 accumulator
+constexpr long long kMmaWaitCap = 4000000000LL;            // ~2 s of SM clocks
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+// shared-memory matrix descriptor: start, leading and stride byte offsets (16-byte units),
+// descriptor version 1 (bits 46-47), base offset 0, no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((smem_addr(p) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(kIdescBf16), "r"(accumulate) : "memory");
+}
+// arrive on the barrier once every tcgen05 operation this thread issued so far has completed
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ bool bar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!bar_try_wait(bar, parity))
+        if (clock64() - t0 > kMmaWaitCap) return false;
+    return true;
+}
+// 32 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes (one lane per
+// thread); the wait sits in the same statement, so no use of r can precede it
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32]) {
+    uint32_t u[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];\n tcgen05.wait::ld.sync.aligned;"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
+          "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
+          "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+        : "r"(taddr) : "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) r[j] = __uint_as_float(u[j]);
+}
+// h = hi + mid + lo exactly: hi is h with the low 16 bits of its FP32 pattern cleared (a bf16
+// value), r = h - hi is exact and holds the remaining 16 significand bits, mid is r cleared
+// the same way, and lo = r - mid, also exact, has at most 8 significant bits, so it is a
+// bf16 value too.  The upper halves of the three patterns are the bf16 terms; eight values
+// of one row go out as one 16-byte line per term.
+__device__ __forceinline__ void split_store8(const float (&h)[8], __nv_bfloat16* hi, __nv_bfloat16* mid,
+                                             __nv_bfloat16* lo, int at) {
+    uint32_t t[3][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        t[0][j] = __float_as_uint(h[j]) & 0xFFFF0000u;
+        const float r = h[j] - __uint_as_float(t[0][j]);
+        t[1][j] = __float_as_uint(r) & 0xFFFF0000u;
+        t[2][j] = __float_as_uint(r - __uint_as_float(t[1][j]));
+    }
+    __nv_bfloat16* dst[3] = {hi, mid, lo};
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[j] = __byte_perm(t[u][2 * j], t[u][2 * j + 1], 0x7632);
+        *reinterpret_cast<uint4*>(dst[u] + at) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+struct TcSmem {
+    __nv_bfloat16 w[NIMG];                 // 80 KB
+    __nv_bfloat16 a[3][kTM * kHid];        // 96 KB: hi, mid, lo terms of the layer input
+    float w4[kOut][kHid];                  // bf16-rounded output layer
+    float bias[NBIAS];
+    float red[kColGroups][kTM][kOut];      // output-layer partial sums per column group
+    uint64_t bar;
+    uint32_t tmem;
+};
+
+// grid: ceil(B / 128); block: 512; dynamic smem: sizeof(TcSmem).  Warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 (the quarter a warp may access), i.e. samples s0 + 32 (w % 4) + lane, and
+// columns 32 (w / 4) .. + 31 of each accumulator row: bias + GELU there, and the next layer's
+// operand terms (or the output layer's partial sums) for those 32 columns.
+__global__ void __launch_bounds__(kTcThreads, 1)
+mlp_forward_tc_kernel(const float* __restrict__ x, int B, const float* __restrict__ w,
+                      const __nv_bfloat16* __restrict__ wt, const __nv_bfloat16* __restrict__ wimg,
+                      float* __restrict__ out, unsigned* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcSmem& sm = *reinterpret_cast<TcSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, cg = warp >> 2;
+    const int srow = 32 * quarter + lane;               // this thread's sample (TMEM lane)
+    const int s0 = blockIdx.x * kTM;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_addr(&sm.tmem)), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(wimg);
+        uint4* dst = reinterpret_cast<uint4*>(sm.w);
+#pragma unroll
+        for (int k = tid; k < NIMG / 8; k += kTcThreads) dst[k] = __ldg(src + k);
+    }
+    for (int k = tid; k < kOut * kHid; k += kTcThreads) {
+        const int o = k / kHid, i = k - o * kHid;
+        sm.w4[o][i] = __bfloat162float(wt[T4 + i * kOut + o]);
+    }
+    for (int k = tid; k < kHid; k += kTcThreads) {
+        sm.bias[k] = w[OFF_B1 + k];
+        sm.bias[kHid + k] = w[OFF_B2 + k];
+        sm.bias[2 * kHid + k] = w[OFF_B3 + k];
+    }
+    if (tid < kOut) sm.bias[3 * kHid + tid] = w[OFF_B4 + tid];
+    {   // the layer-1 operand (K = 64): thread (sample tid % 128, features 16 (tid / 128) ..
+        // + 15); zero past the batch
+        const int sl = tid & (kTM - 1), f0 = 16 * (tid >> 7);
+        const bool valid = s0 + sl < B;
+        const float* xr = x + (size_t)(valid ? s0 + sl : 0) * kIn + f0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            float h[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) h[j] = valid ? __ldg(xr + 8 * c + j) : 0.f;
+            split_store8(h, sm.a[0], sm.a[1], sm.a[2], img_at(sl, f0 + 8 * c, kIn));
+        }
+    }
+    proxy_fence();                      // generic-proxy stores -> the tensor cores' reads
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+    float o[kOut] = {0.f, 0.f, 0.f, 0.f};
+    int failed = -1;                    // layer whose MMA batch did not complete in time
+#pragma unroll 1
+    for (int layer = 0; layer < 3; ++layer) {
+        const int K = layer == 0 ? kIn : kHid;
+        if (tid == 0) {
+            const __nv_bfloat16* wl = sm.w + (layer == 0 ? IMG1 : layer == 1 ? IMG2 : IMG3);
+            const uint32_t sbo = (uint32_t)K * 16;
+#pragma unroll 1
+            for (int kk = 0; kk < K / 16; ++kk) {
+                const uint64_t bd = smem_desc(wl + kk * 128, 128, sbo);
+#pragma unroll
+                for (int u = 0; u < 3; ++u)
+                    mma_bf16(tmem, smem_desc(sm.a[u] + kk * 128, 128, sbo), bd, (kk | u) != 0);
+            }
+            mma_commit(&sm.bar);
+        }
+        const bool done = bar_wait_bounded(&sm.bar, (uint32_t)(layer & 1));
+        tc_fence_after();
+        if (__syncthreads_or(done ? 0 : 1)) {
+            failed = layer;
+            break;
+        }
+        const float* bl = sm.bias + layer * kHid;
+        {
+            const int col0 = 32 * cg;
+            float r[32];
+            tmem_ld32(lane_base + col0, r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) r[j] = gelu(r[j] + bl[col0 + j]);
+            if (layer < 2) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float h8[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) h8[j] = r[8 * c + j];
+                    split_store8(h8, sm.a[0], sm.a[1], sm.a[2], img_at(srow, col0 + 8 * c, kHid));
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+#pragma unroll
+                    for (int q = 0; q < kOut; ++q) o[q] = fmaf(r[j], sm.w4[q][col0 + j], o[q]);
+            }
+        }
+        proxy_fence();
+        tc_fence_before();
+        __syncthreads();                // every accumulator row read, next operand written
+        tc_fence_after();
+    }
+    if (failed < 0) {
+#pragma unroll
+        for (int q = 0; q < kOut; ++q) sm.red[cg][srow][q] = o[q];
+        __syncthreads();
+        if (tid < kTM && s0 + tid < B) {
+#pragma unroll
+            for (int q = 0; q < kOut; ++q) {
+                float acc = sm.bias[3 * kHid + q];
+#pragma unroll
+                for (int g = 0; g < kColGroups; ++g) acc += sm.red[g][tid][q];
+                out[(size_t)(s0 + tid) * kOut + q] = acc;
+            }
+        }
+    } else {
+        // an MMA batch that has not completed within the bound: report it, give the tensor
+        // cores a second bounded wait before the accumulator is released
+        if (tid == 0) atomicOr(status, 2u);
+        (void)bar_wait_bounded(&sm.bar, (uint32_t)(failed & 1));
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    __syncwarp();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                     : "memory");
 }
 
 struct Smem {
@@ -136,13 +385,11 @@ __device__ __forceinline__ void weight_grad(const float (*d)[OUT], const float (
 }
 
 // grid: ceil(B / kSB); block: kThreads; dynamic smem: sizeof(Smem)
-template <bool TRAIN>
 __global__ void __launch_bounds__(kThreads)
 mlp_chunk_kernel(const float* __restrict__ x, const float* __restrict__ tgt, int B,
                  const float* __restrict__ w, const __nv_bfloat16* __restrict__ wt,
-                 float* __restrict__ out, float* __restrict__ partials,
-                 float* __restrict__ loss_part) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+                 float* __restrict__ partials, float* __restrict__ loss_part) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int tid = threadIdx.x;
     const int s0 = blockIdx.x * kSB;
@@ -174,8 +421,7 @@ mlp_chunk_kernel(const float* __restrict__ x, const float* __restrict__ tgt, int
         float acc = sm.bias[3 * kHid + o];
         for (int k = 0; k < kHid; ++k) acc = fmaf(sm.h3[s][k], __bfloat162float(sm.wt[T4 + k * kOut + o]), acc);
         sm.o[s][o] = acc;
-        if (!TRAIN && s < ns) out[(size_t)(s0 + s) * kOut + o] = acc;
-        if (TRAIN) {
+        {
             // loss term and dL/do for this (sample, output); mean over the batch
             float l = 0.f, d = 0.f;
             if (s < ns) {
@@ -195,7 +441,7 @@ mlp_chunk_kernel(const float* __restrict__ x, const float* __restrict__ tgt, int
             sm.lsum[tid] = l;
         }
     }
-    if constexpr (TRAIN) {
+    {
         __syncthreads();
         float* part = partials + (size_t)blockIdx.x * NPARAM;
         if (tid == 0) {
@@ -259,17 +505,33 @@ __device__ __forceinline__ int wt_index(int p) {
     return -1;
 }
 
-__global__ void bf16_copy_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wt) {
+// index of master parameter p in the tensor-core operand images (W1..W3), or -1
+__device__ __forceinline__ int img_index(int p) {
+    if (p < OFF_B1) { const int o = p / kIn, i = p - o * kIn; return IMG1 + img_at(o, i, kIn); }
+    if (p < OFF_W2) return -1;
+    if (p < OFF_B2) { const int q = p - OFF_W2, o = q / kHid, i = q - o * kHid; return IMG2 + img_at(o, i, kHid); }
+    if (p < OFF_W3) return -1;
+    if (p < OFF_B3) { const int q = p - OFF_W3, o = q / kHid, i = q - o * kHid; return IMG3 + img_at(o, i, kHid); }
+    return -1;
+}
+
+__device__ __forceinline__ void put_bf16(int p, float v, __nv_bfloat16* wt, __nv_bfloat16* wimg) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    const int k = wt_index(p);
+    if (k >= 0) wt[k] = b;
+    const int g = img_index(p);
+    if (g >= 0) wimg[g] = b;
+}
+
+__global__ void bf16_copy_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wt,
+                                 __nv_bfloat16* __restrict__ wimg) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < NPARAM) {
-        const int k = wt_index(p);
-        if (k >= 0) wt[k] = __float2bfloat16_rn(w[p]);
-    }
+    if (p < NPARAM) put_bf16(p, w[p], wt, wimg);
 }
 
 __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
-                            const float* __restrict__ g, __nv_bfloat16* __restrict__ wt, float lr,
-                            float c1, float c2) {
+                            const float* __restrict__ g, __nv_bfloat16* __restrict__ wt,
+                            __nv_bfloat16* __restrict__ wimg, float lr, float c1, float c2) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= NPARAM) return;
     const float gp = g[p];
@@ -279,8 +541,7 @@ __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float*
     v[p] = vp;
     const float wn = w[p] - lr * (mp * c1) / (sqrtf(vp * c2) + 1e-8f);
     w[p] = wn;
-    const int k = wt_index(p);
-    if (k >= 0) wt[k] = __float2bfloat16_rn(wn);
+    put_bf16(p, wn, wt, wimg);
 }
 
 }  // namespace
@@ -299,6 +560,8 @@ struct ddm_mlp_s {
     float* partials;
     float* loss_part;
     __nv_bfloat16* wt;
+    __nv_bfloat16* wimg;    // W1..W3 as tensor-core operand images
+    unsigned* status;       // bit 1: a bounded wait gave up
 };
 
 namespace ddm {
@@ -306,12 +569,11 @@ namespace ddm {
 int mlp_max_batch(const ddm_mlp_s* m) { return m->max_batch; }
 
 ddm_status mlp_forward_raw(const ddm_mlp_s* m, const float* x, int B, float* o, cudaStream_t s) {
-    const int chunks = (B + kSB - 1) / kSB;
-    auto k = mlp_chunk_kernel<false>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) !=
+    auto k = mlp_forward_tc_kernel;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem)) !=
         cudaSuccess)
         return DDM_ERR_CUDA;
-    k<<<chunks, kThreads, sizeof(Smem), s>>>(x, nullptr, B, m->w, m->wt, o, nullptr, nullptr);
+    k<<<(B + kTM - 1) / kTM, kTcThreads, sizeof(TcSmem), s>>>(x, B, m->w, m->wt, m->wimg, o, m->status);
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 
@@ -330,17 +592,19 @@ void free_mlp(ddm_mlp_s* m) {
     cudaFree(m->partials);
     cudaFree(m->loss_part);
     cudaFree(m->wt);
+    cudaFree(m->wimg);
+    cudaFree(m->status);
     delete m;
 }
 
 ddm_status run_grad(ddm_mlp_s* m, const float* x, const float* t, int B, float* grad, float* loss,
                     cudaStream_t s) {
     const int chunks = (B + kSB - 1) / kSB;
-    auto k = mlp_chunk_kernel<true>;
+    auto k = mlp_chunk_kernel;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) !=
         cudaSuccess)
         return DDM_ERR_CUDA;
-    k<<<chunks, kThreads, sizeof(Smem), s>>>(x, t, B, m->w, m->wt, nullptr, m->partials, m->loss_part);
+    k<<<chunks, kThreads, sizeof(Smem), s>>>(x, t, B, m->w, m->wt, m->partials, m->loss_part);
     if (cudaGetLastError() != cudaSuccess) return DDM_ERR_CUDA;
     mlp_reduce_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(m->partials, chunks, grad, m->loss_part, loss);
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
@@ -363,7 +627,9 @@ ddm_status ddm_mlp_create(ddm_mlp* out, int max_batch) {
               cudaMalloc(&m->grad, sizeof(float) * NPARAM) == cudaSuccess &&
               cudaMalloc(&m->partials, sizeof(float) * NPARAM * (size_t)chunks) == cudaSuccess &&
               cudaMalloc(&m->loss_part, sizeof(float) * chunks) == cudaSuccess &&
-              cudaMalloc(&m->wt, sizeof(__nv_bfloat16) * NWT) == cudaSuccess;
+              cudaMalloc(&m->wt, sizeof(__nv_bfloat16) * NWT) == cudaSuccess &&
+              cudaMalloc(&m->wimg, sizeof(__nv_bfloat16) * NIMG) == cudaSuccess &&
+              cudaMalloc(&m->status, sizeof(unsigned)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_mlp(m);
@@ -373,6 +639,8 @@ ddm_status ddm_mlp_create(ddm_mlp* out, int max_batch) {
     cudaMemset(m->m, 0, sizeof(float) * NPARAM);
     cudaMemset(m->v, 0, sizeof(float) * NPARAM);
     cudaMemset(m->wt, 0, sizeof(__nv_bfloat16) * NWT);
+    cudaMemset(m->wimg, 0, sizeof(__nv_bfloat16) * NIMG);
+    cudaMemset(m->status, 0, sizeof(unsigned));
     *out = m;
     return DDM_OK;
 }
@@ -389,7 +657,7 @@ ddm_status ddm_mlp_set_weights(ddm_mlp m, const float* host_w) {
         cudaMemset(m->v, 0, sizeof(float) * NPARAM) != cudaSuccess)
         return DDM_ERR_CUDA;
     m->step = 0;
-    bf16_copy_kernel<<<(NPARAM + 255) / 256, 256>>>(m->w, m->wt);
+    bf16_copy_kernel<<<(NPARAM + 255) / 256, 256>>>(m->w, m->wt, m->wimg);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return DDM_ERR_CUDA;
     return DDM_OK;
 }
@@ -420,8 +688,20 @@ ddm_status ddm_mlp_set_state(ddm_mlp m, const float* host_state) {
         cudaMemcpy(m->v, host_state + 2 * NPARAM, sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess)
         return DDM_ERR_CUDA;
     m->step = (int)st;
-    bf16_copy_kernel<<<(NPARAM + 255) / 256, 256>>>(m->w, m->wt);
+    bf16_copy_kernel<<<(NPARAM + 255) / 256, 256>>>(m->w, m->wt, m->wimg);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return DDM_ERR_CUDA;
+    return DDM_OK;
+}
+
+ddm_status ddm_mlp_last_device_status(ddm_mlp m, ddm_status* out) {
+    if (!m || !out) return DDM_ERR_INVALID_ARG;
+    unsigned h = 0;
+    if (cudaMemcpy(&h, m->status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(m->status, 0, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return DDM_ERR_CUDA;
+    }
+    *out = (h & 2u) ? DDM_ERR_TIMEOUT : DDM_OK;
     return DDM_OK;
 }
 
@@ -444,8 +724,8 @@ ddm_status ddm_mlp_train_step(ddm_mlp m, const float* x, const float* t, int B, 
     if (st != DDM_OK) return st;
     m->step += 1;
     const double c1 = 1.0 / (1.0 - pow(0.9, m->step)), c2 = 1.0 / (1.0 - pow(0.999, m->step));
-    adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(m->w, m->m, m->v, m->grad, m->wt, lr, (float)c1,
-                                                   (float)c2);
+    adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(m->w, m->m, m->v, m->grad, m->wt, m->wimg, lr,
+                                                   (float)c1, (float)c2);
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 

@@ -107,6 +107,76 @@ def test_mlp_forward_matches_oracle():
     np.testing.assert_array_equal(mlp.get_weights(), w)
 
 
+@pytest.mark.parametrize("Bn", [1, 127, 128, 129, 300, 4096])
+def test_mlp_forward_tensor_cores_ragged_batches(Bn):
+    """The forward runs 128 samples per CTA on the tensor cores: batches below, at and just
+    past one CTA's tile, and the training batch, against the oracle (FP32 activations)."""
+    import torch
+    w = synth.mlp_init(8)
+    rng = np.random.Generator(np.random.PCG64(Bn))
+    x = rng.uniform(0, 1.2, (Bn, 64)).astype(np.float32)
+    mlp = ddm.MLP(4096)
+    mlp.set_weights(w)
+    o = torch.full((Bn * 4,), float("nan"), device="cuda")
+    mlp.forward(_cuda(x.reshape(-1)), Bn, o)
+    assert mlp.last_device_status() == B.DDM_OK
+    ref, _ = F.mlp_forward(w.astype(np.float64), x.astype(np.float64), bf16=True)
+    got = o.cpu().numpy().reshape(Bn, 4)
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_mlp_forward_unaligned_pointers_and_trained_weights():
+    """Inputs and outputs one float past an aligned allocation; weights changed by Adam steps
+    (the tensor-core operand images are rebuilt with every step)."""
+    import torch
+    w = synth.mlp_init(9)
+    rng = np.random.Generator(np.random.PCG64(9))
+    Bn = 200
+    x = rng.uniform(0, 1.2, (Bn, 64)).astype(np.float32)
+    t = rng.uniform(0, 1, (Bn, 4)).astype(np.float32)
+    mlp = ddm.MLP(Bn)
+    mlp.set_weights(w)
+    xd, td = _cuda(x.reshape(-1)), _cuda(t.reshape(-1))
+    for _ in range(3):
+        mlp.train_step(xd, td, Bn, 1e-2)
+    wk = mlp.get_weights().astype(np.float64)
+    assert np.max(np.abs(wk - w)) > 1e-3
+    xb = torch.empty(Bn * 64 + 1, device="cuda")
+    xb[1:] = xd
+    ob = torch.full((Bn * 4 + 1,), float("nan"), device="cuda")
+    mlp.forward(xb[1:], Bn, ob[1:])
+    assert mlp.last_device_status() == B.DDM_OK
+    ref, _ = F.mlp_forward(wk, x.astype(np.float64), bf16=True)
+    got = ob[1:].cpu().numpy().reshape(Bn, 4)
+    assert np.isnan(ob[0].item())
+    assert np.max(np.abs(got - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_mlp_forward_agrees_with_training_forward():
+    """The loss that the training kernel (CUDA cores) computes equals the loss of the
+    tensor-core forward's outputs."""
+    import torch
+    w = synth.mlp_init(10)
+    rng = np.random.Generator(np.random.PCG64(10))
+    Bn = 512
+    x = rng.uniform(0, 1.2, (Bn, 64)).astype(np.float32)
+    t = np.stack([rng.normal(0, 1, Bn), rng.uniform(0, 6, Bn), rng.uniform(0.5, 1.1, Bn),
+                  rng.uniform(0, 0.5, Bn)], axis=1).astype(np.float32)
+    mlp = ddm.MLP(Bn)
+    mlp.set_weights(w)
+    g = torch.empty(B.DDM_MLP_PARAMS, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    mlp.grad(_cuda(x.reshape(-1)), _cuda(t.reshape(-1)), Bn, g, loss)
+    o = torch.empty(Bn * 4, device="cuda")
+    mlp.forward(_cuda(x.reshape(-1)), Bn, o)
+    oo = o.cpu().numpy().reshape(Bn, 4).astype(np.float64)
+    sig = 1.0 / (1.0 + np.exp(-oo[:, 2]))
+    yhat = np.stack([oo[:, 0], oo[:, 1], 0.3 + 0.9 * sig, oo[:, 3]], axis=1)
+    l_tc = float(np.sum((yhat - t) ** 2) / Bn)
+    assert float(loss.item()) == pytest.approx(l_tc, rel=1e-5)
+
+
 def test_mlp_gradient_matches_oracle():
     import torch
     w = synth.mlp_init(6)
