@@ -25,7 +25,7 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 constexpr int kRadialChunk = 64;   // wave vectors per radial partial sum
 
-constexpr int kMaxSide = 2048;         // powers of two; other even sides up to 1022
+constexpr int kMaxSide = 2048;         // powers of two; mixed-radix sides up to 1280; others up to 1022
 constexpr int kMaxFrames = 16384;
 // stored wave vectors from which the time kernels read a blocked copy (measured: at L = 16384
 // 512x512 gains 1.11x with the copy included; at L = 4096 512x512 (131584) loses 1.3x, while
@@ -225,7 +225,13 @@ ddm_status validate(const ddm_plan_desc* d) {
     if (!d) return DDM_ERR_INVALID_ARG;
     if (d->H < 2 || d->W < 2 || d->H % 2 != 0 || d->W % 2 != 0) return DDM_ERR_INVALID_ARG;
     if (d->H > kMaxSide || d->W > kMaxSide) return DDM_ERR_UNSUPPORTED;
-    if ((!is_pow2(d->H) && d->H > 1024) || (!is_pow2(d->W) && d->W > 1024)) return DDM_ERR_UNSUPPORTED;
+    {   // above 1024 pixels: powers of two, or a side the mixed-radix kernels are built for
+        int P = 0, T = 0;
+        mixed_shape(d->H, &P, &T);
+        if (!is_pow2(d->H) && d->H > 1024 && P == 0) return DDM_ERR_UNSUPPORTED;
+        mixed_shape(d->W, &P, &T);
+        if (!is_pow2(d->W) && d->W > 1024 && P == 0) return DDM_ERR_UNSUPPORTED;
+    }
     if (d->N < 1) return DDM_ERR_INVALID_ARG;
     if (d->N > kMaxFrames) return DDM_ERR_UNSUPPORTED;
     if (d->dtype != DDM_IN_U16 && d->dtype != DDM_IN_F32) return DDM_ERR_INVALID_ARG;
@@ -355,7 +361,7 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
     // Bluestein tables: rows when W is not a power of two; columns when either side is not
     // (the power-of-two column kernel takes whole blocks of 16 stored columns).  Sides of
     // 2048: the same kernels' 2048-point transform alone (no chirp).
-    // mixed-radix kernels first for the sides they are built for (480, 600, 640, 720, 800, 960)
+    // mixed-radix kernels first for the sides they are built for (mixed_shape)
     int mP = 0, mT = 0;
     mixed_shape(desc->W, &mP, &mT);
     const bool mix_w = mP > 0;

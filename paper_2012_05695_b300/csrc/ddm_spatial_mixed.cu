@@ -1,5 +1,5 @@
 // Step one (Sec. 2) for frame sides n = P T with P, T of the form 2^a 3^b 5^c (common camera
-// sides: 384, 480, 540, 600, 640, 720, 768, 800, 900, 960, 1000): a two-pass mixed-radix
+// sides: 384, 480, 540, 600, 640, 720, 768, 800, 900, 960, 1000, 1080, 1200, 1280): a two-pass mixed-radix
 // transform instead of Bluestein's, about 6x less arithmetic at n = 800.  T threads per transform, P points per
 // thread in the cyclic layout (thread i holds x[i + T u], u < P):
 //   pass 1: the P-point DFT over u (dft_mix), the twiddle w_n^{i k1} (host table, double
@@ -275,6 +275,9 @@ cudaError_t rows_dispatch(const ddm_plan_s* p, const void* frames, float2* spec,
         case 900: return rows_t<30, 30, In>(p, frames, spec, s);
         case 960: return rows_t<30, 32, In>(p, frames, spec, s);
         case 1000: return rows_t<25, 40, In>(p, frames, spec, s);
+        case 1080: return rows_t<27, 40, In>(p, frames, spec, s);
+        case 1200: return rows_t<30, 40, In>(p, frames, spec, s);
+        case 1280: return rows_t<32, 40, In>(p, frames, spec, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -295,6 +298,9 @@ void mixed_shape(int n, int* P, int* T) {
         case 900: *P = 30; *T = 30; return;
         case 960: *P = 30; *T = 32; return;
         case 1000: *P = 25; *T = 40; return;
+        case 1080: *P = 27; *T = 40; return;
+        case 1200: *P = 30; *T = 40; return;
+        case 1280: *P = 32; *T = 40; return;
         default: *P = 0; *T = 0; return;
     }
 }
@@ -317,6 +323,9 @@ cudaError_t launch_cols_mixed(const ddm_plan_s* p, float2* spec, cudaStream_t s,
         case 900: return cols_t<30, 30>(p, spec, s, out);
         case 960: return cols_t<30, 32>(p, spec, s, out);
         case 1000: return cols_t<25, 40>(p, spec, s, out);
+        case 1080: return cols_t<27, 40>(p, spec, s, out);
+        case 1200: return cols_t<30, 40>(p, spec, s, out);
+        case 1280: return cols_t<32, 40>(p, spec, s, out);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -53,6 +53,8 @@ def test_desc_init_defaults():
     ("H", 21, B.DDM_ERR_INVALID_ARG),             # odd sides: rows are transformed in pairs
     ("W", 7, B.DDM_ERR_INVALID_ARG),
     ("W", 1030, B.DDM_ERR_UNSUPPORTED),           # above 1024
+    ("H", 1100, B.DDM_ERR_UNSUPPORTED),           # above 1024, not a mixed-radix side
+    ("W", 1536, B.DDM_ERR_UNSUPPORTED),
     ("W", 0, B.DDM_ERR_INVALID_ARG),
     ("H", 4096, B.DDM_ERR_UNSUPPORTED),
     ("N", 0, B.DDM_ERR_INVALID_ARG),
@@ -114,6 +116,16 @@ def test_null_arguments():
 def test_valid_plan_without_device_is_a_cuda_error():
     d = _desc(8, 8, 4)
     h = ctypes.c_void_p()
+    assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == B.DDM_ERR_CUDA
+    assert not h.value
+
+
+@pytest.mark.parametrize("H,W", [(1080, 1280), (1200, 1024), (2048, 1280), (1280, 1022)])
+def test_mixed_radix_sides_above_1024_pass_validation(H, W):
+    """1080 = 27 x 40, 1200 = 30 x 40 and 1280 = 32 x 40 are built; without a device the plan
+    gets as far as the first CUDA call."""
+    d = _desc(H, W, 4)
+    h = ctypes.c_void_p(123)
     assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == B.DDM_ERR_CUDA
     assert not h.value
 
