@@ -79,7 +79,8 @@ typedef enum ddm_spatial_path {
 typedef struct ddm_plan_desc {
     int H, W;          /* frame height and width in pixels, even: powers of two 2..2048
                           by radix-2 register FFTs; the sides 384, 480, 540, 600, 640,
-                          720, 768, 800, 900, 960, 1000, 1080, 1200, 1280 by two-pass
+                          720, 768, 800, 900, 960, 1000, 1080, 1200, 1280, 1440, 1536,
+                          1600, 1920, 2000 by two-pass
                           mixed-radix (2, 3, 5) transforms; other even sides (6 .. 1022)
                           by Bluestein's chirp-z transform (a cyclic convolution of length
                           max(32, 2^ceil(log2(2n - 1))) <= 2048); odd sides

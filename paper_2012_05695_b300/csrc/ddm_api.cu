@@ -25,7 +25,7 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 constexpr int kRadialChunk = 64;   // wave vectors per radial partial sum
 
-constexpr int kMaxSide = 2048;         // powers of two; mixed-radix sides up to 1280; others up to 1022
+constexpr int kMaxSide = 2048;         // powers of two; mixed-radix sides up to 2000; others up to 1022
 constexpr int kMaxFrames = 16384;
 // stored wave vectors from which the time kernels read a blocked copy (measured: at L = 16384
 // 512x512 gains 1.11x with the copy included; at L = 4096 512x512 (131584) loses 1.3x, while

@@ -1,5 +1,6 @@
 // Step one (Sec. 2) for frame sides n = P T with P, T of the form 2^a 3^b 5^c (common camera
-// sides: 384, 480, 540, 600, 640, 720, 768, 800, 900, 960, 1000, 1080, 1200, 1280): a two-pass mixed-radix
+// sides: 384, 480, 540, 600, 640, 720, 768, 800, 900, 960, 1000, 1080, 1200, 1280, 1440, 1536,
+// 1600, 1920, 2000): a two-pass mixed-radix
 // transform instead of Bluestein's, about 6x less arithmetic at n = 800.  T threads per transform, P points per
 // thread in the cyclic layout (thread i holds x[i + T u], u < P):
 //   pass 1: the P-point DFT over u (dft_mix), the twiddle w_n^{i k1} (host table, double
@@ -41,7 +42,7 @@ struct MShape {
     static constexpr size_t OUT = STG;
     static constexpr size_t XE = XCH > STG ? (XCH > OUT ? XCH : OUT) : (STG > OUT ? STG : OUT);
     static constexpr size_t BYTES = sizeof(float2) * (XE + (size_t)N);
-    static_assert(P <= 32 && T <= 40 && QT >= 1, "mixed-radix shapes");
+    static_assert(P <= 40 && T <= 50 && QT >= 1, "mixed-radix shapes");
     static_assert(P <= T, "pass 2 gives each k1 < P its own thread: P <= T");
 };
 
@@ -278,6 +279,11 @@ cudaError_t rows_dispatch(const ddm_plan_s* p, const void* frames, float2* spec,
         case 1080: return rows_t<27, 40, In>(p, frames, spec, s);
         case 1200: return rows_t<30, 40, In>(p, frames, spec, s);
         case 1280: return rows_t<32, 40, In>(p, frames, spec, s);
+        case 1440: return rows_t<30, 48, In>(p, frames, spec, s);
+        case 1536: return rows_t<32, 48, In>(p, frames, spec, s);
+        case 1600: return rows_t<32, 50, In>(p, frames, spec, s);
+        case 1920: return rows_t<40, 48, In>(p, frames, spec, s);
+        case 2000: return rows_t<40, 50, In>(p, frames, spec, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -301,6 +307,11 @@ void mixed_shape(int n, int* P, int* T) {
         case 1080: *P = 27; *T = 40; return;
         case 1200: *P = 30; *T = 40; return;
         case 1280: *P = 32; *T = 40; return;
+        case 1440: *P = 30; *T = 48; return;
+        case 1536: *P = 32; *T = 48; return;
+        case 1600: *P = 32; *T = 50; return;
+        case 1920: *P = 40; *T = 48; return;
+        case 2000: *P = 40; *T = 50; return;
         default: *P = 0; *T = 0; return;
     }
 }
@@ -326,6 +337,11 @@ cudaError_t launch_cols_mixed(const ddm_plan_s* p, float2* spec, cudaStream_t s,
         case 1080: return cols_t<27, 40>(p, spec, s, out);
         case 1200: return cols_t<30, 40>(p, spec, s, out);
         case 1280: return cols_t<32, 40>(p, spec, s, out);
+        case 1440: return cols_t<30, 48>(p, spec, s, out);
+        case 1536: return cols_t<32, 48>(p, spec, s, out);
+        case 1600: return cols_t<32, 50>(p, spec, s, out);
+        case 1920: return cols_t<40, 48>(p, spec, s, out);
+        case 2000: return cols_t<40, 50>(p, spec, s, out);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -54,7 +54,7 @@ def test_desc_init_defaults():
     ("W", 7, B.DDM_ERR_INVALID_ARG),
     ("W", 1030, B.DDM_ERR_UNSUPPORTED),           # above 1024
     ("H", 1100, B.DDM_ERR_UNSUPPORTED),           # above 1024, not a mixed-radix side
-    ("W", 1536, B.DDM_ERR_UNSUPPORTED),
+    ("W", 1700, B.DDM_ERR_UNSUPPORTED),
     ("W", 0, B.DDM_ERR_INVALID_ARG),
     ("H", 4096, B.DDM_ERR_UNSUPPORTED),
     ("N", 0, B.DDM_ERR_INVALID_ARG),
@@ -120,10 +120,11 @@ def test_valid_plan_without_device_is_a_cuda_error():
     assert not h.value
 
 
-@pytest.mark.parametrize("H,W", [(1080, 1280), (1200, 1024), (2048, 1280), (1280, 1022)])
+@pytest.mark.parametrize("H,W", [(1080, 1280), (1200, 1024), (2048, 1280), (1280, 1022), (1080, 1920),
+                                 (1536, 1600), (2000, 1440)])
 def test_mixed_radix_sides_above_1024_pass_validation(H, W):
-    """1080 = 27 x 40, 1200 = 30 x 40 and 1280 = 32 x 40 are built; without a device the plan
-    gets as far as the first CUDA call."""
+    """The mixed-radix sides above 1024 (1080 = 27 x 40 ... 2000 = 40 x 50) are built; without
+    a device the plan gets as far as the first CUDA call."""
     d = _desc(H, W, 4)
     h = ctypes.c_void_p(123)
     assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == B.DDM_ERR_CUDA

@@ -51,6 +51,11 @@ def _frames(N, H, W, dtype, seed):
     (1200, 1024, 2, "f32"),    # (30 40) columns beside power-of-two rows
     (2048, 1280, 2, "u16"),    # 2048-point columns beside mixed rows
     (1280, 1022, 2, "f32"),    # Bluestein rows (M = 2048) beside mixed columns
+    (1080, 1920, 2, "u16"),    # full HD: (27 40 columns, 40 48 rows)
+    (1920, 1080, 2, "f32"),    # and turned: (40 48 columns, 27 40 rows)
+    (1536, 1536, 2, "u16"),    # (32 48)
+    (1600, 2000, 2, "f32"),    # (32 50 columns, 40 50 rows)
+    (2048, 1440, 2, "u16"),    # 2048-point columns beside (30 48) rows
 ])
 def test_spatial_fft_non_power_of_two_matches_oracle_dft(H, W, N, dtype):
     import torch
@@ -122,7 +127,7 @@ def test_mixed_rows_unaligned_frames_match_aligned(H, W, dtype, sub):
     (8, 12, 3, "f32"), (6, 10, 1, "u16"), (12, 8, 50, "u16"),
     (18, 22, 40, "f32"), (48, 80, 64, "u16"), (100, 64, 33, "u16"), (64, 100, 20, "f32"),
     (250, 250, 100, "f32"), (600, 800, 16, "u16"), (2048, 64, 40, "u16"), (16, 2048, 33, "f32"),
-    (480, 640, 12, "f32"), (720, 96, 30, "u16"), (1080, 1280, 6, "u16"),
+    (480, 640, 12, "f32"), (720, 96, 30, "u16"), (1080, 1280, 6, "u16"), (1080, 1920, 4, "u16"),
 ])
 def test_structure_function_non_power_of_two_matches_oracle(H, W, N, dtype):
     frames = _frames(N, H, W, dtype, seed=11 * N + H)
