@@ -178,10 +178,13 @@ ddm_status ddm_plan_stats(ddm_plan p, float* step_one_ms, float* step_two_ms);
 
 /* Test hook for the bounded device waits (no plan needed, current device, synchronous):
  * launches one CTA that arms a tile barrier for bytes no copy will deliver and waits on it
- * with the same bounded routine the time kernels use, giving up after cap_cycles SM clock
- * cycles (clamped to 1e3 .. 4e9).  Returns DDM_ERR_TIMEOUT when the bound fired and was
- * reported through a status word (the expected outcome), DDM_OK if the wait had completed
- * (never, unless the bound is broken), DDM_ERR_CUDA on a launch or copy failure. */
+ * with the same bounded routine the time kernels use, and one CTA that holds tensor memory
+ * and waits on an MMA barrier no commit will complete with the routine and give-up path of
+ * the MLP's tensor-core forward (it then releases the tensor memory); each gives up after
+ * cap_cycles SM clock cycles (clamped to 1e3 .. 4e9).  Returns DDM_ERR_TIMEOUT when both
+ * bounds fired and were reported through status words (the expected outcome), DDM_OK if a
+ * wait had completed (never, unless a bound is broken), DDM_ERR_CUDA on a launch or copy
+ * failure. */
 ddm_status ddm_selftest_bounded_wait(long long cap_cycles);
 
 /* ---- the hot path ---------------------------------------------------------------- */

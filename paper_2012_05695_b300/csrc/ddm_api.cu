@@ -570,21 +570,22 @@ ddm_status ddm_plan_stats(ddm_plan p, float* step_one_ms, float* step_two_ms) {
 ddm_status ddm_selftest_bounded_wait(long long cap_cycles) {
     if (cap_cycles < 1000) cap_cycles = 1000;
     if (cap_cycles > 4000000000LL) cap_cycles = 4000000000LL;
-    unsigned* word = nullptr;
-    if (cudaMalloc(&word, sizeof(unsigned)) != cudaSuccess) {
+    unsigned* word = nullptr;   // [0]: the tile-barrier wait, [1]: the MMA-barrier wait
+    if (cudaMalloc(&word, 2 * sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         return DDM_ERR_CUDA;
     }
-    unsigned h = 0;
-    bool ok = cudaMemset(word, 0, sizeof(unsigned)) == cudaSuccess &&
+    unsigned h[2] = {0, 0};
+    bool ok = cudaMemset(word, 0, 2 * sizeof(unsigned)) == cudaSuccess &&
               launch_wait_selftest(word, cap_cycles, nullptr) == cudaSuccess &&
-              cudaMemcpy(&h, word, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess;
+              launch_mlp_wait_selftest(word + 1, cap_cycles, nullptr) == cudaSuccess &&
+              cudaMemcpy(h, word, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess;
     cudaFree(word);
     if (!ok) {
         cudaGetLastError();
         return DDM_ERR_CUDA;
     }
-    return (h & 2u) ? DDM_ERR_TIMEOUT : DDM_OK;
+    return ((h[0] & 2u) && (h[1] & 2u)) ? DDM_ERR_TIMEOUT : DDM_OK;
 }
 
 ddm_status ddm_plan_last_device_status(ddm_plan p, ddm_status* out) {

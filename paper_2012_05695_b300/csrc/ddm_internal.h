@@ -114,6 +114,7 @@ void mixed_shape(int n, int* P, int* T);
 cudaError_t launch_rows_mixed(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
 cudaError_t launch_cols_mixed(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out);
 cudaError_t launch_wait_selftest(unsigned* status, long long cap_cycles, cudaStream_t s);
+cudaError_t launch_mlp_wait_selftest(unsigned* status, long long cap_cycles, cudaStream_t s);
 cudaError_t launch_rows_bluestein(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
 cudaError_t launch_cols_bluestein(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out);
 ddm_status launch_radial(const ddm_plan_s* p, const float* D, float* Dr, int* counts, bool normalise,

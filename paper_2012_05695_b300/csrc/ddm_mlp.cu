@@ -101,11 +101,30 @@ __device__ __forceinline__ bool bar_try_wait(uint64_t* bar, uint32_t parity) {
         : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool bar_wait_bounded(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool bar_wait_bounded(uint64_t* bar, uint32_t parity, long long cap = kMmaWaitCap) {
     const long long t0 = clock64();
     while (!bar_try_wait(bar, parity))
-        if (clock64() - t0 > kMmaWaitCap) return false;
+        if (clock64() - t0 > cap) return false;
     return true;
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_addr(slot)), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t tmem) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                 : "memory");
+}
+// An MMA batch that has not completed within the bound (block-uniform call): report it in
+// the status word (bit 1), give the tensor cores one more bounded wait, then every thread
+// is done with tensor memory and the caller may release it.
+__device__ __forceinline__ void mma_give_up(unsigned* status, uint64_t* bar, uint32_t parity, long long cap) {
+    if (threadIdx.x == 0) atomicOr(status, 2u);
+    (void)bar_wait_bounded(bar, parity, cap);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 }
 // 32 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes (one lane per
 // thread); the wait sits in the same statement, so no use of r can precede it
@@ -172,11 +191,7 @@ mlp_forward_tc_kernel(const float* __restrict__ x, int B, const float* __restric
     const int quarter = warp & 3, cg = warp >> 2;
     const int srow = 32 * quarter + lane;               // this thread's sample (TMEM lane)
     const int s0 = blockIdx.x * kTM;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_addr(&sm.tmem)), "r"(kTmemCols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (warp == 0) tmem_alloc(&sm.tmem);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -280,18 +295,33 @@ mlp_forward_tc_kernel(const float* __restrict__ x, int B, const float* __restric
             }
         }
     } else {
-        // an MMA batch that has not completed within the bound: report it, give the tensor
-        // cores a second bounded wait before the accumulator is released
-        if (tid == 0) atomicOr(status, 2u);
-        (void)bar_wait_bounded(&sm.bar, (uint32_t)(failed & 1));
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
+        mma_give_up(status, &sm.bar, (uint32_t)(failed & 1), kMmaWaitCap);
     }
     __syncwarp();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
-                     : "memory");
+    if (warp == 0) tmem_free(tmem);
+}
+
+// Test hook for the bounded MMA wait and the give-up path above: one CTA takes tensor memory
+// and an MMA barrier as the forward does, waits (bound: cap cycles) on a phase that no commit
+// will complete (no MMA is issued), reports through the status word, waits once more and
+// releases the tensor memory.
+__global__ void __launch_bounds__(128) mlp_wait_selftest_kernel(unsigned* status, long long cap) {
+    __shared__ uint64_t bar;
+    __shared__ uint32_t slot;
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) tmem_alloc(&slot);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = slot;
+    const bool done = bar_wait_bounded(&bar, 0u, cap);
+    if (__syncthreads_or(done ? 0 : 1)) mma_give_up(status, &bar, 0u, cap);
+    __syncwarp();
+    if (warp == 0) tmem_free(tmem);
 }
 
 struct Smem {
@@ -567,6 +597,11 @@ struct ddm_mlp_s {
 namespace ddm {
 
 int mlp_max_batch(const ddm_mlp_s* m) { return m->max_batch; }
+
+cudaError_t launch_mlp_wait_selftest(unsigned* status, long long cap_cycles, cudaStream_t s) {
+    mlp_wait_selftest_kernel<<<1, 128, 0, s>>>(status, cap_cycles);
+    return cudaGetLastError();
+}
 
 ddm_status mlp_forward_raw(const ddm_mlp_s* m, const float* x, int B, float* o, cudaStream_t s) {
     auto k = mlp_forward_tc_kernel;

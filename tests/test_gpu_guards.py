@@ -103,12 +103,20 @@ def test_fit_outputs_stay_inside_their_buffers():
 
 @pytest.mark.parametrize("cap", [1000, 2_000_000])
 def test_bounded_wait_gives_up_with_timeout(cap):
-    """A barrier armed for bytes no copy delivers: the wait must give up after its bound
-    and report DDM_ERR_TIMEOUT through the status word; the context stays usable."""
+    """A tile barrier armed for bytes no copy delivers, and an MMA barrier no commit
+    completes (in a CTA holding tensor memory): both waits must give up after their bound
+    and report DDM_ERR_TIMEOUT through the status words, the tensor memory is released, and
+    the context stays usable (the tensor-core forward still runs afterwards)."""
     import torch
     assert ddm.selftest_bounded_wait(cap) == ddm._binding.DDM_ERR_TIMEOUT
     x = torch.ones(1024, device="cuda")
     assert float(x.sum().item()) == 1024.0
+    mlp = ddm.MLP(256)
+    mlp.set_weights(synth.mlp_init(1))
+    o = torch.full((256 * 4,), float("nan"), device="cuda")
+    mlp.forward(torch.rand(256 * 64, device="cuda"), 256, o)
+    assert mlp.last_device_status() == ddm._binding.DDM_OK
+    assert bool(torch.isfinite(o).all())
 
 
 def test_plan_stats_time_both_steps():
