@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(FusedShape<S, CL>::NT, FusedShape<S, CL>::NT <
 fused_r2c_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int N, int subtract_ref,
                  const float2* __restrict__ tw_g, int n_clusters, unsigned* status) {
     using C = FusedShape<S, CL>;
-    constexpr int T = C::T, P = C::P, NT = C::NT, PAIRS = C::PAIRS, CW = C::CW, RH = C::RH;
+    constexpr int T = C::T, P = C::P, NT = C::NT, CW = C::CW, RH = C::RH;
     constexpr int Wh = S / 2;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2* X = reinterpret_cast<float2*>(smem_raw);
@@ -730,26 +730,32 @@ row_bulk_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
     __syncthreads();                                   // staging read: region becomes the exchange
     const AddrSwizzled<W> addr{j * W};
     fft_cyclic<W, false>(v, i, X, addr, tw, SyncBlock{});
-#pragma unroll
-    for (int u = 0; u < P; ++u) X[addr(i + T * u)] = v[u];
-    __syncthreads();
-    if (active) {
+    static_assert(P >= 2 && 32 % T == 0, "row pairs: P >= 2 points per thread, T | 32");
+    // The split into the two real rows pairs X[k] with X[W - k].  Thread i holds X[i + T u];
+    // for k = i + T u, X[W - k] sits in thread (T - i) % T of the same transform (the same
+    // warp: T divides 32) at u' = P - 1 - u (i > 0) or (P - u) % P (i = 0), so it comes by a
+    // shuffle, with no shared-memory round trip and no block barrier.
+    {
         // kc > 0 (low-frequency restriction): rows of kx = 0..kc, no Nyquist packing
         const int rowlen = kc > 0 ? kc + 1 : W / 2;
+        const int lane = tid & 31;
+        const int src = lane - i + ((T - i) & (T - 1));
         float2* outa = spec + (size_t)t * frame_stride + (size_t)(2 * (pair0 + j)) * rowlen;
         float2* outb = outa + rowlen;
 #pragma unroll
         for (int u = 0; u < (P + 1) / 2; ++u) {
+            const float2 send = (i == 0) ? v[(P - u) & (P - 1)] : v[P - 1 - u];
+            float2 zr;
+            zr.x = __shfl_sync(0xffffffffu, send.x, src);
+            zr.y = __shfl_sync(0xffffffffu, send.y, src);
             const int k = i + T * u;
-            if (k >= rowlen) break;
-            const float2 z = X[addr(k)];
+            if (!active || k >= rowlen) continue;
+            const float2 z = v[u];
             if (k == 0) {
-                const float nyq_a = kc > 0 ? 0.f : X[addr(W / 2)].x;
-                const float nyq_b = kc > 0 ? 0.f : X[addr(W / 2)].y;
-                outa[0] = make_float2(z.x, nyq_a);
-                outb[0] = make_float2(z.y, nyq_b);
+                const float2 nyq = v[P / 2];                      // X[W / 2]: thread 0, u = P / 2
+                outa[0] = make_float2(z.x, kc > 0 ? 0.f : nyq.x);
+                outb[0] = make_float2(z.y, kc > 0 ? 0.f : nyq.y);
             } else {
-                const float2 zr = X[addr(W - k)];
                 outa[k] = make_float2(0.5f * (z.x + zr.x), 0.5f * (z.y - zr.y));
                 outb[k] = make_float2(0.5f * (z.y + zr.y), 0.5f * (zr.x - z.x));
             }
