@@ -9,8 +9,9 @@
 // Inference (ddm_mlp_forward, the fit's seeds) runs the three hidden layers on the
 // 5th-generation tensor cores: tcgen05.mma (kind::f16, bf16 operands, FP32 accumulators in
 // tensor memory), one CTA per 128 samples.  Each FP32 activation enters as three bf16 terms
-// whose sum is exactly the activation (8 + 8 + 8 significand bits), so that every product is
-// exact and the result is the FP32-activation network's to within FP32 accumulation order.
+// whose sum is exactly the activation (8 + 8 + 8 significand bits; for |h| >= 2^-103), so
+// that every product is exact and the result is the FP32-activation network's to within FP32
+// accumulation order.
 //
 // Training: one CTA handles a chunk of kSB samples with all bf16 weights resident in shared
 // memory (83 KB): forward, backward pass and the chunk's weight-gradient partials on CUDA
@@ -142,11 +143,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32]) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) r[j] = __uint_as_float(u[j]);
 }
-// h = hi + mid + lo exactly: hi is h with the low 16 bits of its FP32 pattern cleared (a bf16
+// h = hi + mid + lo: hi is h with the low 16 bits of its FP32 pattern cleared (a bf16
 // value), r = h - hi is exact and holds the remaining 16 significand bits, mid is r cleared
 // the same way, and lo = r - mid, also exact, has at most 8 significant bits, so it is a
-// bf16 value too.  The upper halves of the three patterns are the bf16 terms; eight values
-// of one row go out as one 16-byte line per term.
+// bf16 value too whenever it is a normal FP32 number (|h| >= 2^-103; below that the upper
+// half of its subnormal pattern drops less than 2^-133).  The upper halves of the three
+// patterns are the bf16 terms; eight values of one row go out as one 16-byte line per term.
 __device__ __forceinline__ void split_store8(const float (&h)[8], __nv_bfloat16* hi, __nv_bfloat16* mid,
                                              __nv_bfloat16* lo, int at) {
     uint32_t t[3][8];
