@@ -27,10 +27,10 @@ constexpr int mixed_row(int T, int QT) {
     return r;
 }
 
-template <int P_, int T_>
+template <int P_, int T_, int NT_ = 256>
 struct MShape {
     static constexpr int P = P_, T = T_, N = P * T;
-    static constexpr int NT = 256;
+    static constexpr int NT = NT_;
     static constexpr int QT = NT / T;                       // transforms per CTA
     static constexpr int ROW = mixed_row(T, QT);            // exchange row of one k1
     static constexpr size_t XCH = (size_t)P * ROW * QT;     // (k1 ROW + i) QT + ql
@@ -49,10 +49,10 @@ struct MShape {
 // QT interleaved transforms; thread (ql, i) with i < T.  live: the thread is one of the
 // T QT threads that carry a transform (the CTA may have a few spare threads).  Returns with
 // thread (ql, j), j < P, holding X[j + P k2] in w[k2].
-template <int P, int T>
+template <int P, int T, int NT = 256>
 __device__ __forceinline__ void fft_mixed(float2 (&v)[P], float2 (&w)[T], int i, int ql, bool live,
                                           float2* xs, const float2* tw) {
-    using C = MShape<P, T>;
+    using C = MShape<P, T, NT>;
     dft_mix<P, false>(v);
     if (live) {
 #pragma unroll
@@ -184,12 +184,13 @@ row_mixed_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H
 }
 
 // ------------------------------------------------------------- columns (H = P T)
-// grid: (ceil(Wh / QT), N); block: 256.  In place, QT stored columns of one frame.
-template <int P, int T>
-__global__ void __launch_bounds__(256)
+// grid: (ceil(Wh / QT), N); block: NTC (256, or 512 for the wide shapes: 12 columns of T = 40
+// threads, 96-byte row segments).  In place, QT stored columns of one frame.
+template <int P, int T, int NTC>
+__global__ void __launch_bounds__(NTC)
 col_mixed_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride, const float2* __restrict__ tw_g,
                  SpecOut out) {
-    using C = MShape<P, T>;
+    using C = MShape<P, T, NTC>;
     constexpr int H = C::N, QT = C::QT, NT = C::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2* xs = reinterpret_cast<float2*>(smem_raw);
@@ -205,7 +206,7 @@ col_mixed_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride, const f
     float2 v[P], w[T];
 #pragma unroll
     for (int u = 0; u < P; ++u) v[u] = valid ? base[(size_t)(i + T * u) * Wh + kx] : make_float2(0.f, 0.f);
-    fft_mixed<P, T>(v, w, i, ql, live, xs, tw);
+    fft_mixed<P, T, NTC>(v, w, i, ql, live, xs, tw);
     const bool holds = live && i < P;                       // holds X[i + P k2], k2 < T
     const int t = blockIdx.y;
     if (blockIdx.x != 0) {
@@ -250,10 +251,10 @@ cudaError_t rows_t(const ddm_plan_s* p, const void* frames, float2* spec, cudaSt
     return cudaGetLastError();
 }
 
-template <int P, int T>
+template <int P, int T, int NTC = 256>
 cudaError_t cols_t(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out) {
-    using C = MShape<P, T>;
-    auto k = col_mixed_kernel<P, T>;
+    using C = MShape<P, T, NTC>;
+    auto k = col_mixed_kernel<P, T, NTC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
     if (e != cudaSuccess) return e;
     dim3 grid((p->Wh + C::QT - 1) / C::QT, p->d.N);
@@ -333,14 +334,14 @@ cudaError_t launch_cols_mixed(const ddm_plan_s* p, float2* spec, cudaStream_t s,
         case 800: return cols_t<25, 32>(p, spec, s, out);
         case 900: return cols_t<30, 30>(p, spec, s, out);
         case 960: return cols_t<30, 32>(p, spec, s, out);
-        case 1000: return cols_t<25, 40>(p, spec, s, out);
-        case 1080: return cols_t<27, 40>(p, spec, s, out);
-        case 1200: return cols_t<30, 40>(p, spec, s, out);
-        case 1280: return cols_t<32, 40>(p, spec, s, out);
+        case 1000: return cols_t<25, 40, 512>(p, spec, s, out);
+        case 1080: return cols_t<27, 40, 512>(p, spec, s, out);
+        case 1200: return cols_t<30, 40, 512>(p, spec, s, out);
+        case 1280: return cols_t<32, 40, 512>(p, spec, s, out);
         case 1440: return cols_t<30, 48>(p, spec, s, out);
         case 1536: return cols_t<32, 48>(p, spec, s, out);
         case 1600: return cols_t<32, 50>(p, spec, s, out);
-        case 1920: return cols_t<40, 48>(p, spec, s, out);
+        case 1920: return cols_t<40, 48, 512>(p, spec, s, out);
         case 2000: return cols_t<40, 50>(p, spec, s, out);
         default: return cudaErrorInvalidValue;
     }
