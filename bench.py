@@ -259,12 +259,20 @@ def time_mlp_forward(mlp, x, sizes, reps=50):
     return res
 
 
+def head_targets(params, p8):
+    """Fit labels (A, tau, beta, B) -> the seed network's regression targets
+    (ln(A/p8), ln tau, beta, B/A): the inverse of the head A = p8 e^{o0}, tau = e^{o1},
+    B = A o3 that include/ddm.h documents (beta is regressed through its sigmoid)."""
+    A, tau, beta, B = (params[:, k] for k in range(4))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.stack([np.log(A / p8), np.log(tau), beta, B / A], axis=1)
+
+
 def compare_fits(ddm, plan, Dr, stream):
     """Train the seed network on synthetic curves (library kernels), then fit the stack's
     radial curves with plain LM and with the MLP seed; times and iteration counts."""
     import torch
     import synth
-    from oracle import fit as F   # host-side targets for the training labels only
     B_ = ddm._binding
     n_train, batch, steps = 65536, 4096, 6000
     # decay times and noise floors of the kind a blob stack's radial curves span where the
@@ -290,7 +298,7 @@ def compare_fits(ddm, plan, Dr, stream):
         & (labels[:, 0] > 0) & (labels[:, 1] > 0)
     with np.errstate(divide="ignore", invalid="ignore"):
         good &= (np.abs(np.log(labels[:, 1]) - np.log(gen[:, 1])) < 0.7) & (np.abs(labels[:, 2] - gen[:, 2]) < 0.3)
-    tg = F.targets(labels, p8h)
+    tg = head_targets(labels, p8h)
     tg[~good] = 0.0
     good &= np.all(np.isfinite(tg), axis=1) & (np.abs(tg) < 50).all(axis=1)
     keep = np.nonzero(good)[0]
