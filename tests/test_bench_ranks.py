@@ -39,3 +39,18 @@ def test_single_rank_and_throughput():
     # two ranks, 1024 frames each, 10 steps in 20 ms -> 1,024,000 frames/s for the job
     assert bench.job_throughput(2, 1024, 10, 20.0) == pytest.approx(1.024e6)
     assert bench.job_throughput(1, 1024, 10, 20.0) == pytest.approx(5.12e5)
+
+
+def test_fit_label_targets_invert_the_network_head():
+    """The bench trains the seed network on targets it derives from fit labels; they must be
+    the inverse of the head (oracle.fit.head): targets(head(o)) = (o0, o1, beta(o2), o3)."""
+    import numpy as np
+    from oracle import fit as F
+    rng = np.random.Generator(np.random.PCG64(4))
+    o = np.stack([rng.normal(0, 1, 500), rng.normal(1, 2, 500), rng.normal(0, 2, 500),
+                  rng.normal(0, 0.5, 500)], axis=1)
+    p8 = rng.uniform(0.1, 10, 500)
+    phys = F.head(o, p8)
+    t = bench.head_targets(phys, p8)
+    np.testing.assert_allclose(t[:, [0, 1, 3]], o[:, [0, 1, 3]], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(t[:, 2], phys[:, 2], rtol=0, atol=0)
