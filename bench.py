@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 tier timing")
     ap.add_argument("--sweep", action="store_true",
                     help="also time the image-size sweep 128^2 .. 2048^2 at N = 16384 (4096 at 2048^2)")
+    ap.add_argument("--crossover", action="store_true",
+                    help="also time WITH_FT vs WITHOUT_FT step two at 512^2 for N = 128 .. 16384")
     ap.add_argument("--no-long", action="store_true",
                     help="skip the 512x512x16384 (longest stacks) timing")
     ap.add_argument("--kmax", type=int, default=63,
@@ -418,6 +420,52 @@ def time_long_stack(ddm, dev, stream, seed, H=512, W=512, N=16384, steps=3):
             "frames_per_s": N / (sum(ms) / 1e3), "device_status": status, "steps": steps}
 
 
+def crossover_sweep(ddm, dev, stream, seed, side=512,
+                    Ns=(128, 256, 512, 1024, 2048, 4096, 8192, 16384)):
+    """The paper's comparison of its two schemes (Sec. 2, Figs. 1 and 3) on this GPU: per
+    stack length N, step one once, then step two by the Fourier route (ddm_temporal_sf) and
+    by explicit frame differences (ddm_temporal_sf_direct, WITHOUT_FT) on the same spectrum;
+    frames drawn on the device (timing only).  Returns the per-N times and the smallest N
+    at which the Fourier route's whole stack (step one + step two) is faster."""
+    import torch
+    rows = []
+    for N in Ns:
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed + N)
+        frames = torch.randint(1800, 2201, (N, side, side), generator=g, device=dev,
+                               dtype=torch.int16).view(torch.uint16)
+        plan = ddm.Plan(side, side, N, dtype="u16")
+        spec = torch.empty(2 * N * plan.n_q, dtype=torch.float32, device=dev)
+        D = torch.empty(plan.n_q * N, dtype=torch.float32, device=dev)
+        reps = 5 if N <= 2048 else (2 if N <= 8192 else 1)
+
+        def timed(fn, reps=reps):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        sp = timed(lambda: plan.spatial_fft(frames, spec, stream))
+        ft = timed(lambda: plan.temporal_sf(spec, D, stream))
+        dr = timed(lambda: plan.temporal_sf_direct(spec, D, stream))
+        status = plan.last_device_status()
+        rows.append({"N": N, "spatial_ms": sp, "temporal_ft_ms": ft, "temporal_direct_ms": dr,
+                     "with_ft_ms": sp + ft, "without_ft_ms": sp + dr,
+                     "speedup_with_ft": (sp + dr) / (sp + ft), "device_status": status})
+        plan.close()
+        del frames, spec, D
+        torch.cuda.empty_cache()
+    wins = [r["N"] for r in rows if r["speedup_with_ft"] > 1.0]
+    return {"side": side, "rows": rows,
+            "frames": "uniform counts 1800..2200 drawn on the device (timing only)",
+            "with_ft_faster_from_N": min(wins) if wins else None}
+
+
 def image_size_sweep(ddm, dev, stream, seed):
     """The paper's second workload (Fig. 3 shape): frame sides 128 .. 2048 at the longest
     stacks that fit (N = 16384 up to 1024^2; 2048^2 at N = 4096: its spectrum at N = 16384
@@ -666,6 +714,7 @@ def run_ours(args):
     if rank == 0 and not args.no_long:
         long_stack = time_long_stack(ddm, dev, stream, args.seed)
     sweep = image_size_sweep(ddm, dev, stream, args.seed) if (rank == 0 and args.sweep) else None
+    crossover = crossover_sweep(ddm, dev, stream, args.seed) if (rank == 0 and args.crossover) else None
 
     # ---- fit of the 362 radial curves: plain LM vs LM seeded by the trained MLP
     fit_cmp = None
@@ -751,6 +800,8 @@ def run_ours(args):
         out["long_stack"] = long_stack
     if sweep:
         out["image_size_sweep"] = sweep
+    if crossover:
+        out["crossover"] = crossover
     if fit_cmp:
         out["fit"] = fit_cmp
     if e2e:

@@ -205,6 +205,17 @@ ddm_status ddm_spatial_fft(ddm_plan p, const void* frames, float* spectrum, void
  * zero-padded transform in time (Eq. B4), D = (P1 + P2 - 2 Re C) / (N - m). */
 ddm_status ddm_temporal_sf(ddm_plan p, const float* spectrum, float* D, void* stream);
 
+/* The paper's WITHOUT_FT scheme (Sec. 2; the comparison method of its Figs. 1 and 3) on
+ * the GPU: D(q, m) = 1/(N - m) sum_{t < N-m} |F(q, t+m) - F(q, t)|^2 straight from Eq. 1,
+ * by explicit differences of the stored spectra, O(N^2) per wave vector in FP32 (sums per
+ * lag in time order).  Same input layout, output layout, wave-vector range (q_begin/q_end),
+ * low-frequency store (kmax) and status reporting as ddm_temporal_sf, so the two schemes
+ * can be timed against each other on one spectrum:
+ *   spectrum [N][n_q] complex64, device, read only (as ddm_spatial_fft writes it)
+ *   D        [n_q][N] float32, device, written (D[q][0] = 0)
+ * DDM_ERR_UNSUPPORTED for DDM_PREC_FP64 plans (complex128 spectra). */
+ddm_status ddm_temporal_sf_direct(ddm_plan p, const float* spectrum, float* D, void* stream);
+
 /* Both steps: frames [N][H][W] -> D [n_q][N].  Uses the plan's workspace for the
  * spectrum (allocated on first use if none is attached). */
 ddm_status ddm_structure_function(ddm_plan p, const void* frames, float* D, void* stream);
@@ -333,8 +344,11 @@ ddm_status ddm_mlp_train_step(ddm_mlp m, const float* x, const float* t, int B, 
  *   - the spectrum, n_q * N * 8 bytes, must fit DDM_STATIC_SCRATCH_BYTES, else
  *     DDM_ERR_UNSUPPORTED is returned and nothing is enqueued;
  *   - the plan's device must be the current device, else DDM_ERR_INVALID_ARG;
- *   - the first call on a device looks up the scratch's device address (one-time set-up);
+ *   - the first call in a CUDA context (on each device, and again after that device has
+ *     been reset) looks up the scratch's device address in that context and caches it;
  *     make that first call before capturing any stream;
+ *   - with stats enabled (ddm_plan_enable_stats), ddm_plan_stats reports this call's two
+ *     step times, as it does for ddm_structure_function;
  *   - all calls share the one scratch: calls whose work overlaps on the GPU (different
  *     streams, no ordering between them) race and give wrong results; calls ordered on
  *     one stream are safe.  Nothing in the scratch needs to start at zero. */

@@ -95,6 +95,7 @@ def lib():
         "ddm_mlp_set_state": (st, [vp, vp]),
         "ddm_spatial_fft": (st, [vp, vp, vp, vp]),
         "ddm_temporal_sf": (st, [vp, vp, vp, vp]),
+        "ddm_temporal_sf_direct": (st, [vp, vp, vp, vp]),
         "ddm_structure_function": (st, [vp, vp, vp, vp]),
         "ddm_azimuthal_average": (st, [vp, vp, vp, vp, vp]),
         "ddm_azimuthal_sums": (st, [vp, vp, vp, vp, vp]),
@@ -256,6 +257,15 @@ class Plan:
                                      _dev_ptr(spectrum, "spectrum", torch.float32, 2 * self.N * self.n_q),
                                      _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
                                      _stream_ptr(stream)), "ddm_temporal_sf")
+
+    def temporal_sf_direct(self, spectrum, D, stream=None):
+        """The WITHOUT_FT scheme (explicit frame differences, O(N^2) per wave vector) on the
+        same spectrum and output layout as temporal_sf."""
+        import torch
+        _check(lib().ddm_temporal_sf_direct(self._h,
+                                            _dev_ptr(spectrum, "spectrum", torch.float32, 2 * self.N * self.n_q),
+                                            _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
+                                            _stream_ptr(stream)), "ddm_temporal_sf_direct")
 
     def structure_function(self, frames, D, stream=None):
         import torch

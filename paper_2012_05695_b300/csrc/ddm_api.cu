@@ -626,6 +626,7 @@ ddm_status ddm_structure_function(ddm_plan p, const void* frames, float* D, void
     if (st != DDM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const bool stats = p->stats_ev[0] != nullptr;
+    p->stats_recorded = false;   // until this call's three events are on the stream
     if (stats && cudaEventRecord(p->stats_ev[0], s) != cudaSuccess) return DDM_ERR_CUDA;
     if (p->d.precision == DDM_PREC_FP64) {
         // one launch sequence: step one and step two are not separated in the stats

@@ -71,23 +71,28 @@ def test_lm_matches_oracle_on_noiseless_curves():
 
 
 def test_lm_matches_oracle_on_noisy_curves():
-    """Same curves, same algorithm: the FP32 kernel's final cost is within 1e-3 of the
-    FP64 oracle's, and its parameters agree where they are well determined."""
+    """Same curves, same algorithm, per curve: the FP32 kernel's final cost is within 1e-4
+    of the FP64 oracle's optimum, and each of its parameters (A, B, ln tau, beta) sits within
+    5 % of that parameter's standard error at the oracle's optimum (sigma^2 (J^T J)^-1,
+    sigma^2 = cost / (64 - 4)): the FP32 arithmetic moves the fit by far less than the
+    data's own noise determines it."""
     N, n = 1024, 64
     D, labels = synth.stretched_exp_curves(n, N, 2)
     plan = ddm.Plan(8, 8, N, dtype="f32")
     params, cost, iters, flags = _fit(plan, D, B.DDM_FIT_LM)
+    assert np.all(flags & B.DDM_FIT_CONVERGED), flags
     lam = F.log_lags(N)
     y = F.sample_log_lags(D.astype(np.float64))
-    worse = 0
     for c in range(n):
         p, co, it, fl = F.lm_fit(lam, y[c], F.heuristic_seed(lam, y[c]))
-        assert cost[c] <= co * (1 + 1e-3) + 1e-12 * y[c, -1] ** 2 or cost[c] <= co * 1.05, (c, cost[c], co)
-        worse += cost[c] > co * (1 + 1e-3)
-        phys = F.params_to_physical(p)
-        if 2.0 < phys[1] < 300.0:
-            np.testing.assert_allclose(params[c, [0, 2]], phys[[0, 2]], rtol=2e-2)
-    assert worse <= n // 16
+        assert fl & F.FLAG_CONVERGED
+        assert cost[c] <= co * (1 + 1e-4) + 1e-12 * y[c, -1] ** 2, (c, cost[c], co)
+        _, J = F._model_and_jac(lam, p)
+        se = np.sqrt(np.diag(np.linalg.inv(J.T @ J)) * co / (F.N_LAGS - 4))
+        A, tau, beta, Bb = params[c]
+        got = np.array([A, Bb, math.log(tau), beta])
+        dev = np.abs(got - p)
+        assert np.all(dev <= 0.05 * se + 1e-5 * np.abs(p)), (c, got, p, se)
 
 
 def test_mlp_forward_matches_oracle():
