@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ddm_fft.cuh"
 #include "ddm_internal.h"
 
 namespace ddm {
@@ -50,23 +51,9 @@ __device__ __forceinline__ int64_t direct_public_q(int64_t s, int H, int Wh, int
     return (s - main) * (Wh + 1) + Wh;
 }
 
-// Blackwell's paired FP32 instructions (PTX sub.rn.f32x2 / fma.rn.f32x2): one instruction
-// for the real and imaginary parts.  Each accumulator is a float2 that sums dx^2 and dy^2
-// separately; the two halves are added when a lag is finished.
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-    float2 r;
-    asm("{\n .reg .b64 ra, rb, rr;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
-        " sub.rn.f32x2 rr, ra, rb;\n mov.b64 {%0, %1}, rr;\n}"
-        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return r;
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    float2 r;
-    asm("{\n .reg .b64 ra, rb, rc, rr;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
-        " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rr, ra, rb, rc;\n mov.b64 {%0, %1}, rr;\n}"
-        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return r;
-}
+// The accumulators are float2: the squares of the real and imaginary differences are
+// summed in the two halves with paired FP32 instructions (sub2, fma2 of ddm_fft.cuh) and
+// added when a lag is finished.
 
 // padded shared-memory position of time index e: one gap per R elements
 __host__ __device__ __forceinline__ int pidx(int e) { return e + e / kR; }

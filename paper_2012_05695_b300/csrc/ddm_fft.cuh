@@ -85,9 +85,53 @@ __device__ __forceinline__ T* opaque_ptr(T* p) {
 // of a thread's table loads up front and run out of registers.
 __device__ __forceinline__ void hoist_fence() { asm volatile("" ::: "memory"); }
 
+// ------------------------------------------------------------------ paired FP32
+// Blackwell executes two FP32 additions or FMAs in one instruction (PTX add/sub/fma
+// .rn.f32x2 on a 64-bit register pair).  Each lane rounds exactly as the scalar
+// instruction does, so results are bitwise those of the scalar code; only the number of
+// issued instructions changes.  DDM_PAIRED selects how much of the complex arithmetic uses
+// them: 0 none, 1 complex additions, 2 also the two FMAs that finish a general butterfly.
+#ifndef DDM_PAIRED
+#define DDM_PAIRED 2
+#endif
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rr;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " add.rn.f32x2 rr, ra, rb;\n mov.b64 {%0, %1}, rr;\n}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rr;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rr, ra, rb;\n mov.b64 {%0, %1}, rr;\n}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+// a * b + c, lane by lane
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rc, rr;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rr, ra, rb, rc;\n mov.b64 {%0, %1}, rr;\n}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+
 // ------------------------------------------------------------------ complex helpers
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+#if DDM_PAIRED >= 1
+    return add2(a, b);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+#if DDM_PAIRED >= 1
+    return sub2(a, b);
+#else
+    return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
     return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
 }
@@ -145,14 +189,26 @@ __device__ __forceinline__ void bfly_const(float2 e, float2 o, float2& lo, float
             constexpr float cf = (float)c;
             constexpr float tf = (float)(s / c);
             const float ux = fmaf(-tf, o.y, o.x), uy = fmaf(tf, o.x, o.y);
+#if DDM_PAIRED >= 2
+            const float2 u = make_float2(ux, uy);
+            lo = fma2(u, make_float2(cf, cf), e);
+            hi = fma2(u, make_float2(-cf, -cf), e);
+#else
             lo = make_float2(fmaf(cf, ux, e.x), fmaf(cf, uy, e.y));
             hi = make_float2(fmaf(-cf, ux, e.x), fmaf(-cf, uy, e.y));
+#endif
         } else {
             constexpr float sf = (float)s;
             constexpr float tf = (float)(c / s);
             const float ux = fmaf(tf, o.x, -o.y), uy = fmaf(tf, o.y, o.x);
+#if DDM_PAIRED >= 2
+            const float2 u = make_float2(ux, uy);
+            lo = fma2(u, make_float2(sf, sf), e);
+            hi = fma2(u, make_float2(-sf, -sf), e);
+#else
             lo = make_float2(fmaf(sf, ux, e.x), fmaf(sf, uy, e.y));
             hi = make_float2(fmaf(-sf, ux, e.x), fmaf(-sf, uy, e.y));
+#endif
         }
     }
 }
