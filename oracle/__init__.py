@@ -207,15 +207,34 @@ def structure_function(frames: np.ndarray, kx_sel=None, nthreads=None):
     return D, plateau_scale(F)
 
 
-def scaled_error(D_test, D_ref, s_q, floor_rel=1e-12):
-    """max over q, m of |D_test - D_ref| / s_q.
+TOLERANCE = 1e-4        # |D - D_oracle| relative to the wave vector's plateau
+STATIC_REL = 1e-12      # s_q below this fraction of the largest plateau: a static mode
+STATIC_BOUND = 1e-6     # a static mode must have |D| <= STATIC_BOUND * max s_q
 
-    Static modes (s_q < floor_rel * max s_q) are measured against floor_rel * max s_q
-    instead, so that a mode with no dynamics must give D close to 0 on the global scale.
+
+def scaled_error(D_test, D_ref, s_q):
+    """The precision metric: max over q, m of |D_test - D_ref| / s_q, with s_q = 2 var_t F(q)
+    the large-lag plateau of each wave vector.
+
+    Static modes -- s_q < STATIC_REL * max s_q, whose whole time variation is far below
+    what FP32 arithmetic on the plane resolves (e.g. the DC mode of a field whose mean never
+    changes, where only the input's own rounding moves) -- are judged on the global scale
+    instead: they must have |D_test| <= STATIC_BOUND * max s_q.  Each of them enters the
+    maximum as TOLERANCE * |D_test| / (STATIC_BOUND * max s_q), so that a result <= TOLERANCE
+    means every mode passed its own rule.
     """
     s = np.asarray(s_q, dtype=np.float64)
     smax = float(np.max(s)) if s.size else 0.0
-    scale = np.maximum(s, floor_rel * smax if smax > 0 else 1.0)
-    scale = np.where(scale > 0, scale, 1.0)
-    diff = np.abs(np.asarray(D_test, np.float64) - np.asarray(D_ref, np.float64))
-    return float(np.max(diff / scale[..., None])) if diff.size else 0.0
+    Dt = np.asarray(D_test, np.float64)
+    diff = np.abs(Dt - np.asarray(D_ref, np.float64))
+    if diff.size == 0:
+        return 0.0
+    if smax <= 0.0:                        # every mode static at zero: compare absolutely
+        return float(np.max(diff))
+    static = s < STATIC_REL * smax
+    scale = np.where(static, 1.0, s)
+    err = diff / scale[..., None]
+    if np.any(static):
+        err_static = TOLERANCE * np.abs(Dt) / (STATIC_BOUND * smax)
+        err = np.where(static[..., None], err_static, err)
+    return float(np.max(err))

@@ -271,3 +271,51 @@ def test_scaled_error_metric():
     D2 = D.copy()
     D2[1, 2] = 2e-4
     assert oracle.scaled_error(D2, D, s) == pytest.approx(5e-5)
+
+
+def test_scaled_error_static_modes_on_the_global_scale():
+    """A mode whose plateau is below 1e-12 of the largest is static: it passes when
+    |D| <= 1e-6 of the largest plateau, whatever the reference says, and enters the metric
+    scaled so that the 1e-4 bar means exactly that."""
+    s = np.array([2.0, 1e-13, 0.5])
+    D_ref = np.zeros((3, 4))
+    D = D_ref.copy()
+    D[1, 3] = 1e-6 * 2.0                     # exactly the static bound
+    assert oracle.scaled_error(D, D_ref, s) == pytest.approx(oracle.TOLERANCE)
+    D[1, 3] = 3e-6 * 2.0
+    assert oracle.scaled_error(D, D_ref, s) == pytest.approx(3 * oracle.TOLERANCE)
+    D[1, 3] = 0.0
+    D_ref[1, 1] = 5.0                        # a static mode's reference plays no part
+    assert oracle.scaled_error(D, D_ref, s) == 0.0
+    D[2, 0] = 1e-5                           # an ordinary mode: relative to its own plateau
+    assert oracle.scaled_error(D, D_ref, s) == pytest.approx(2e-5)
+    # a plateau of exactly 1e-12 of the largest is not static
+    assert oracle.scaled_error(np.array([[0.0, 0.0], [0.0, 1e-16]]), np.zeros((2, 2)),
+                               np.array([1.0, 1e-12])) == pytest.approx(1e-4)
+
+
+def test_ou_torch_generator_closed_form_statistics():
+    """The torch rendering of the OU law (used for the 1024x1024x4096 precision sweep, run
+    here on the CPU) obeys the same closed form E[D] = H W (2 S (1 - e^{-D0 q^2 m}) +
+    2 sigma^2) within 5 standard errors, and its log-uniform D0 lies in [0.01, 1]."""
+    H = W = 32
+    N = 96
+    D0, width, sigma = 0.5, 0.3, 0.05
+    cols = list(range(1, W // 2))
+    ratios = {m: [] for m in (1, 3, 10, 30)}
+    qmag = synth.q_magnitude(H, W)[:, cols]
+    S = np.exp(-qmag ** 2 / (2 * width ** 2))
+    for seed in range(4):
+        frames = synth.ou_stack_torch(H, W, N, D0, synth.gaussian_spectrum(width), sigma, seed,
+                                      device="cpu").numpy()
+        D = oracle.sf_direct(oracle.dft2(frames, cols))
+        for m in ratios:
+            expect = H * W * (2 * S * (1 - np.exp(-D0 * qmag ** 2 * m)) + 2 * sigma ** 2)
+            ratios[m].append((D[:, :, m] / expect).ravel())
+    for m, r in ratios.items():
+        r = np.concatenate(r)
+        se = np.std(r) / math.sqrt(r.size)
+        assert abs(np.mean(r) - 1.0) < 5 * se, (m, np.mean(r), se)
+    rng = np.random.Generator(np.random.PCG64(1))
+    d0s = [synth.log_uniform_d0()(rng) for _ in range(200)]
+    assert 0.01 <= min(d0s) and max(d0s) <= 1.0 and min(d0s) < 0.03 and max(d0s) > 0.3
