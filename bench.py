@@ -63,6 +63,12 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 tier timing")
     ap.add_argument("--sweep", action="store_true",
                     help="also time the image-size sweep 128^2 .. 2048^2 at N = 16384 (4096 at 2048^2)")
+    ap.add_argument("--split", choices=["none", "kx"], default="none",
+                    help="kx: one stack split across the ranks by kx columns (strong scaling): "
+                         "each rank transforms every row, its own columns and their time "
+                         "sequences; the radial sums are all-reduced")
+    ap.add_argument("--no-precision-sweep", action="store_true",
+                    help="skip the 1024x1024x4096 float32 precision sweep (three tiers)")
     ap.add_argument("--crossover", action="store_true",
                     help="also time WITH_FT vs WITHOUT_FT step two at 512^2 for N = 128 .. 16384")
     ap.add_argument("--no-long", action="store_true",
@@ -479,6 +485,55 @@ def image_size_sweep(ddm, dev, stream, seed):
     return out
 
 
+def precision_sweep(ddm, dev, stream, seed, with_oracle, H=1024, W=1024, N=4096):
+    """The precision-sweep workload (1024x1024 float32, N = 4096, OU Fourier modes,
+    S(q) = 1 / max(q, 0.02)^2, D0 log-uniform in [0.01, 1]) through every precision tier of
+    ddm_structure_function: device time per stack and, with the oracle leg on, each tier's
+    max scaled error against the FP64 oracle on a bounded sample (kx = 1 and W/2, every
+    fourth ky, every lag)."""
+    import torch
+    import synth
+    frames = synth.ou_precision_sweep_1024x1024x4096(seed=seed, N=N, H=H, W=W, device=dev)
+    cols, ky_step = [1, W // 2], 4
+    D_or = s_q = None
+    if with_oracle:
+        import oracle
+        parts = [oracle.dft2(frames[t0:t0 + 128].cpu().numpy(), cols) for t0 in range(0, N, 128)]
+        F = np.concatenate(parts, axis=0)[:, ::ky_step, :]
+        D_or = oracle.sf_direct(F)
+        s_q = oracle.plateau_scale(F)
+    tiers = {}
+    for name, prec, reps in (("fp32", ddm.DDM_PREC_FP32, 3), ("fp32_fp64fix", ddm.DDM_PREC_FP32_FP64FIX, 3),
+                             ("fp64", ddm.DDM_PREC_FP64, 1)):
+        plan = ddm.Plan(H, W, N, dtype="f32", precision=prec)
+        D = torch.empty(plan.n_q * N, dtype=torch.float32, device=dev)
+        plan.structure_function(frames, D, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            plan.structure_function(frames, D, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        row = {"structure_function_ms": ms, "frames_per_s": N / (ms / 1e3),
+               "device_status": plan.last_device_status()}
+        if D_or is not None:
+            got = D.view(H, W // 2 + 1, N)[::ky_step, cols, :].cpu().numpy()
+            row["max_rel_err"] = oracle.scaled_error(got, D_or, s_q)
+        tiers[name] = row
+        plan.close()
+        del D
+        torch.cuda.empty_cache()
+    del frames
+    torch.cuda.empty_cache()
+    return {"workload": f"ou_powerlaw_{H}x{W}x{N}_f32", "H": H, "W": W, "N": N,
+            "frames": "OU Fourier modes, S = 1/max(q, 0.02)^2, D0 log-uniform [0.01, 1], rendered on the device",
+            "error_sample": (f"kx in {cols}, every {ky_step}th ky, all lags; max |D - D_oracle| / s_q"
+                             if with_oracle else None),
+            "tiers": tiers}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -511,6 +566,82 @@ def run_reference(args):
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_split(args):
+    """One 512x512x1024 stack per step, split across the ranks by kx columns
+    (partition.kx_ranges): every rank reads the whole stack and transforms every row, then
+    only its own columns (step one) and their time sequences (step two); its radial sums
+    are all-reduced (the one collective) and rank 0 fits the merged radial curves.  The
+    whole job processes one stack per step, so "value" is strong scaling."""
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2012_05695_b300 as ddm
+    import synth
+    from paper_2012_05695_b300 import partition
+    dev = torch.device("cuda", local)
+    frames_np = synth.blobs_512x512x1024(seed=args.seed, N=N_FRAMES, H=H, W=W)   # one stack
+    kx0, kx1 = partition.kx_ranges(W, ws)[rank]
+    plan = ddm.Plan(H, W, N_FRAMES, dtype="u16", n_bins=N_BINS, kx_begin=kx0, kx_end=kx1)
+    frames = torch.from_numpy(frames_np).to(dev)
+    D = torch.empty(plan.d_rows * N_FRAMES, dtype=torch.float32, device=dev)
+    sums = torch.empty(N_BINS * N_FRAMES, dtype=torch.float32, device=dev)
+    counts = torch.empty(N_BINS, dtype=torch.int32, device=dev)
+    prm = torch.empty(N_BINS * 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.structure_function(frames, D, stream)
+        plan.azimuthal_sums(D, sums, counts, stream)
+        if dist:
+            Dr = partition.allreduce_radial(sums.view(N_BINS, N_FRAMES), counts)
+        else:
+            Dr = partition.merge_radial(sums.view(N_BINS, N_FRAMES), counts)
+        if rank == 0:
+            plan.fit(Dr.contiguous().view(-1), N_BINS, ddm._binding.DDM_FIT_LM, None, prm,
+                     None, None, None, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = clk.mark()
+        start.record(stream)
+        for _ in range(args.steps):
+            step()
+        end.record(stream)
+        torch.cuda.synchronize()
+        t1 = clk.mark()
+        if dist:
+            dist.barrier()
+    ms_total = max_over_ranks(start.elapsed_time(end), dist, dev)
+    value = N_FRAMES * args.steps / (ms_total / 1e3)          # one stack per step, whole job
+    status = plan.last_device_status()
+    out = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "N": N_FRAMES, "n_bins": N_BINS,
+                   "parallelism": f"kx-column split x{ws}", "rank0_kx_range": [kx0, kx1],
+                   "l2": "inputs larger than L2: no flush"},
+        "gpu_launches": 7 * args.steps, "clocks": clk.summary(t0, t1), "device_status": status,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -715,6 +846,10 @@ def run_ours(args):
         long_stack = time_long_stack(ddm, dev, stream, args.seed)
     sweep = image_size_sweep(ddm, dev, stream, args.seed) if (rank == 0 and args.sweep) else None
     crossover = crossover_sweep(ddm, dev, stream, args.seed) if (rank == 0 and args.crossover) else None
+    psweep = None
+    if rank == 0 and not args.no_precision_sweep:
+        psweep = precision_sweep(ddm, dev, stream, args.seed,
+                                 with_oracle=(ws == 1 and not args.no_cpu_baseline))
 
     # ---- fit of the 362 radial curves: plain LM vs LM seeded by the trained MLP
     fit_cmp = None
@@ -802,6 +937,8 @@ def run_ours(args):
         out["image_size_sweep"] = sweep
     if crossover:
         out["crossover"] = crossover
+    if psweep:
+        out["precision_sweep"] = psweep
     if fit_cmp:
         out["fit"] = fit_cmp
     if e2e:
@@ -819,6 +956,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.split == "kx":
+        return run_split(args)
     return run_ours(args)
 
 

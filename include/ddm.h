@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define DDM_ABI_VERSION 4
+#define DDM_ABI_VERSION 5
 
 typedef enum ddm_status {
     DDM_OK = 0,
@@ -119,6 +119,23 @@ typedef struct ddm_plan_desc {
                           whose sides are powers of two (DDM_ERR_UNSUPPORTED otherwise).
                           The plan then also owns an
                           intermediate of N * H * (kmax + 1) complex64 for step one */
+    int kx_begin;      /* kx-column range [kx_begin, kx_end) of one rank's share of a stack
+                          split across GPUs by columns of the half plane (0, 0 = every
+                          column).  Step one transforms every row (it needs all of them)
+                          but only the range's columns; its spectrum store holds just the
+                          range: [N][n_q], n_q = H (kx_end - kx_begin), stored [ky][kx -
+                          kx_begin], followed -- for the range that starts at kx_begin = 0 --
+                          by the H entries of the kx = W/2 column (n_q += H).  Step two, the
+                          radial stage and D rows work on that store; D rows keep the
+                          whole plane's public order q = ky (W/2 + 1) + kx, so every D
+                          argument is [H (W/2 + 1)][N] (rows of other columns untouched),
+                          and the ranks' D rows together are the whole plan's, bitwise.  kx_begin and kx_end multiples of 16,
+                          0 <= kx_begin < kx_end <= W/2 (DDM_ERR_INVALID_ARG otherwise);
+                          power-of-two sides 32 .. 1024, DDM_PREC_FP32 or _FP64FIX, no kmax,
+                          no q_begin/q_end, two-pass step one (DDM_ERR_UNSUPPORTED
+                          otherwise).  The workspace then also holds step one's row-pass
+                          output for the whole plane (N H (W/2 + 1) complex64) */
+    int kx_end;
 } ddm_plan_desc;
 
 typedef struct ddm_plan_s* ddm_plan;

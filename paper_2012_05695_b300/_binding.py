@@ -62,6 +62,7 @@ class ddm_plan_desc(ctypes.Structure):
         ("spatial_path", ctypes.c_int),
         ("q_begin", ctypes.c_int64), ("q_end", ctypes.c_int64),
         ("kmax", ctypes.c_int),
+        ("kx_begin", ctypes.c_int), ("kx_end", ctypes.c_int),
     ]
 
 
@@ -184,7 +185,7 @@ class Plan:
     def __init__(self, H: int, W: int, N: int, dtype: str = "u16", n_bins: int = 0,
                  precision: int = DDM_PREC_FP32, subtract_ref: int = 1, M: int = 0,
                  fix_lags: int = 0, max_workspace_bytes: int = 0, spatial_path: int = 0,
-                 q_begin: int = 0, q_end: int = 0, kmax: int = 0):
+                 q_begin: int = 0, q_end: int = 0, kmax: int = 0, kx_begin: int = 0, kx_end: int = 0):
         L = lib()
         d = ddm_plan_desc()
         _check(L.ddm_plan_desc_init(ctypes.byref(d), H, W, N), "ddm_plan_desc_init")
@@ -199,9 +200,12 @@ class Plan:
         d.q_begin = q_begin
         d.q_end = q_end
         d.kmax = kmax
+        d.kx_begin = kx_begin
+        d.kx_end = kx_end
         self.desc = d
         self.H, self.W, self.N, self.n_bins = H, W, N, n_bins
         self.kmax = kmax
+        self.kx_begin, self.kx_end = kx_begin, kx_end
         self.dtype = dtype
         h = ctypes.c_void_p()
         _check(L.ddm_plan_create(ctypes.byref(h), ctypes.byref(d)), "ddm_plan_create")
@@ -209,13 +213,18 @@ class Plan:
         nq = ctypes.c_int64()
         _check(L.ddm_plan_n_q(h, ctypes.byref(nq)), "ddm_plan_n_q")
         self.n_q = int(nq.value)
+        # rows of D: the stored wave vectors, except for a kx-column range, whose rows keep
+        # the whole half plane's order (its D is the whole plane's size)
+        self.d_rows = H * (W // 2 + 1) if kx_end > 0 else self.n_q
 
     @property
     def handle(self):
         return self._h
 
     def wave_vectors(self):
-        """(ky, kx) of every D row, ky in 0..H-1 (numpy int arrays of length n_q)."""
+        """(ky, kx) of every stored wave vector, in the spectrum store's order, ky in 0..H-1
+        (numpy int arrays of length n_q).  For the whole plane and the cropped store this is
+        also the order of D's rows; a kx-column range writes D rows ky (W/2 + 1) + kx."""
         import numpy as np
         if self.kmax > 0:
             k = self.kmax
@@ -223,6 +232,14 @@ class Plan:
             kys = np.where(r <= k, r, r - (2 * k + 1)) % self.H
             ky = np.repeat(kys, k + 1)
             kx = np.tile(np.arange(k + 1), 2 * k + 1)
+            return ky, kx
+        if self.kx_end > 0:
+            nk = self.kx_end - self.kx_begin
+            ky = np.repeat(np.arange(self.H), nk)
+            kx = np.tile(np.arange(self.kx_begin, self.kx_end), self.H)
+            if self.kx_begin == 0:
+                ky = np.concatenate([ky, np.arange(self.H)])
+                kx = np.concatenate([kx, np.full(self.H, self.W // 2)])
             return ky, kx
         q = np.arange(self.n_q)
         return q // (self.W // 2 + 1), q % (self.W // 2 + 1)
@@ -255,7 +272,7 @@ class Plan:
         import torch
         _check(lib().ddm_temporal_sf(self._h,
                                      _dev_ptr(spectrum, "spectrum", torch.float32, 2 * self.N * self.n_q),
-                                     _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
+                                     _dev_ptr(D, "D", torch.float32, self.d_rows * self.N),
                                      _stream_ptr(stream)), "ddm_temporal_sf")
 
     def temporal_sf_direct(self, spectrum, D, stream=None):
@@ -264,25 +281,25 @@ class Plan:
         import torch
         _check(lib().ddm_temporal_sf_direct(self._h,
                                             _dev_ptr(spectrum, "spectrum", torch.float32, 2 * self.N * self.n_q),
-                                            _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
+                                            _dev_ptr(D, "D", torch.float32, self.d_rows * self.N),
                                             _stream_ptr(stream)), "ddm_temporal_sf_direct")
 
     def structure_function(self, frames, D, stream=None):
         import torch
         _check(lib().ddm_structure_function(self._h, self._frames(frames),
-                                            _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
+                                            _dev_ptr(D, "D", torch.float32, self.d_rows * self.N),
                                             _stream_ptr(stream)), "ddm_structure_function")
 
     def azimuthal_average(self, D, Dr, counts=None, stream=None):
         import torch
         cp = ctypes.c_void_p(0) if counts is None else _dev_ptr(counts, "counts", torch.int32, self.n_bins)
-        _check(lib().ddm_azimuthal_average(self._h, _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
+        _check(lib().ddm_azimuthal_average(self._h, _dev_ptr(D, "D", torch.float32, self.d_rows * self.N),
                                            _dev_ptr(Dr, "Dr", torch.float32, self.n_bins * self.N),
                                            cp, _stream_ptr(stream)), "ddm_azimuthal_average")
 
     def azimuthal_sums(self, D, sums, counts, stream=None):
         import torch
-        _check(lib().ddm_azimuthal_sums(self._h, _dev_ptr(D, "D", torch.float32, self.n_q * self.N),
+        _check(lib().ddm_azimuthal_sums(self._h, _dev_ptr(D, "D", torch.float32, self.d_rows * self.N),
                                         _dev_ptr(sums, "sums", torch.float32, self.n_bins * self.N),
                                         _dev_ptr(counts, "counts", torch.int32, self.n_bins),
                                         _stream_ptr(stream)), "ddm_azimuthal_sums")

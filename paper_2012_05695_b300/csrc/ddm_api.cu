@@ -185,9 +185,19 @@ std::vector<float2> pass_twiddles(int L) {
     return t;
 }
 
+bool kx_ranged(const ddm_plan_desc& d) { return d.kx_begin != 0 || d.kx_end != 0; }
+
 size_t stored_wave_vectors(const ddm_plan_desc& d) {
     if (d.kmax > 0) return (size_t)(2 * d.kmax + 1) * (size_t)(d.kmax + 1);
+    if (kx_ranged(d))
+        return (size_t)d.H * (size_t)(d.kx_end - d.kx_begin) + (d.kx_begin == 0 ? (size_t)d.H : 0);
     return (size_t)d.H * (size_t)(d.W / 2 + 1);
+}
+
+// kx-column range: step one's whole-plane row output, after the range's store
+size_t row_output_bytes(const ddm_plan_desc& d) {
+    if (!kx_ranged(d)) return 0;
+    return (size_t)d.H * (size_t)(d.W / 2 + 1) * (size_t)d.N * sizeof(float2);
 }
 
 size_t spectrum_bytes(const ddm_plan_desc& d) {
@@ -210,7 +220,7 @@ size_t blocked_bytes(const ddm_plan_desc& d) {
 // allows the extra copy.
 bool spectrum_blocked(const ddm_plan_desc& d) {
     const int L = 1 << ilog2(d.N);
-    if (L < 2048 || d.precision == DDM_PREC_FP64) return false;
+    if (L < 2048 || d.precision == DDM_PREC_FP64 || kx_ranged(d)) return false;
     if ((int64_t)stored_wave_vectors(d) < (L == 16384 ? kBlockedMinQ16k : kBlockedMinQ)) return false;
     if (d.max_workspace_bytes != 0 && spectrum_bytes(d) + blocked_bytes(d) > d.max_workspace_bytes)
         return false;
@@ -218,7 +228,7 @@ bool spectrum_blocked(const ddm_plan_desc& d) {
 }
 
 size_t workspace_bytes(const ddm_plan_desc& d) {
-    return spectrum_bytes(d) + (spectrum_blocked(d) ? blocked_bytes(d) : 0);
+    return spectrum_bytes(d) + (spectrum_blocked(d) ? blocked_bytes(d) : 0) + row_output_bytes(d);
 }
 
 ddm_status validate(const ddm_plan_desc* d) {
@@ -263,6 +273,16 @@ ddm_status validate(const ddm_plan_desc* d) {
         const int64_t nq = (int64_t)stored_wave_vectors(*d);
         if (d->q_begin < 0 || d->q_begin % 64 != 0 || d->q_end <= d->q_begin || d->q_end > nq)
             return DDM_ERR_INVALID_ARG;
+    }
+    if (kx_ranged(*d)) {
+        const int Wh = d->W / 2;
+        if (d->kx_begin < 0 || d->kx_begin % 16 != 0 || d->kx_end % 16 != 0 ||
+            d->kx_end <= d->kx_begin || d->kx_end > Wh)
+            return DDM_ERR_INVALID_ARG;
+        if (!is_pow2(d->H) || !is_pow2(d->W) || d->W < 32 || d->H > 1024 || d->W > 1024 ||
+            d->kmax != 0 || d->q_begin != 0 || d->q_end != 0 || d->precision == DDM_PREC_FP64 ||
+            d->spatial_path != DDM_SPATIAL_TWO_PASS)
+            return DDM_ERR_UNSUPPORTED;
     }
     if (d->precision == DDM_PREC_FP64 && !fp64_supported(*d)) return DDM_ERR_UNSUPPORTED;
     if (d->max_workspace_bytes != 0 && workspace_bytes(*d) > d->max_workspace_bytes)
@@ -339,7 +359,11 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
     p->L = 1 << ilog2(desc->N);
     p->Wh = desc->W / 2;
     p->kc = desc->kmax;
+    p->kx0 = kx_ranged(*desc) ? desc->kx_begin : 0;
+    p->nk = kx_ranged(*desc) ? desc->kx_end - desc->kx_begin : 0;
+    p->full_nq = (int64_t)desc->H * (desc->W / 2 + 1);
     p->n_q = (int64_t)stored_wave_vectors(*desc);
+    p->inter_offset = spectrum_bytes(*desc);
     const bool ranged = desc->q_begin != 0 || desc->q_end != 0;
     p->q0 = ranged ? desc->q_begin : 0;
     p->q1 = ranged ? desc->q_end : p->n_q;
@@ -423,15 +447,25 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
         // D row of (ky, kx) and its stored index: the full half plane (D row ky*(Wh+1)+kx;
         // stored main block then the kx = W/2 column) or the cropped window (both in the
         // window's order)
-        std::vector<int> bin_of((size_t)p->n_q, -1);
-        std::vector<int> count(nb, 0), start(nb + 1, 0);
+        // (a kx-column range: the range's columns, D rows in the whole plane's order)
         const int KC = p->kc;
         const int rows = KC > 0 ? 2 * KC + 1 : H, cols = KC > 0 ? KC + 1 : Wh + 1;
+        const int64_t n_rows_d = (int64_t)rows * cols;      // D rows indexed below
+        std::vector<int> bin_of((size_t)n_rows_d, -1);
+        std::vector<int> count(nb, 0), start(nb + 1, 0);
         for (int r = 0; r < rows; ++r) {
             const int ys = KC > 0 ? (r <= KC ? r : r - (2 * KC + 1)) : (r > H / 2 ? r - H : r);
             for (int kx = 0; kx < cols; ++kx) {
-                const int64_t stored = KC > 0 ? (int64_t)r * cols + kx
-                                              : (kx < Wh ? (int64_t)r * Wh + kx : (int64_t)H * Wh + r);
+                int64_t stored;
+                if (KC > 0) {
+                    stored = (int64_t)r * cols + kx;
+                } else if (p->nk > 0) {
+                    if (kx < Wh && (kx < p->kx0 || kx >= p->kx0 + p->nk)) continue;
+                    if (kx == Wh && p->kx0 != 0) continue;
+                    stored = kx < Wh ? (int64_t)r * p->nk + (kx - p->kx0) : (int64_t)H * p->nk + r;
+                } else {
+                    stored = kx < Wh ? (int64_t)r * Wh + kx : (int64_t)H * Wh + r;
+                }
                 if (stored < p->q0 || stored >= p->q1) continue;
                 const int b = radial_bin(ys, kx, H, W, nb);
                 bin_of[(size_t)r * cols + kx] = b;
@@ -441,7 +475,7 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
         }
         for (int b = 0; b < nb; ++b) start[b + 1] += start[b];
         std::vector<int> items((size_t)start[nb] > 0 ? (size_t)start[nb] : 1), fill(start.begin(), start.end() - 1);
-        for (int64_t q = 0; q < p->n_q; ++q) {
+        for (int64_t q = 0; q < n_rows_d; ++q) {
             if (bin_of[q] < 0) continue;
             const int kx = (int)(q % cols);
             const bool single = kx == 0 || (KC == 0 && kx == Wh);
@@ -604,6 +638,10 @@ ddm_status ddm_spatial_fft(ddm_plan p, const void* frames, float* spectrum, void
     if (!check_plan(p) || !frames || !spectrum) return DDM_ERR_INVALID_ARG;
     if (p->d.precision == DDM_PREC_FP64) return DDM_ERR_UNSUPPORTED;
     if ((reinterpret_cast<uintptr_t>(spectrum) & 7) != 0) return DDM_ERR_INVALID_ARG;
+    if (p->nk > 0) {                       // the whole-plane row output lives in the workspace
+        const ddm_status st = ensure_workspace(p);
+        if (st != DDM_OK) return st;
+    }
     return launch_spatial(p, frames, reinterpret_cast<float2*>(spectrum), (cudaStream_t)stream);
 }
 

@@ -35,14 +35,23 @@ struct DirArgs {
     int pairs;         // nb / 2
     int QC;            // wave vectors per CTA
     int S;             // padded sequence stride (float2), odd
-    int H, Wh, crop;
+    int H, Wh, crop, kx0, nk;
     int64_t n_q, q0, q1;
     unsigned* status;
 };
 
-// storage index -> public q (the row of D), as in the WITH_FT time kernels
-__device__ __forceinline__ int64_t direct_public_q(int64_t s, int H, int Wh, int crop) {
-    if (crop) return s;
+// storage index -> public q (the row of D), as in the WITH_FT time kernels: crop = 1 the
+// low-frequency store (D rows in stored order), 2 a kx-column range [kx0, kx0 + nk)
+__device__ __forceinline__ int64_t direct_public_q(int64_t s, int H, int Wh, int crop, int kx0, int nk) {
+    if (crop == 1) return s;
+    if (crop == 2) {
+        const int64_t main = (int64_t)H * nk;
+        if (s < main) {
+            const int64_t ky = s / nk;
+            return ky * (Wh + 1) + kx0 + (s - ky * nk);
+        }
+        return (s - main) * (Wh + 1) + Wh;
+    }
     const int64_t main = (int64_t)H * Wh;
     if (s < main) {
         const int64_t ky = s / Wh;
@@ -139,7 +148,7 @@ direct_sf_kernel(const float2* __restrict__ spec, float* __restrict__ D, DirArgs
     const int64_t q = qb + c;
     if (q >= a.q1) return;
     const float2* g = ser + c * S;
-    float* drow = D + direct_public_q(q, a.H, a.Wh, a.crop) * (int64_t)N;
+    float* drow = D + direct_public_q(q, a.H, a.Wh, a.crop, a.kx0, a.nk) * (int64_t)N;
     if (tg == 0) drow[0] = 0.f;
     float chk = 0.f;
     float2 acc[kR];
@@ -198,7 +207,9 @@ ddm_status launch_direct(const ddm_plan_s* p, const float2* spec, float* D, cuda
     a.QC = QC;
     a.H = p->d.H;
     a.Wh = p->Wh;
-    a.crop = p->kc > 0 ? 1 : 0;
+    a.crop = p->kc > 0 ? 1 : (p->nk > 0 ? 2 : 0);
+    a.kx0 = p->kx0;
+    a.nk = p->nk;
     a.n_q = p->n_q;
     a.q0 = p->q0;
     a.q1 = p->q1;

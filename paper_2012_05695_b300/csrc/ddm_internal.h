@@ -31,6 +31,11 @@ struct ddm_plan_s {
     int64_t n_q;        // H * (W/2 + 1)
     int64_t q0, q1;     // stored wave vectors covered by step two and the radial stage
     int kc;             // low-frequency restriction: kmax (0 = full half plane)
+    int kx0, nk;        // kx-column range [kx0, kx0 + nk) (nk = 0: every column); its store
+                        // is [N][n_q], n_q = H nk (+ H for the kx = W/2 column when kx0 = 0)
+    int64_t full_nq;    // H (W/2 + 1): frame stride of step one's whole-plane row output
+    size_t inter_offset = 0;   // kx-column range: byte offset of that row output in the
+                               // workspace (after the range's own store)
     ddm_bluestein blue_w, blue_h;   // rows / columns of non-power-of-two length
     ddm_mixed mix_w, mix_h;         // rows / columns of a mixed-radix side (before Bluestein)
     double2* tw64 = nullptr;        // FP64 tier: exp(-2 pi i r / fp64_ntab), r < fp64_ntab / 2
@@ -91,12 +96,32 @@ ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cu
 // Where a column pass writes the spectrum entry (frame t, stored wave vector q): in place in
 // the [t][q] spectrum (blk == nullptr), or into the blocked copy [b][t][16] of the range
 // [q0, q1) that the long time kernels read (entries outside the range are not written).
+// Or, for a kx-column range, into the range's store [t][n_qc] (entries of other columns
+// are not written): stored index ky nk + (kx - kx0), then the kx = W/2 column (kx0 = 0).
 struct SpecOut {
     float2* blk;
     int N;
     int64_t q0, q1;
+    float2* col = nullptr;
+    int64_t n_qc = 0;
+    int H = 0, Wh = 0, kx0 = 0, nk = 0;
 #ifdef __CUDACC__
+    __device__ __forceinline__ bool redirected() const { return blk != nullptr || col != nullptr; }
     __device__ __forceinline__ void put(float2* frame, int t, int64_t q, float2 v) const {
+        if (col) {
+            const int64_t main = (int64_t)H * Wh;
+            int64_t cs;
+            if (q < main) {
+                const int64_t ky = q / Wh, kx = q - ky * Wh;
+                if (kx < kx0 || kx >= kx0 + nk) return;
+                cs = ky * nk + (kx - kx0);
+            } else {
+                if (kx0 != 0) return;
+                cs = (int64_t)H * nk + (q - main);
+            }
+            col[(int64_t)t * n_qc + cs] = v;
+            return;
+        }
         if (!blk) {
             frame[q] = v;
             return;

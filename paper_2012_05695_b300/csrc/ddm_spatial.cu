@@ -110,7 +110,7 @@ row_r2c_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
 template <int H, int QC>
 __global__ void __launch_bounds__(QC * FftShape<H>::T, (QC * FftShape<H>::T) >= 512 ? 1 : (QC * FftShape<H>::T) >= 256 ? 2 : 4)
 col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
-               const float2* __restrict__ tw_g, SpecOut out) {
+               const float2* __restrict__ tw_g, SpecOut out, int bx0) {
     using S = FftShape<H>;
     constexpr int P = S::P, T = S::T, NT = QC * T;
     extern __shared__ float2 smem[];
@@ -123,7 +123,8 @@ col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
     }
     const int ql = tid % QC;
     const int i = tid / QC;
-    const int kx = blockIdx.x * QC + ql;
+    const int bx = blockIdx.x + bx0;          // column block (a kx-column range starts at bx0)
+    const int kx = bx * QC + ql;
     const int t = blockIdx.y;
     float2* base = spec + (size_t)t * frame_stride;
     // 32-bit element offsets (a frame holds < 2^32 elements): cheap strided addressing
@@ -137,8 +138,8 @@ col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
     fft_cyclic<H, false>(v, i, xs, addr, tw, SyncBlock{});
 
     base = opaque_ptr(base);
-    if (blockIdx.x != 0) {
-        if (!out.blk) {
+    if (bx != 0) {
+        if (!out.redirected()) {
 #pragma unroll
             for (int u = 0; u < P; ++u) base[off0 + (uint32_t)u * step] = v[u];
         } else {
@@ -258,11 +259,13 @@ cudaError_t launch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecO
     const size_t frame_stride = spectrum_frame_stride(p);
     auto go = [&](auto qc_tag) -> cudaError_t {
         constexpr int QC = decltype(qc_tag)::value;
-        dim3 grid(Wh / QC, N);
+        // a kx-column range transforms only its own column blocks
+        const int nblk = p->nk > 0 ? p->nk / QC : Wh / QC, bx0 = p->nk > 0 ? p->kx0 / QC : 0;
+        dim3 grid(nblk, N);
         const size_t smem = sizeof(float2) * ((S::T > 1 ? H : 0) + (size_t)H * QC);
         auto k = col_c2c_kernel<H, QC>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, QC * S::T, smem, s>>>(spec, Wh, frame_stride, p->tw_col, out);
+        k<<<grid, QC * S::T, smem, s>>>(spec, Wh, frame_stride, p->tw_col, out, bx0);
         return cudaGetLastError();
     };
     if (Wh >= 16) return go(std::integral_constant<int, 16>{});
@@ -307,7 +310,7 @@ cudaError_t dispatch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s, Spe
 
 }  // namespace
 
-size_t spectrum_frame_stride(const ddm_plan_s* p) { return (size_t)p->n_q; }
+size_t spectrum_frame_stride(const ddm_plan_s* p) { return (size_t)(p->nk > 0 ? p->full_nq : p->n_q); }
 
 bool fused_spatial_supported(const ddm_plan_s* p);
 ddm_status launch_spatial_fused(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);
@@ -321,6 +324,25 @@ ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
                           float2* blk_out, bool* wrote_blocked) {
     if (wrote_blocked) *wrote_blocked = false;
     const SpecOut out{blk_out, p->d.N, p->q0, p->q1};
+    if (p->nk > 0) {
+        // kx-column range: every row into the whole-plane row output in the workspace, then
+        // the range's column blocks into the range's own store `spec`
+        if (!p->workspace) return DDM_ERR_NO_WORKSPACE;
+        float2* inter = reinterpret_cast<float2*>(static_cast<char*>(p->workspace) + p->inter_offset);
+        cudaError_t e = rows_bulk_supported(p, frames)
+                            ? launch_rows_bulk(p, frames, inter, s)
+                            : ((p->d.dtype == DDM_IN_U16) ? dispatch_rows<uint16_t>(p, frames, inter, s)
+                                                          : dispatch_rows<float>(p, frames, inter, s));
+        if (e != cudaSuccess) return DDM_ERR_CUDA;
+        SpecOut cout{nullptr, p->d.N, p->q0, p->q1};
+        cout.col = spec;
+        cout.n_qc = p->n_q;
+        cout.H = p->d.H;
+        cout.Wh = p->Wh;
+        cout.kx0 = p->kx0;
+        cout.nk = p->nk;
+        return dispatch_cols(p, inter, s, cout) == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
+    }
     if (p->kc > 0) {
         // low-frequency restriction: bulk-staged row pass into the intermediate, then the
         // cropping column pass
@@ -778,7 +800,7 @@ cudaError_t launch_rows_bulk_t(const ddm_plan_s* p, const void* frames, float2* 
     // intermediate [N][H][kc + 1]
     const bool crop = p->kc > 0;
     float2* out = crop ? p->crop_inter : spec;
-    const size_t fstride = crop ? (size_t)p->d.H * (size_t)(p->kc + 1) : (size_t)p->n_q;
+    const size_t fstride = crop ? (size_t)p->d.H * (size_t)(p->kc + 1) : spectrum_frame_stride(p);
     k<<<grid, C::NT, C::BYTES, s>>>((const In*)frames, out, p->d.H, fstride, p->d.subtract_ref,
                                      p->tw_row, p->dev_status, p->kc);
     return cudaGetLastError();

@@ -88,6 +88,7 @@ extern "C" ddm_status ddm_structure_function_static(ddm_plan p, const void* fram
     if (!p || !frames || !D) return DDM_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(D) & 3) != 0) return DDM_ERR_INVALID_ARG;
     if (p->d.precision == DDM_PREC_FP64) return DDM_ERR_UNSUPPORTED;
+    if (p->nk > 0) return DDM_ERR_UNSUPPORTED;   // a kx-column range needs its workspace
     const size_t need = (size_t)p->n_q * (size_t)p->d.N * sizeof(float2);
     if (need > (size_t)DDM_STATIC_SCRATCH_BYTES) return DDM_ERR_UNSUPPORTED;
     int dev = -1;

@@ -139,7 +139,9 @@ struct TArgs {
     int N;            // frames
     int kd;           // directly evaluated trailing lags (<= 32, < N)
     int H, Wh;        // for the storage -> public q map
-    int crop;         // low-frequency restriction: D rows in stored order
+    int crop;         // stored order -> D row: 0 whole half plane, 1 low-frequency store
+                      // (D rows in stored order), 2 kx-column range [kx0, kx0 + nk)
+    int kx0, nk;
     int64_t n_q;      // stored wave vectors = spectrum frame stride
     int64_t q0, q1;   // stored wave vectors this launch covers: [q0, q1)
     int64_t n_tiles;  // tiles of [q0, q1) (of one group, L >= 512; of one CTA, L <= 256)
@@ -154,10 +156,20 @@ struct TArgs {
 };
 
 // storage index -> public q = ky * (Wh + 1) + kx (Wh = W/2 is a power of two); with the
-// low-frequency restriction (crop) the stored order is the D order
-__device__ __forceinline__ int public_q(int s, int H, int Wh, int crop) {
-    if (crop) return s;
-    const int main = H * Wh;
+// low-frequency restriction (crop = 1) the stored order is the D order; a kx-column range
+// (crop = 2) stores [ky][kx - kx0] and then, for kx0 = 0, the kx = W/2 column
+__device__ __forceinline__ int public_q(int s, const TArgs& a) {
+    if (a.crop == 1) return s;
+    const int Wh = a.Wh;
+    if (a.crop == 2) {
+        const int main = a.H * a.nk;
+        if (s < main) {
+            const int ky = s / a.nk;
+            return ky * (Wh + 1) + a.kx0 + (s - ky * a.nk);
+        }
+        return (s - main) * (Wh + 1) + Wh;
+    }
+    const int main = a.H * Wh;
     if (s < main) {
         const int ky = s / Wh;
         return ky * (Wh + 1) + (s - ky * Wh);
@@ -534,7 +546,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             if (tg < QG) {
                 const int64_t sr = q0 + gt * QG + tg;
                 if (sr < q1) {
-                    float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.crop) * N;
+                    float* drow = D + (int64_t)public_q((int)sr, a) * N;
                     bulk_store(drow, ab + tg * DS, (uint32_t)N * (uint32_t)sizeof(float));
                 }
                 bulk_commit();
@@ -544,7 +556,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             for (int r = 0; r < QG; ++r) {
                 const int64_t sr = q0 + gt * QG + r;
                 if (sr >= q1) break;
-                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.crop) * N;
+                float* drow = D + (int64_t)public_q((int)sr, a) * N;
                 for (int m = tg; m < N; m += GT) drow[m] = ab[r * DS + m];
             }
         }
@@ -886,7 +898,7 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             if (tid < QG) {
                 const int64_t sr = q0 + tile * QG + tid;
                 if (sr < q1) {
-                    float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.crop) * N;
+                    float* drow = D + (int64_t)public_q((int)sr, a) * N;
                     bulk_store(drow, ab + tid * DS, (uint32_t)N * (uint32_t)sizeof(float));
                 }
                 bulk_commit();
@@ -895,7 +907,7 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             for (int r = 0; r < QG; ++r) {
                 const int64_t sr = q0 + tile * QG + r;
                 if (sr >= q1) break;
-                float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.crop) * N;
+                float* drow = D + (int64_t)public_q((int)sr, a) * N;
                 for (int m = tid; m < N; m += NT) drow[m] = ab[r * DS + m];
             }
         }
@@ -1124,7 +1136,7 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
         }
         __syncthreads();
         // ---- D(m) = (P1 + P2 - 2 Re C) / (N - m), m = i + T u, straight to global memory
-        float* drow = D + (int64_t)public_q((int)sq, a.H, a.Wh, a.crop) * N;
+        float* drow = D + (int64_t)public_q((int)sq, a) * N;
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             const int m = i + T * u;
@@ -1378,7 +1390,7 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
         for (int r = 0; r < QT; ++r) {
             const int64_t sr = q0 + tile * QT + r;
             if (sr >= q1) break;
-            float* drow = D + (int64_t)public_q((int)sr, a.H, a.Wh, a.crop) * N;
+            float* drow = D + (int64_t)public_q((int)sr, a) * N;
             for (int m = tid; m < N; m += NT) {
                 const float d = xf[r * DS + m];
                 bad |= !isfinite(d);
@@ -1474,7 +1486,9 @@ void fill_args(TArgs& a, const ddm_plan_s* p, float* D, int qt) {
     a.kd = p->kd;
     a.H = p->d.H;
     a.Wh = p->Wh;
-    a.crop = p->kc > 0;
+    a.crop = p->kc > 0 ? 1 : (p->nk > 0 ? 2 : 0);
+    a.kx0 = p->kx0;
+    a.nk = p->nk;
     a.vec4 = (p->d.N % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
     a.blocked = 0;
     a.fix = (p->d.precision == DDM_PREC_FP32_FP64FIX) ? p->fix_lags : 0;

@@ -3,7 +3,9 @@
 The paper measured 16-bit microscopy image sets of up to 2^14 frames (Sec. 2); those sets
 are not available, so these generators stand in for them.  This module is shared by the
 oracle side and the CUDA side as *input only*: it holds none of the structure-function
-arithmetic, and every random number is drawn here, on the host, from numpy's PCG64.
+arithmetic.  Random numbers are drawn here, on the host from numpy's PCG64, except in the
+``*_torch`` generators, which draw them with torch's seeded generator on the device that
+renders the stack (for stacks too large to render on the host).
 
 Two families:
 
@@ -73,6 +75,61 @@ def ou_stack(H: int, W: int, N: int, D0: float, spectrum, sigma: float, seed: in
             field = field + sigma * rng.standard_normal((H, W))
         out[t] = field.astype(dtype)
     return out
+
+
+def ou_stack_torch(H: int, W: int, N: int, D0, spectrum, sigma: float, seed: int,
+                   device="cuda"):
+    """The law of :func:`ou_stack`, drawn with torch's generator and rendered on ``device``
+    (a CUDA device for stacks too large to render on the host in reasonable time, e.g.
+    1024x1024x4096 float32 = 17 GB).  Returns a float32 torch tensor [N, H, W].
+
+    Same recursion: G(k, 0) ~ CN(0, S); G(k, t+1) = e^{-Gamma} G(k, t) +
+    sqrt(S (1 - e^{-2 Gamma})) xi_t, E|xi|^2 = 1; frame = sqrt(2) Re(IDFT_ortho(G_t)) +
+    N(0, sigma^2).  Modes are carried in complex64 and the inverse transform is torch's
+    (an input generator only; it is not part of the structure-function path).  D0 may be a
+    float or a callable ``numpy_rng -> float`` (drawn from PCG64 seeded by ``seed``).
+    """
+    import torch
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), 0x0A2])))
+    if callable(D0):
+        D0 = float(D0(rng))
+    q = q_magnitude(H, W)
+    S = np.asarray(spectrum(q), dtype=np.float64)
+    gamma = D0 * q ** 2
+    decay = torch.from_numpy(np.exp(-gamma).astype(np.float32)).to(device)
+    drive = torch.from_numpy(np.sqrt(S * (1.0 - np.exp(-2.0 * gamma))).astype(np.float32)).to(device)
+    amp = torch.from_numpy(np.sqrt(S).astype(np.float32)).to(device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 7919 + 17)
+
+    def cnormal():
+        z = torch.randn((2, H, W), generator=g, device=device, dtype=torch.float32) / math.sqrt(2.0)
+        return torch.complex(z[0], z[1])
+
+    G = amp * cnormal()
+    out = torch.empty((N, H, W), dtype=torch.float32, device=device)
+    for t in range(N):
+        if t > 0:
+            G = decay * G + drive * cnormal()
+        field = math.sqrt(2.0) * torch.fft.ifft2(G, norm="ortho").real
+        if sigma > 0:
+            field = field + sigma * torch.randn((H, W), generator=g, device=device, dtype=torch.float32)
+        out[t] = field
+    return out
+
+
+def log_uniform_d0(lo: float = 0.01, hi: float = 1.0):
+    """A D0 drawn log-uniformly in [lo, hi] from the generator's own numpy stream."""
+    return lambda rng: float(math.exp(rng.uniform(math.log(lo), math.log(hi))))
+
+
+def ou_precision_sweep_1024x1024x4096(seed: int = 0, N: int = 4096, H: int = 1024, W: int = 1024,
+                                      device="cuda"):
+    """The precision-sweep stack: 1024x1024 float32, N = 4096, OU Fourier modes with
+    S(q) = 1 / max(q, 0.02)^2, D0 log-uniform in [0.01, 1] (once per stack), no pixel noise;
+    rendered on ``device`` (torch tensor)."""
+    return ou_stack_torch(H, W, N, log_uniform_d0(0.01, 1.0), power_law_spectrum(0.02), 0.0, seed,
+                          device=device)
 
 
 def ou_params(D0: float, spectrum_width: float):

@@ -38,3 +38,16 @@ def plane_to_storage(F, H, W):
     """[N, H, W/2+1] complex -> spectrum storage [N, n_q]."""
     ky, kx = ddm.spectrum_index_map(H, W)
     return np.ascontiguousarray(F[:, ky, kx])
+
+
+def oracle_columns_of_device_stack(frames_dev, cols, chunk=128):
+    """The oracle's spectrum F [N, H, len(cols)] (complex128) of a float32 stack that lives
+    on the device: frames are copied to the host a chunk at a time (a 1024x1024x4096 stack
+    is 17 GB) and transformed by the oracle's own DFT restricted to the columns ``cols``."""
+    import oracle
+    N = frames_dev.shape[0]
+    parts = []
+    for t0 in range(0, N, chunk):
+        host = frames_dev[t0:t0 + chunk].cpu().numpy()
+        parts.append(oracle.dft2(host, cols))
+    return np.concatenate(parts, axis=0)

@@ -12,7 +12,7 @@ from conftest import cuda_available
 
 def test_library_is_in_tree_and_loads():
     L = ddm.lib()
-    assert L.ddm_abi_version() == 4
+    assert L.ddm_abi_version() == 5
     assert ddm.LIB_PATH.endswith("paper_2012_05695_b300/_lib/libddm_b300.so")
 
 
@@ -159,3 +159,33 @@ def test_fp64_tier_limits(H, W, N, kmax, status):
     h = ctypes.c_void_p(123)
     assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == status
     assert not h.value
+
+
+@pytest.mark.parametrize("H,W,kx0,kx1,extra,status", [
+    (64, 64, 8, 32, {}, B.DDM_ERR_INVALID_ARG),           # not whole blocks of 16 columns
+    (64, 64, 0, 48, {}, B.DDM_ERR_INVALID_ARG),           # beyond W/2
+    (64, 64, 16, 16, {}, B.DDM_ERR_INVALID_ARG),          # empty
+    (64, 64, -16, 16, {}, B.DDM_ERR_INVALID_ARG),
+    (64, 64, 16, 32, {"kmax": 7}, B.DDM_ERR_UNSUPPORTED),
+    (64, 64, 16, 32, {"q_begin": 0, "q_end": 64}, B.DDM_ERR_UNSUPPORTED),
+    (64, 64, 16, 32, {"precision": B.DDM_PREC_FP64}, B.DDM_ERR_UNSUPPORTED),
+    (64, 64, 16, 32, {"spatial_path": B.DDM_SPATIAL_FUSED}, B.DDM_ERR_UNSUPPORTED),
+    (96, 96, 0, 16, {}, B.DDM_ERR_UNSUPPORTED),           # the power-of-two column pass only
+    (64, 16, 0, 8, {}, B.DDM_ERR_INVALID_ARG),
+])
+def test_kx_column_range_validation(H, W, kx0, kx1, extra, status):
+    d = _desc(H, W, 100)
+    d.kx_begin, d.kx_end = kx0, kx1
+    for k, v in extra.items():
+        setattr(d, k, v)
+    h = ctypes.c_void_p(123)
+    assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == status
+    assert not h.value
+
+
+@pytest.mark.skipif(cuda_available(), reason="checks the no-device path")
+def test_kx_column_range_passes_validation():
+    d = _desc(64, 512, 100)
+    d.kx_begin, d.kx_end = 96, 256
+    h = ctypes.c_void_p(123)
+    assert ddm.lib().ddm_plan_create(ctypes.byref(h), ctypes.byref(d)) == B.DDM_ERR_CUDA

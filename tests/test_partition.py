@@ -95,3 +95,61 @@ def test_two_rank_gloo_allreduce_of_radial_sums(tmp_path):
     Dr_ref, _ = oracle.radial_average(D_full, NB)
     for r in range(world):
         np.testing.assert_allclose(np.load(tmp_path / f"dr{r}.npy"), Dr_ref, rtol=1e-12, atol=1e-12)
+
+
+def test_kx_ranges_cover_the_columns_in_aligned_blocks():
+    from paper_2012_05695_b300 import partition
+    for W, parts in [(32, 1), (512, 2), (512, 3), (512, 8), (1024, 7), (256, 8)]:
+        r = partition.kx_ranges(W, parts)
+        assert len(r) == parts and r[0][0] == 0 and r[-1][1] == W // 2
+        for (a, b), (c, _) in zip(r, r[1:]):
+            assert b == c
+        for a, b in r:
+            assert a % 16 == 0 and b % 16 == 0 and b > a
+        sizes = [b - a for a, b in r]
+        assert max(sizes) - min(sizes) <= 16
+    with pytest.raises(ValueError):
+        partition.kx_ranges(256, 9)      # 8 blocks of 16 columns
+    with pytest.raises(ValueError):
+        partition.kx_ranges(40, 1)       # W/2 = 20 is not whole blocks
+
+
+def _kx_rank_main(rank, world, port, out_dir):
+    """One rank of a stack split by kx columns: the oracle D of its columns only (plus the
+    kx = W/2 column on the rank whose range starts at 0), its radial sums, the gloo sum."""
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        Hk, Wk, Nk = 16, 64, 24
+        frames = synth.ou_stack(Hk, Wk, Nk, 0.5, synth.gaussian_spectrum(0.3), 0.05, seed=4)
+        kx0, kx1 = partition.kx_ranges(Wk, world)[rank]
+        cols = list(range(kx0, kx1)) + ([Wk // 2] if kx0 == 0 else [])
+        D = oracle.sf_direct(oracle.dft2(frames, cols))          # [H, len(cols), N]
+        bins = oracle.radial_bins(Hk, Wk, NB)
+        s = np.zeros((NB, Nk))
+        c = np.zeros(NB, np.int64)
+        for j, kx in enumerate(cols):
+            w = 1 if kx in (0, Wk // 2) else 2
+            for ky in range(Hk):
+                s[bins[ky, kx]] += w * D[ky, j]
+                c[bins[ky, kx]] += w
+        Dr = partition.allreduce_radial(torch.from_numpy(s), torch.from_numpy(c))
+        np.save(os.path.join(out_dir, f"kxdr{rank}.npy"), Dr.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_gloo_kx_column_split(tmp_path):
+    """The kx-column split's host logic on two gloo ranks: each rank's columns (the ranges
+    of kx_ranges, the kx = W/2 column with the first) give radial sums whose all-reduce is
+    the oracle's whole-plane radial average."""
+    import torch.multiprocessing as mp
+    world = 2
+    mp.spawn(_kx_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    frames = synth.ou_stack(16, 64, 24, 0.5, synth.gaussian_spectrum(0.3), 0.05, seed=4)
+    Dr_ref, _ = oracle.radial_average(oracle.sf_direct(oracle.dft2(frames)), NB)
+    for r in range(world):
+        np.testing.assert_allclose(np.load(tmp_path / f"kxdr{r}.npy"), Dr_ref, rtol=1e-12, atol=1e-12)
