@@ -212,6 +212,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo), or None."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def oracle_sample(frames, cols, nthreads):
     """Run the FP64 oracle on kx columns `cols` (every ky, every lag); returns (seconds, D, s_q)."""
     import oracle
@@ -267,89 +278,63 @@ def time_mlp_forward(mlp, x, sizes, reps=50):
     return res
 
 
-def head_targets(params, p8):
-    """Fit labels (A, tau, beta, B) -> the seed network's regression targets
-    (ln(A/p8), ln tau, beta, B/A): the inverse of the head A = p8 e^{o0}, tau = e^{o1},
-    B = A o3 that include/ddm.h documents (beta is regressed through its sigmoid)."""
-    A, tau, beta, B = (params[:, k] for k in range(4))
-    with np.errstate(divide="ignore", invalid="ignore"):
-        return np.stack([np.log(A / p8), np.log(tau), beta, B / A], axis=1)
+from paper_2012_05695_b300.seed_training import head_targets  # noqa: E402  (re-exported)
 
 
-def compare_fits(ddm, plan, Dr, stream):
-    """Train the seed network on synthetic curves (library kernels), then fit the stack's
-    radial curves with plain LM and with the MLP seed; times and iteration counts."""
+def compare_fits(ddm, plan, Dr, stream, n_train=200, n_held=20, n_keep=256, steps=6000, batch=4096):
+    """The learned fit stage on structure functions this pipeline computes: seeded
+    polydisperse blob stacks (512x512x1024, log-normal D0, median 0.2, sigma_ln 0.5; seeds
+    1000.. train, 2000.. held out) go through ddm_structure_function and the radial
+    average; the curves inside the inscribed Nyquist circle (the first n_keep of 362 bins)
+    are labelled by LM and train the seed network with the library's kernels; then plain LM
+    and LM seeded by the network fit the held-out stacks' curves and this run's own bench
+    stack (its 362 radial curves)."""
     import torch
     import synth
-    B_ = ddm._binding
-    n_train, batch, steps = 65536, 4096, 6000
-    # decay times and noise floors of the kind a blob stack's radial curves span where the
-    # curve is identifiable from 1023 lags: tau from 0.5 to 5000 frames, B/A from 1e-3 to 10.
-    # The network learns to predict where LM ends (amortised fit): labels are the LM optima
-    # of the training curves (heuristic seed), kept where they lie near the generating
-    # parameters.  Curves outside that range (the lowest and highest |q| bins) are left to the
-    # heuristic seed: DDM_FIT_MLP_LM starts LM from whichever seed costs less.
-    Dtr, gen = synth.stretched_exp_curves(n_train, N_FRAMES, 10, log10_tau=(-0.3, 3.7),
-                                          log10_b_over_a=(-3.0, 1.0))
-    tplan = ddm.Plan(8, 8, N_FRAMES, dtype="f32")
-    Dtr_dev = torch.from_numpy(Dtr.reshape(-1)).cuda()
-    x = torch.empty(n_train * 64, device="cuda")
-    p8 = torch.empty(n_train, device="cuda")
-    tplan.fit_features(Dtr_dev, n_train, x, p8)
-    lab = torch.empty(n_train * 4, device="cuda")
-    lflags = torch.empty(n_train, dtype=torch.int32, device="cuda")
-    tplan.fit(Dtr_dev, n_train, B_.DDM_FIT_LM, None, lab, None, None, lflags)
-    torch.cuda.synchronize()
-    labels = lab.cpu().numpy().reshape(n_train, 4).astype(np.float64)
-    p8h = p8.cpu().numpy().astype(np.float64)
-    good = ((lflags.cpu().numpy() & B_.DDM_FIT_CONVERGED) > 0) & np.all(np.isfinite(labels), axis=1) \
-        & (labels[:, 0] > 0) & (labels[:, 1] > 0)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        good &= (np.abs(np.log(labels[:, 1]) - np.log(gen[:, 1])) < 0.7) & (np.abs(labels[:, 2] - gen[:, 2]) < 0.3)
-    tg = head_targets(labels, p8h)
-    tg[~good] = 0.0
-    good &= np.all(np.isfinite(tg), axis=1) & (np.abs(tg) < 50).all(axis=1)
-    keep = np.nonzero(good)[0]
-    n_keep = (keep.size // batch) * batch
-    keep = keep[:n_keep]
-    idx = torch.from_numpy(keep).cuda()
-    x = x.view(n_train, 64)[idx].reshape(-1).contiguous()
-    tgt = torch.from_numpy(tg[keep].astype(np.float32).reshape(-1)).cuda()
-    n_train = n_keep
+    from paper_2012_05695_b300 import seed_training as st
+    dev = Dr.device
+    D = torch.empty(plan.d_rows * N_FRAMES, dtype=torch.float32, device=dev)
+    Dr_s = torch.empty(N_BINS * N_FRAMES, dtype=torch.float32, device=dev)
+
+    def curves(seeds):
+        cs = []
+        for sd in seeds:
+            fr = synth.polydisperse_blobs_512x512x1024(sd, N=N_FRAMES, H=H, W=W, device=dev)
+            cs.append(st.stack_curves(plan, fr, n_keep, stream, D, Dr_s))
+            del fr
+        return torch.cat(cs, dim=0).contiguous()
+
+    t0 = time.perf_counter()
+    train_curves = curves(range(1000, 1000 + n_train))
+    held = curves(range(2000, 2000 + n_held))
+    t_data = time.perf_counter() - t0
+    x, tgt, keep = st.labelled_features(plan, train_curves, stream)
     mlp = ddm.MLP(batch)
     mlp.set_weights(synth.mlp_init(0))
-    loss = torch.empty(1, device="cuda")
-    rng = np.random.Generator(np.random.PCG64(0))
     t0 = time.perf_counter()
-    for k in range(steps):
-        b = int(rng.integers(0, n_train // batch))
-        mlp.train_step(x[b * batch * 64:(b + 1) * batch * 64], tgt[b * batch * 4:(b + 1) * batch * 4],
-                       batch, 2e-3 if k < 4500 else 5e-4, loss)
+    loss0, loss1 = st.train(mlp, x, tgt, steps, batch, seed=0, stream=stream)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    out = {"train_steps": steps, "train_batch": batch, "train_s": train_s,
-           "train_loss": float(loss.item()), "curves": N_BINS,
-           "mlp_forward": time_mlp_forward(mlp, x, (N_BINS, batch))}
-    for name, mode, net in (("lm", B_.DDM_FIT_LM, None), ("mlp_lm", B_.DDM_FIT_MLP_LM, mlp)):
-        prm = torch.empty(N_BINS * 4, device="cuda")
-        cst = torch.empty(N_BINS, device="cuda")
-        its = torch.empty(N_BINS, dtype=torch.int32, device="cuda")
-        flg = torch.empty(N_BINS, dtype=torch.int32, device="cuda")
+    out = {"training_data": (f"{n_train} polydisperse blob stacks {H}x{W}x{N_FRAMES} (seeds 1000..), "
+                             f"{n_keep} radial curves each, labelled by LM"),
+           "training_curves": int(keep.size), "labelled": int(keep.sum()),
+           "data_s": t_data, "train_steps": steps, "train_batch": batch, "train_s": train_s,
+           "train_loss_first": loss0, "train_loss": loss1,
+           "held_out": dict(st.compare(plan, held, mlp, stream), stacks=n_held),
+           "bench_stack": st.compare(plan, Dr.view(N_BINS, N_FRAMES), mlp, stream),
+           "mlp_forward": time_mlp_forward(mlp, x.view(-1), (N_BINS, batch))}
+    for name, mode, net in (("lm", ddm._binding.DDM_FIT_LM, None), ("mlp_lm", ddm._binding.DDM_FIT_MLP_LM, mlp)):
+        prm = torch.empty(N_BINS * 4, device=dev)
         for _ in range(3):
-            plan.fit(Dr, N_BINS, mode, net, prm, cst, its, flg, stream)
+            plan.fit(Dr, N_BINS, mode, net, prm, None, None, None, stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(20):
-            plan.fit(Dr, N_BINS, mode, net, prm, cst, its, flg, stream)
+            plan.fit(Dr, N_BINS, mode, net, prm, None, None, None, stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        f = flg.cpu().numpy()
-        out[name] = {"ms": e0.elapsed_time(e1) / 20, "iters_mean": float(its.cpu().numpy().mean()),
-                     "iters_max": int(its.cpu().numpy().max()),
-                     "converged": float(np.mean((f & B_.DDM_FIT_CONVERGED) > 0)),
-                     "mlp_accepted": float(np.mean((f & B_.DDM_FIT_MLP_ACCEPTED) > 0)),
-                     "seed_heuristic": float(np.mean((f & B_.DDM_FIT_SEED_HEURISTIC) > 0)),
-                     "cost_sum": float(cst.cpu().numpy().astype(np.float64).sum())}
+        out["bench_stack"][name + "_ms"] = e0.elapsed_time(e1) / 20
+    mlp.close()
     return out
 
 
@@ -562,7 +547,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "H": H, "W": W, "N": N_FRAMES, "n_bins": N_BINS},
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -724,51 +709,84 @@ def run_ours(args):
     # buffers, the next stack's upload on a copy stream under the current stack's compute;
     # every step still uploads its own frames and reads back its own results.
     e2e = None
+    e2e_radial = None
     if not args.no_e2e:
         host = torch.from_numpy(frames_np).pin_memory()
+        D_host = torch.empty(plan.d_rows * N_FRAMES, dtype=torch.float32).pin_memory()
         Dr_host = torch.empty(N_BINS * N_FRAMES, dtype=torch.float32).pin_memory()
         params_host = torch.empty(N_BINS * 4, dtype=torch.float32).pin_memory()
         bufs = [torch.empty_like(frames), torch.empty_like(frames)]
-        copy_stream = torch.cuda.Stream(device=dev)
+        Dbufs = [D, torch.empty_like(D)]
+        up_stream = torch.cuda.Stream(device=dev)
+        down_stream = torch.cuda.Stream(device=dev)
         ready = [torch.cuda.Event(), torch.cuda.Event()]
         free = [torch.cuda.Event(), torch.cuda.Event()]
+        computed = [torch.cuda.Event(), torch.cuda.Event()]
+        read = [torch.cuda.Event(), torch.cuda.Event()]
 
-        def e2e_run(k_steps, start_ev=None):
+        def e2e_run(k_steps, full_D, start_ev=None):
+            """Per step: upload the stack from pinned host memory, the structure function,
+            then either D itself back to pinned host memory (full_D) or the radial average
+            and the fit of its curves, whose Dr and parameters come back.  Uploads run on
+            their own stream under the previous stack's compute, D read-backs on another."""
             if start_ev is not None:
-                copy_stream.wait_event(start_ev)
+                up_stream.wait_event(start_ev)
             for k in range(k_steps):
                 b = k % 2
-                with torch.cuda.stream(copy_stream):
+                with torch.cuda.stream(up_stream):
                     if k >= 2:
-                        copy_stream.wait_event(free[b])   # stack k-2 has left this buffer
+                        up_stream.wait_event(free[b])     # stack k-2 has left this buffer
                     bufs[b].copy_(host, non_blocking=True)
-                    ready[b].record(copy_stream)
+                    ready[b].record(up_stream)
                 stream.wait_event(ready[b])
-                plan.structure_function(bufs[b], D, stream)
+                if full_D and k >= 2:
+                    stream.wait_event(read[b])            # D of stack k-2 has been read back
+                plan.structure_function(bufs[b], Dbufs[b], stream)
                 free[b].record(stream)
-                plan.azimuthal_average(D, Dr, counts, stream)
-                plan.fit(Dr, N_BINS, ddm._binding.DDM_FIT_LM, None, fit_params, None, None, None, stream)
-                Dr_host.copy_(Dr, non_blocking=True)
-                params_host.copy_(fit_params, non_blocking=True)
+                if full_D:
+                    computed[b].record(stream)
+                    with torch.cuda.stream(down_stream):
+                        down_stream.wait_event(computed[b])
+                        D_host.copy_(Dbufs[b], non_blocking=True)
+                        read[b].record(down_stream)
+                else:
+                    plan.azimuthal_average(Dbufs[b], Dr, counts, stream)
+                    plan.fit(Dr, N_BINS, ddm._binding.DDM_FIT_LM, None, fit_params, None, None, None, stream)
+                    Dr_host.copy_(Dr, non_blocking=True)
+                    params_host.copy_(fit_params, non_blocking=True)
+            if full_D:
+                stream.wait_stream(down_stream)
 
-        e2e_run(max(2, args.warmup))
-        torch.cuda.synchronize()
-        k_e2e = max(3, min(args.steps, 20))
-        if dist:
-            dist.barrier()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        e2e_run(k_e2e, s0)
-        s1.record(stream)
-        torch.cuda.synchronize()
-        e_ms = max_over_ranks(s0.elapsed_time(s1), dist, dev)
+        def e2e_time(full_D):
+            e2e_run(max(2, args.warmup), full_D)
+            torch.cuda.synchronize()
+            k_e2e = max(3, min(args.steps, 20))
+            if dist:
+                dist.barrier()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            e2e_run(k_e2e, full_D, s0)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            return max_over_ranks(s0.elapsed_time(s1), dist, dev), k_e2e
+
+        h2d = int(host.numel() * host.element_size())
+        e_ms, k_e2e = e2e_time(True)
         e2e = {"value": job_throughput(n_gpus, N_FRAMES, k_e2e, e_ms), "unit": "frames/s",
-               "h2d_bytes_per_step": int(host.numel() * host.element_size()),
-               "d2h_bytes_per_step": int(Dr_host.numel() * Dr_host.element_size()
-                                         + params_host.numel() * params_host.element_size()),
-               "h2d_effective_gbs": round(host.numel() * host.element_size() * k_e2e / (e_ms / 1e3) / 1e9, 1),
-               "pipelined": "next stack's upload overlaps this stack's compute",
+               "returns": "the full D(q, lag) of every stack, to pinned host memory",
+               "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": int(D_host.numel() * D_host.element_size()),
+               "h2d_effective_gbs": round(h2d * k_e2e / (e_ms / 1e3) / 1e9, 1),
+               "pipelined": "next stack's upload and the previous stack's D read-back overlap this stack's compute",
                "steps": k_e2e}
+        e_ms, k_e2e = e2e_time(False)
+        e2e_radial = {"value": job_throughput(n_gpus, N_FRAMES, k_e2e, e_ms), "unit": "frames/s",
+                      "returns": "the radial average Dr and the LM fit parameters of every stack",
+                      "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": int(Dr_host.numel() * Dr_host.element_size()
+                                                + params_host.numel() * params_host.element_size()),
+                      "steps": k_e2e}
+        del Dbufs, bufs
 
     # ---- precision tiers on the same stack: the FP32+FP64-fixup temporal stage
     tiers = {"fp32": {"temporal_ms": tm_ms}}
@@ -813,6 +831,7 @@ def run_ours(args):
         lp = ddm.Plan(H, W, N_FRAMES, dtype="u16", n_bins=N_BINS, kmax=args.kmax)
         spec_c = torch.empty(2 * N_FRAMES * lp.n_q, dtype=torch.float32, device=dev)
         D_c = torch.empty(lp.n_q * N_FRAMES, dtype=torch.float32, device=dev)
+        Dr_c = torch.empty(N_BINS * N_FRAMES, dtype=torch.float32, device=dev)   # not the stack's Dr
         lev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(10)]
         for k in range(13):
             e = lev[k - 3] if k >= 3 else None
@@ -824,7 +843,7 @@ def run_ours(args):
             lp.temporal_sf(spec_c, D_c, stream)
             if e:
                 e[2].record(stream)
-            lp.azimuthal_average(D_c, Dr, counts, stream)
+            lp.azimuthal_average(D_c, Dr_c, None, stream)
             if e:
                 e[3].record(stream)
         torch.cuda.synchronize()
@@ -832,7 +851,7 @@ def run_ours(args):
         low_q = {"kmax": args.kmax, "n_q": lp.n_q, "kept_fraction": lp.n_q / N_Q,
                  "stages_ms": {"spatial_fft": ls[0], "temporal_sf": ls[1], "azimuthal_average": ls[2]},
                  "frames_per_s": N_FRAMES / (sum(ls) / 1e3)}
-        del spec_c, D_c, lp
+        del spec_c, D_c, Dr_c, lp
 
     # ---- a camera whose sides are not powers of two (Bluestein spatial transforms) and a
     # long stack: 600 x 800 x 3000 uint16.  Timing only (kernel times do not depend on the
@@ -867,10 +886,15 @@ def run_ours(args):
         t_s, D_or, s_q = oracle_sample(frames_np, cols, cores)
         q_sample = H * len(cols)
         cpu_value = N_FRAMES / (t_s * N_Q / q_sample)
+        t_1, _, _ = oracle_sample(frames_np, cols[:1], 1)          # the same oracle on one core
         cpu = {"value": cpu_value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+               "cpu_model": cpu_model(),
                "sample": f"{len(cols)} kx columns x {H} ky x {N_FRAMES} frames x all lags "
                          f"({q_sample} of {N_Q} wave vectors), {t_s:.1f} s; frames/s extrapolated "
-                         f"linearly in the q count"}
+                         f"linearly in the q count",
+               "one_core": {"value": N_FRAMES / (t_1 * N_Q / H), "unit": "frames/s", "cores": 1,
+                            "sample": f"1 kx column x {H} ky x {N_FRAMES} frames x all lags, {t_1:.1f} s; "
+                                      f"extrapolated linearly in the q count"}}
         plan.structure_function(frames, D, stream)
         torch.cuda.synchronize()
         Dg = D.view(H, W // 2 + 1, N_FRAMES)[:, cols, :].cpu().numpy()
@@ -943,6 +967,8 @@ def run_ours(args):
         out["fit"] = fit_cmp
     if e2e:
         out["e2e"] = e2e
+    if e2e_radial:
+        out["e2e_radial_fit"] = e2e_radial
     if cpu:
         out["cpu_baseline"] = cpu
     if rank == 0:

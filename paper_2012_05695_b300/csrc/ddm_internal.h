@@ -106,22 +106,21 @@ struct SpecOut {
     int64_t n_qc = 0;
     int H = 0, Wh = 0, kx0 = 0, nk = 0;
 #ifdef __CUDACC__
-    __device__ __forceinline__ bool redirected() const { return blk != nullptr || col != nullptr; }
-    __device__ __forceinline__ void put(float2* frame, int t, int64_t q, float2 v) const {
-        if (col) {
-            const int64_t main = (int64_t)H * Wh;
-            int64_t cs;
-            if (q < main) {
-                const int64_t ky = q / Wh, kx = q - ky * Wh;
-                if (kx < kx0 || kx >= kx0 + nk) return;
-                cs = ky * nk + (kx - kx0);
-            } else {
-                if (kx0 != 0) return;
-                cs = (int64_t)H * nk + (q - main);
-            }
-            col[(int64_t)t * n_qc + cs] = v;
-            return;
+    // the kx-column range store (its own kernel instances: the check stays out of the others)
+    __device__ __forceinline__ void put_col(int t, int64_t q, float2 v) const {
+        const int64_t main = (int64_t)H * Wh;
+        int64_t cs;
+        if (q < main) {
+            const int64_t ky = q / Wh, kx = q - ky * Wh;
+            if (kx < kx0 || kx >= kx0 + nk) return;
+            cs = ky * nk + (kx - kx0);
+        } else {
+            if (kx0 != 0) return;
+            cs = (int64_t)H * nk + (q - main);
         }
+        col[(int64_t)t * n_qc + cs] = v;
+    }
+    __device__ __forceinline__ void put(float2* frame, int t, int64_t q, float2 v) const {
         if (!blk) {
             frame[q] = v;
             return;

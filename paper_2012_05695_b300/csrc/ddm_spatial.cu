@@ -107,7 +107,9 @@ row_r2c_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
 }
 
 // grid: (Wh / QC, N); block: QC * T threads.  H = L points per column, QC columns.
-template <int H, int QC>
+// COLRANGE: a kx-column range plan, whose output goes to the range's own store (SpecOut
+// put_col) and whose grid starts at column block bx0.
+template <int H, int QC, bool COLRANGE>
 __global__ void __launch_bounds__(QC * FftShape<H>::T, (QC * FftShape<H>::T) >= 512 ? 1 : (QC * FftShape<H>::T) >= 256 ? 2 : 4)
 col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
                const float2* __restrict__ tw_g, SpecOut out, int bx0) {
@@ -123,7 +125,7 @@ col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
     }
     const int ql = tid % QC;
     const int i = tid / QC;
-    const int bx = blockIdx.x + bx0;          // column block (a kx-column range starts at bx0)
+    const int bx = COLRANGE ? (int)blockIdx.x + bx0 : (int)blockIdx.x;   // column block
     const int kx = bx * QC + ql;
     const int t = blockIdx.y;
     float2* base = spec + (size_t)t * frame_stride;
@@ -139,7 +141,13 @@ col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
 
     base = opaque_ptr(base);
     if (bx != 0) {
-        if (!out.redirected()) {
+        if constexpr (COLRANGE) {
+            // row ky = i + T u of column kx in the range's store [ky][kx - kx0]
+            float2* cb = out.col + (size_t)t * (size_t)out.n_qc + (size_t)(kx - out.kx0);
+            const uint32_t c0 = (uint32_t)(i * out.nk), cstep = (uint32_t)(T * out.nk);
+#pragma unroll
+            for (int u = 0; u < P; ++u) cb[c0 + (uint32_t)u * cstep] = v[u];
+        } else if (!out.blk) {
 #pragma unroll
             for (int u = 0; u < P; ++u) base[off0 + (uint32_t)u * step] = v[u];
         } else {
@@ -155,14 +163,18 @@ col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
 #pragma unroll
     for (int u = 0; u < P; ++u) {
         const int ky = i + T * u;
+        auto put = [&](int64_t q, float2 val) {
+            if constexpr (COLRANGE) out.put_col(t, q, val);
+            else out.put(base, t, q, val);
+        };
         if (ql != 0) {
-            out.put(base, t, (int64_t)ky * Wh + kx, v[u]);
+            put((int64_t)ky * Wh + kx, v[u]);
         } else {
             const float2 c = v[u];
             const float2 cr = xs[addr((H - ky) & (H - 1))];
             // F0 = (C[ky] + conj C[-ky]) / 2 ; FN = (C[ky] - conj C[-ky]) / (2i)
-            out.put(base, t, (int64_t)ky * Wh, make_float2(0.5f * (c.x + cr.x), 0.5f * (c.y - cr.y)));
-            out.put(base, t, (int64_t)H * Wh + ky, make_float2(0.5f * (c.y + cr.y), 0.5f * (cr.x - c.x)));
+            put((int64_t)ky * Wh, make_float2(0.5f * (c.x + cr.x), 0.5f * (c.y - cr.y)));
+            put((int64_t)H * Wh + ky, make_float2(0.5f * (c.y + cr.y), 0.5f * (cr.x - c.x)));
         }
     }
 }
@@ -263,7 +275,7 @@ cudaError_t launch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecO
         const int nblk = p->nk > 0 ? p->nk / QC : Wh / QC, bx0 = p->nk > 0 ? p->kx0 / QC : 0;
         dim3 grid(nblk, N);
         const size_t smem = sizeof(float2) * ((S::T > 1 ? H : 0) + (size_t)H * QC);
-        auto k = col_c2c_kernel<H, QC>;
+        auto k = p->nk > 0 ? col_c2c_kernel<H, QC, true> : col_c2c_kernel<H, QC, false>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<grid, QC * S::T, smem, s>>>(spec, Wh, frame_stride, p->tw_col, out, bx0);
         return cudaGetLastError();

@@ -206,6 +206,71 @@ def blob_stack(H: int, W: int, N: int, n_particles: int, sigma_px: float, D0, se
     return out
 
 
+def blob_stack_torch(H: int, W: int, N: int, n_particles: int, sigma_px: float, D0, seed: int,
+                     mean: float = 2000.0, amplitude: float = 1000.0, max_count: int = 4095,
+                     drift: float = 0.0, device="cuda", chunk: int = 32):
+    """The law of :func:`blob_stack` (Brownian Gaussian blobs on a periodic field, Poisson
+    counts clamped to ``max_count``, uint16), drawn with torch's seeded generator and rendered
+    on ``device``: the 200 training stacks of 512x512x1024 that the seed network learns from
+    take minutes each on the host and milliseconds here.  Returns a uint16 tensor [N, H, W].
+
+    Same model: start positions uniform on the field, steps N(0, 2 D0) px per axis per frame
+    (D0 a float or a per-particle array), periodic wrap; the expected frame is
+    bg + amplitude sum_p g(y - y_p) g(x - x_p) with g the Gaussian of ``sigma_px`` at the
+    minimum-image distance, cut at 4 sigma (rounded up to whole pixels), bg making the
+    mean ``mean``; ``drift`` multiplies frame t by 1 + drift t / (N - 1); Poisson counts.
+    """
+    import torch
+    P = int(n_particles)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 1000003 + 0xB10B)
+    d0 = torch.as_tensor(np.broadcast_to(np.asarray(D0, dtype=np.float64), (P,)).copy(), device=device)
+    dims = torch.tensor([H, W], dtype=torch.float64, device=device)
+    start = torch.rand((P, 2), generator=g, device=device, dtype=torch.float64) * dims
+    reach = int(math.ceil(4.0 * sigma_px))
+    bg = mean - P * amplitude * (2.0 * math.pi * sigma_px ** 2) / float(H * W)
+    ys = torch.arange(H, device=device, dtype=torch.float64)
+    xs = torch.arange(W, device=device, dtype=torch.float64)
+    out = torch.empty((N, H, W), dtype=torch.int16, device=device)
+    pos = start.clone()
+    step_sd = torch.sqrt(2.0 * d0)[:, None]
+
+    def profile(centres, coords, L):
+        # centres are wrapped into [0, L) in float64 (trajectories wander far); the
+        # minimum-image distance and the Gaussian in float32 (|d| < L: ~1e-5 px of rounding)
+        c32 = centres.float()
+        d = torch.remainder(coords.float()[None, None, :] - c32[:, :, None] + L / 2.0, float(L)) - L / 2.0
+        v = torch.exp(-(d * d) * (1.0 / (2.0 * sigma_px ** 2)))
+        return torch.where(d.abs() <= reach, v, torch.zeros_like(v))
+
+    for t0 in range(0, N, chunk):
+        n = min(chunk, N - t0)
+        steps = torch.randn((n, P, 2), generator=g, device=device, dtype=torch.float64) * step_sd
+        if t0 == 0:
+            steps[0] = 0.0
+        traj = torch.remainder(pos[None] + torch.cumsum(steps, dim=0), dims)
+        pos = traj[-1].clone()
+        gy = profile(traj[..., 0], ys, H)                 # [n, P, H]
+        gx = profile(traj[..., 1], xs, W)                 # [n, P, W]
+        lam = amplitude * torch.bmm(gy.transpose(1, 2), gx) + bg
+        if drift:
+            tt = torch.arange(t0, t0 + n, device=device, dtype=torch.float32)
+            lam = lam * (1.0 + drift * tt / max(N - 1, 1))[:, None, None]
+        lam = torch.clamp(lam, min=0.0)
+        counts = torch.clamp(torch.poisson(lam, generator=g), max=float(max_count))
+        out[t0:t0 + n] = counts.to(torch.int16)
+    return out.view(torch.uint16)
+
+
+def polydisperse_blobs_512x512x1024(seed: int, N: int = 1024, H: int = 512, W: int = 512,
+                                    device="cuda"):
+    """The learned-stage workload: 512x512 uint16, N = 1024, 3000 blobs (sigma 2 px) with
+    log-normal D0 (median 0.2 px^2/frame, sigma_ln 0.5), mean 2000, Poisson; rendered on
+    ``device`` (seeds 1000-1199 train the seed network, 2000-2019 are held out)."""
+    d0 = lognormal_d0(3000, 0.2, 0.5, seed)
+    return blob_stack_torch(H, W, N, 3000, 2.0, d0, seed, device=device)
+
+
 def lognormal_d0(n: int, median: float, sigma_ln: float, seed: int) -> np.ndarray:
     """Per-particle D0 drawn log-normally (polydisperse sample)."""
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), 0x1D0])))

@@ -266,6 +266,53 @@ def test_trained_mlp_seed_gains_over_heuristic_seed():
     assert np.median(ratio) <= 1.02
 
 
+def test_seed_network_trained_on_pipeline_curves_gains_on_held_out_stacks():
+    """The learned fit stage on this pipeline's own structure functions (the polydisperse
+    blob workload, reduced: 60 training and 8 held-out 512x512x1024 stacks, log-normal D0):
+    each stack through ddm_structure_function and the radial average, the identifiable
+    curves inside the inscribed Nyquist circle labelled by LM, the network trained with the
+    library's kernels.  On the held-out stacks' identifiable curves LM seeded by the network
+    needs fewer iterations than LM from the heuristic seed; where LM ran it reaches plain
+    LM's final cost, and curves that kept the network's parameters met the acceptance rule
+    (RMS residual <= 1e-2 A, checked here from the returned cost and A); over all their curves
+    it needs no more iterations.  The numbers are printed for the record."""
+    import torch
+    from paper_2012_05695_b300 import seed_training as st
+    H = W = 512
+    N, nb, n_keep = 1024, 362, 256
+    plan = ddm.Plan(H, W, N, dtype="u16", n_bins=nb)
+    D = torch.empty(plan.d_rows * N, device="cuda")
+    Dr = torch.empty(nb * N, device="cuda")
+
+    def curves(seeds):
+        return torch.cat([st.stack_curves(plan, synth.polydisperse_blobs_512x512x1024(sd), n_keep, None, D, Dr)
+                          for sd in seeds]).contiguous()
+
+    x, t, keep = st.labelled_features(plan, curves(range(1000, 1060)))
+    mlp = ddm.MLP(2048)
+    mlp.set_weights(synth.mlp_init(0))
+    loss0, loss1 = st.train(mlp, x, t, 3000, 2048, seed=0)
+    held = curves(range(2000, 2008))
+    res = st.compare(plan, held, mlp)
+    ident = res["identifiable"]
+    prm, cost, _, flags = st.fit_curves(plan, held, B.DDM_FIT_MLP_LM, mlp)
+    acc = (flags & B.DDM_FIT_MLP_ACCEPTED) > 0               # cost and A in the curve's units
+    assert np.all(np.sqrt(cost[acc] / 64) <= 1e-2 * np.abs(prm[acc, 0]) * (1 + 1e-5))
+    print(f"\nlabelled {int(keep.sum())} of {keep.size}; loss {loss0:.2f} -> {loss1:.4f}; "
+          f"held-out all: LM {res['lm_iters_mean']:.2f} vs MLP+LM {res['mlp_lm_iters_mean']:.2f} iters; "
+          f"identifiable ({ident['curves']}): {ident['lm_iters_mean']:.2f} vs {ident['mlp_lm_iters_mean']:.2f}, "
+          f"LM fallback {ident['lm_fallback_rate']:.3f}, LM-run cost within 1e-3 "
+          f"{ident['lm_run_cost_within_1e-3']:.4f}, accepted cost ratio median {ident['accepted_cost_ratio_median']}")
+    assert loss1 < 0.1 * loss0
+    assert ident["curves"] >= 300
+    assert ident["mlp_lm_iters_mean"] <= 0.92 * ident["lm_iters_mean"]
+    assert ident["lm_run_cost_within_1e-3"] >= 0.99
+    assert res["mlp_lm_iters_mean"] <= res["lm_iters_mean"]
+    assert res["mlp_lm_converged"] >= res["lm_converged"] - 0.01
+    mlp.close()
+    plan.close()
+
+
 def test_training_resumes_from_a_checkpoint_bitwise():
     """Checkpoint after 3 Adam steps, restore into a fresh network, take 4 more steps in each:
     the weights and the Adam state agree bit for bit with the uninterrupted run."""
