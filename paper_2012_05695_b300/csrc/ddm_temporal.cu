@@ -201,16 +201,15 @@ struct GShape {
     static constexpr int BOX_T = 256, NBOX = L / BOX_T;
     static constexpr int FIX_MAX = 8;
     // per-group buffers (bytes)
-    //   xs:  the tile [t][QG] (TMA layout), the padded transform exchange, the padded
-    //        |g|^2 / prefix-sum rows (floats)
-    //   ab:  |X_odd|^2, then Re C ([m][QG] floats), then the D rows [QG][DS]
+    //   xs:  the tile [t][QG] (TMA layout), then the padded transform exchange
+    //   ab:  |X_odd|^2 ([m][QG] floats), then the padded |g|^2 / prefix-sum rows, then the
+    //        D rows [QG][DS]
     //   red: row totals of the prefix sums; the mean's warp partials
     //   fix: warp partials of the FP64-fixup lags
+    // (the mean-removed sequence and Re C live in tensor memory)
     static constexpr size_t G_XS = (size_t)(L + L / T) * QG * sizeof(float2);
-    // (at T == P the odd-bin transform exchanges through ab, in halves: (L + L/T) * QG floats)
-    static constexpr bool SPLIT = (T == P);
     static constexpr size_t G_AB = cmax(cmax((size_t)L * QG * sizeof(float), (size_t)QG * DS * sizeof(float)),
-                                        SPLIT ? (size_t)(L + L / T) * QG * sizeof(float) : 0);
+                                        (size_t)(L + L / T) * QG * sizeof(float));
     static constexpr size_t G_RED = (size_t)P * QG * sizeof(float);
     static constexpr size_t G_FIX = (size_t)FIX_MAX * NWG * QG * sizeof(float);
     static constexpr size_t OFF_TW = 0;
@@ -226,9 +225,79 @@ struct GShape {
     static_assert(G_XS % 1024 == 0, "TMA destinations stay 1024-byte aligned");
     static_assert((DS % 4) == 0 && (G_AB % 16) == 0, "D rows must be 16-byte aligned for bulk copies");
     static_assert((size_t)NWG * QG * sizeof(float2) <= G_RED, "mean partials must fit");
-    static_assert((size_t)2 * L * QG * sizeof(float) >= (size_t)(L + L / T) * QG * sizeof(float),
-                  "padded prefix rows must fit the tile buffer");
+    static_assert(NG * GT == 512, "tensor-memory columns: four warps of 128 columns per lane quarter");
 };
+
+// ---- tensor memory as per-thread scratch of the grouped kernel.  Thread (warp w, lane l)
+// owns TMEM lane 32 (w mod 4) + l; the four warps that share a lane quarter own 128 columns
+// each (w / 4 selects them), so a 512-thread CTA uses all 512 columns.  Columns [0, 64) of
+// a thread hold its mean-removed time sequence (re, im of its P = 32 samples, in u order),
+// [64, 96) its 32 values of Re C.
+constexpr uint32_t kSeqTmemCols = 512;
+__device__ __forceinline__ void seq_tmem_alloc(uint32_t* slot) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(slot)), "r"(kSeqTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void seq_tmem_free(uint32_t tmem) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kSeqTmemCols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 32 consecutive columns of this thread's lane <- r (warp-wide: every lane stores its own)
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&r)[32]) {
+    __syncwarp();   // the warp-collective tcgen05 forms need a converged warp
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31, %32};"
+        ::"r"(taddr), "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7]),
+          "f"(r[8]), "f"(r[9]), "f"(r[10]), "f"(r[11]), "f"(r[12]), "f"(r[13]), "f"(r[14]), "f"(r[15]),
+          "f"(r[16]), "f"(r[17]), "f"(r[18]), "f"(r[19]), "f"(r[20]), "f"(r[21]), "f"(r[22]), "f"(r[23]),
+          "f"(r[24]), "f"(r[25]), "f"(r[26]), "f"(r[27]), "f"(r[28]), "f"(r[29]), "f"(r[30]), "f"(r[31])
+        : "memory");
+}
+// every tcgen05.st of this thread has completed (before the same columns are read back)
+__device__ __forceinline__ void tmem_st_wait() {
+    __syncwarp();
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// r <- 32 consecutive columns of this thread's lane; the wait is in the same statement
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32]) {
+    __syncwarp();
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];\n tcgen05.wait::ld.sync.aligned;"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]),
+          "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15]),
+          "=f"(r[16]), "=f"(r[17]), "=f"(r[18]), "=f"(r[19]), "=f"(r[20]), "=f"(r[21]), "=f"(r[22]), "=f"(r[23]),
+          "=f"(r[24]), "=f"(r[25]), "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31])
+        : "r"(taddr) : "memory");
+}
+// the 32 complex samples of a thread: v[0..15] in columns [0, 32), v[16..31] in [32, 64)
+__device__ __forceinline__ void tmem_st_seq(uint32_t taddr, const float2 (&v)[32]) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float r[32];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            r[2 * k] = v[16 * h + k].x;
+            r[2 * k + 1] = v[16 * h + k].y;
+        }
+        tmem_st32(taddr + 32u * h, r);
+    }
+}
+__device__ __forceinline__ void tmem_ld_seq(uint32_t taddr, float2 (&v)[32]) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float r[32];
+        tmem_ld32(taddr + 32u * h, r);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[16 * h + k] = make_float2(r[2 * k], r[2 * k + 1]);
+    }
+}
 
 template <int LOG2L, int NGROUPS, bool FIXUP>
 __global__ void __launch_bounds__(GShape<LOG2L, NGROUPS>::NT, 1)
@@ -236,17 +305,19 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
     using C = GShape<LOG2L, NGROUPS>;
     constexpr int L = C::L, P = C::P, T = C::T, QG = C::QG, NG = C::NG, GT = C::GT;
     constexpr int NWG = C::NWG, G = C::G, KT = C::KT, DS = C::DS, FM = C::FIX_MAX;
+    static_assert(P == 32, "one thread holds 32 samples (64 tensor-memory columns)");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t tile_bar[NG];
+    __shared__ uint32_t tmem_slot;
 
     const int tid = threadIdx.x;
+    const int warp = tid >> 5;
     const int grp = tid / GT, tg = tid % GT;
     const int bar_id = 1 + grp;          // named barrier of this group (0 is __syncthreads)
     float2* tw = reinterpret_cast<float2*>(smem_raw + C::OFF_TW);
     float2* tw2 = reinterpret_cast<float2*>(smem_raw + C::OFF_TW2);
     float* inv = reinterpret_cast<float*>(smem_raw + C::OFF_INV);
     float2* xs = reinterpret_cast<float2*>(smem_raw + C::OFF_XS + grp * C::G_XS);
-    float* xf = reinterpret_cast<float*>(xs);
     float* ab = reinterpret_cast<float*>(smem_raw + C::OFF_AB + grp * C::G_AB);
     float* red = reinterpret_cast<float*>(smem_raw + C::OFF_RED + grp * C::G_RED);
     float2* red2 = reinterpret_cast<float2*>(red);
@@ -257,12 +328,18 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) seq_tmem_alloc(&tmem_slot);
     for (int k = tid; k < L; k += C::NT) {
         tw[k] = a.tw[k];
         tw2[k] = a.tw2[k];
         inv[k] = a.inv[k];
     }
-    __syncthreads();   // the only CTA-wide barrier: from here on the groups run on their own
+    tc_fence_before();
+    __syncthreads();   // the only CTA-wide barrier before the end: the groups run on their own
+    tc_fence_after();
+    // this thread's tensor-memory columns: the sequence at t_seq, Re C at t_rec
+    const uint32_t t_seq = tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(warp >> 2) * 128u;
+    const uint32_t t_rec = t_seq + 64u;
 
     const int ql = tg % QG;
     const int i = tg / QG;
@@ -308,7 +385,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
     for (; gt < a.n_tiles; gt += gstride) {
         // (no L2 prefetch of later tiles: with several groups per SM their copies already
         // overlap the other groups' work, and prefetched lines measurably crowd the
-        // current tiles' reloads out of L2 at 512x512x1024: 1.45 ms with, 1.15 ms without)
+        // current tiles out of L2 at 512x512x1024)
         if (!wait()) { timed_out = true; break; }
 
         // ---- the time sequence in the cyclic layout, and its mean
@@ -338,68 +415,13 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
 #pragma unroll
         for (int u = 0; u < P; ++u)
             if (i + T * u < N) v[u] = csub(v[u], mean);
+        // the mean-removed sequence into tensor memory: the even-bin transform and the power
+        // sums take it from there, so the tile is read from shared memory only this once
+        tmem_st_seq(t_seq, v);
 
-        // ---- odd bins: L-point DFT of g(t) e^{-i pi t / L}; |.|^2 parked in ab
-#pragma unroll
-        for (int u = 0; u < P; ++u) {
-            v[u] = cmul(v[u], tw2[i + T * u]);
-            if ((u & 7) == 7) hoist_fence();
-        }
-        if constexpr (C::SPLIT) {
-            fft_cyclic_split<L, false>(v, i, ab, xaddr, tw, sync);   // the tile stays in xs
-        } else {
-            fft_cyclic<L, false>(v, i, xs, xaddr, tw, sync);
-        }
-#pragma unroll
-        for (int u = 0; u < P; ++u) ab[(i + T * u) * QG + ql] = cabs2(v[u]);
-
-        // ---- even bins: L-point DFT of g (still in xs at T == P; else the tile again, from L2)
-        if constexpr (!C::SPLIT) {
-            issue(gt);
-            if (!wait()) { timed_out = true; break; }
-        }
-#pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int t = i + T * u;
-            v[u] = (t < N) ? csub(xs[t * QG + ql], mean) : make_float2(0.f, 0.f);
-        }
-        sync();   // tile read: the exchange overwrites it
-        fft_cyclic<L, false>(v, i, xs, xaddr, tw, sync);
-#pragma unroll
-        for (int u = 0; u < P; ++u) {
-            v[u] = make_float2(cabs2(v[u]), ab[(i + T * u) * QG + ql]);
-            if ((u & 7) == 7) hoist_fence();
-        }
-
-        // ---- inverse transform of Z = |X_even|^2 + i |X_odd|^2, then Re C(m) into ab
-        fft_cyclic<L, true>(v, i, xs, xaddr, tw, sync);
-#pragma unroll
-        for (int u = 0; u < P; ++u) xs[(i + T * u) * QG + ql] = v[u];
-        sync();
-        {
-            const float scale = 0.25f / (float)L;
-#pragma unroll
-            for (int u = 0; u < P; ++u) {
-                const int m = i + T * u;
-                const float2 z = v[u];
-                const float2 zr = xs[((L - m) & (L - 1)) * QG + ql];
-                const float2 w = tw2[m];                   // (cos(pi m/L), -sin(pi m/L))
-                ab[m * QG + ql] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
-                if ((u & 7) == 7) hoist_fence();
-            }
-        }
-        sync();   // partner reads done: xs is free
-
-        // ---- the tile a third time: |g - mean|^2, the trailing lags by differences (Eq. 1)
-        // and, in the FP64-fixup tier, the leading lags by differences
-        issue(gt);
-        if (!wait()) { timed_out = true; break; }
-        float e[P];
-#pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int t = i + T * u;
-            e[u] = (t < N) ? cabs2(csub(xs[t * QG + ql], mean)) : 0.f;
-        }
+        // ---- from the tile while it is still in xs: the trailing lags by differences
+        // (Eq. 1) and, in the FP64-fixup tier, the leading lags' partial sums (differences
+        // do not depend on the mean)
         float tl[KT];
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
@@ -435,12 +457,57 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
                 if (lane < QG) fixw[(k * NWG + wg) * QG + ql] = fp[k];
             }
         }
-        sync();   // tile fully read
 
-        // |g - mean|^2 into padded rows (frame t at t + t / T): both the cyclic writes here
-        // and the row-wise reads below are conflict-free
+        // ---- odd bins: L-point DFT of g(t) e^{-i pi t / L}; |.|^2 parked in ab
 #pragma unroll
-        for (int u = 0; u < P; ++u) xf[(i + u * (T + 1)) * QG + ql] = e[u];
+        for (int u = 0; u < P; ++u) {
+            v[u] = cmul(v[u], tw2[i + T * u]);
+            if ((u & 7) == 7) hoist_fence();
+        }
+        sync();   // every read of the tile is done: xs becomes the exchange
+        fft_cyclic<L, false>(v, i, xs, xaddr, tw, sync);
+#pragma unroll
+        for (int u = 0; u < P; ++u) ab[(i + T * u) * QG + ql] = cabs2(v[u]);
+
+        // ---- even bins: L-point DFT of g, taken back from tensor memory
+        tmem_st_wait();
+        tmem_ld_seq(t_seq, v);
+        fft_cyclic<L, false>(v, i, xs, xaddr, tw, sync);
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            v[u] = make_float2(cabs2(v[u]), ab[(i + T * u) * QG + ql]);
+            if ((u & 7) == 7) hoist_fence();
+        }
+
+        // ---- inverse transform of Z = |X_even|^2 + i |X_odd|^2, then Re C(m) into tensor memory
+        fft_cyclic<L, true>(v, i, xs, xaddr, tw, sync);
+#pragma unroll
+        for (int u = 0; u < P; ++u) xs[(i + T * u) * QG + ql] = v[u];
+        sync();
+        {
+            const float scale = 0.25f / (float)L;
+            float rc[P];
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+                const int m = i + T * u;
+                const float2 z = v[u];
+                const float2 zr = xs[((L - m) & (L - 1)) * QG + ql];
+                const float2 w = tw2[m];                   // (cos(pi m/L), -sin(pi m/L))
+                rc[u] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
+                if ((u & 7) == 7) hoist_fence();
+            }
+            tmem_st32(t_rec, rc);
+        }
+        sync();   // partner reads done: xs is free
+
+        // ---- the next tile's copy overlaps the power sums, the combination and the stores
+        if (gt + gstride < a.n_tiles) issue(gt + gstride);
+
+        // |g - mean|^2 (from tensor memory) into padded rows of ab (frame t at t + t / T):
+        // both the cyclic writes here and the row-wise reads below are conflict-free
+        tmem_ld_seq(t_seq, v);
+#pragma unroll
+        for (int u = 0; u < P; ++u) ab[(i + u * (T + 1)) * QG + ql] = cabs2(v[u]);
         sync();
         // ---- inclusive prefix sums S(t): thread i owns the rows r = i + T g of T frames
         float rowv[G][T];
@@ -451,7 +518,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             float acc = 0.f;
 #pragma unroll
             for (int jj = 0; jj < T; ++jj) {
-                acc += xf[(r * (T + 1) + jj) * QG + ql];
+                acc += ab[(r * (T + 1) + jj) * QG + ql];
                 rowv[g][jj] = acc;
             }
             racc[g] = acc;
@@ -494,7 +561,7 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
         for (int g = 0; g < G; ++g) {
             const int r = i + T * g;
 #pragma unroll
-            for (int jj = 0; jj < T; ++jj) xf[(r * (T + 1) + jj) * QG + ql] = rowv[g][jj] + off[g];
+            for (int jj = 0; jj < T; ++jj) ab[(r * (T + 1) + jj) * QG + ql] = rowv[g][jj] + off[g];
         }
         sync();
         // FP64-fixup tier: lag m = i (1 <= i <= fix) summed over the group's warps in FP64
@@ -510,23 +577,22 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
 
         // ---- D(m) = (P1 + P2 - 2 Re C) / (N - m) for 0 < m < N - kd
         float dv[P];
+        tmem_st_wait();
+        tmem_ld32(t_rec, dv);                              // Re C(i + T u)
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             const int m = i + T * u;
             float d = 0.f;
             if (m > 0 && m < N - kd) {
-                const float p1 = xf[(base2 - u * (T + 1)) * QG + ql];
-                const float p2 = total - xf[(base1 + u * (T + 1)) * QG + ql];
-                d = (p1 + p2 - 2.f * ab[m * QG + ql]) * inv[m];
+                const float p1 = ab[(base2 - u * (T + 1)) * QG + ql];
+                const float p2 = total - ab[(base1 + u * (T + 1)) * QG + ql];
+                d = (p1 + p2 - 2.f * dv[u]) * inv[m];
                 chk = fmaf(d, 0.f, chk);
             }
             dv[u] = d;
             if ((u & 7) == 7) hoist_fence();
         }
-        sync();   // reads of S and Re C done: xs and ab are free
-
-        // ---- the next tile's copy overlaps the staging and the stores of this one
-        if (gt + gstride < a.n_tiles) issue(gt + gstride);
+        sync();   // reads of S done: ab takes the D rows
 
         // ---- D rows [q][m] staged in ab, then copied out
 #pragma unroll
@@ -569,6 +635,12 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
     }
     if (tg < QG) bulk_wait_all();
     if (chk != chk) atomicOr(a.status, 1u);
+    // every group is done with tensor memory before it is released
+    tmem_st_wait();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) seq_tmem_free(tmem_slot);
 }
 
 // =====================================================================================
