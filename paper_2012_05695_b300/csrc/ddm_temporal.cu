@@ -1023,11 +1023,12 @@ struct XLShape {
     static constexpr size_t OFF_RED = OFF_W64 + 32 * sizeof(float2);         // NWG float2 + 2 NWG float
     static constexpr size_t OFF_XS = (OFF_RED + (size_t)NWG * 16 + 1023) & ~size_t(1023);
     static constexpr size_t XS_ELEMS = (size_t)P * (T + PAD);                // handover; >= L
-    static constexpr size_t OFF_AB = OFF_XS + XS_ELEMS * sizeof(float2);
-    static constexpr size_t BYTES = OFF_AB + (size_t)L * sizeof(float);
+    static constexpr size_t OFF_HT = OFF_XS + XS_ELEMS * sizeof(float2);    // 32 head + 32 tail
+    static constexpr size_t BYTES = OFF_HT + 64 * sizeof(float2);
     static_assert(XS_ELEMS >= (size_t)L && (size_t)(L + L / 32) * sizeof(float) <= XS_ELEMS * sizeof(float2),
                   "exchange holds the transform and the padded power sums");
     static_assert(BYTES + 1024 <= 233472, "one CTA per SM");
+    static_assert(NT == 512, "tensor-memory columns: four warps of 128 columns per lane quarter");
 };
 
 struct XLTables {
@@ -1051,10 +1052,13 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
     float* wsum = reinterpret_cast<float*>(smem_raw + C::OFF_RED + NWG * sizeof(float2));
     float2* xs = reinterpret_cast<float2*>(smem_raw + C::OFF_XS);
     float* xf = reinterpret_cast<float*>(xs);
-    float* ab = reinterpret_cast<float*>(smem_raw + C::OFF_AB);
+    float2* head = reinterpret_cast<float2*>(smem_raw + C::OFF_HT);   // g(t), t < 32
+    float2* tail = head + 32;                                          // g(N - 32 + t), t < 32
+    __shared__ uint32_t tmem_slot;
 
     const int i = threadIdx.x;
     const int lane = i & 31, wg = i >> 5;
+    if (wg == 0) seq_tmem_alloc(&tmem_slot);
     for (int k = i; k < 64; k += C::NT) lo[k] = tb.lo[k];
     for (int k = i; k < L / 64; k += C::NT) hi[k] = tb.hi[k];
     for (int k = i; k < T; k += C::NT) twi[k] = tb.inner[k];
@@ -1070,6 +1074,13 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
     const int m_lo = N - kd;
     const int m_tail = m_lo + ((i - m_lo) % T + T) % T;    // this thread's trailing lag, if < N
     float chk = 0.f;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // tensor-memory columns of this thread (lane 32 (warp mod 4) + lane, 128 columns per warp
+    // of a lane quarter): the mean-removed sequence, |X_odd|^2, Re C
+    const uint32_t t_seq = tmem_slot + ((uint32_t)(32 * (wg & 3)) << 16) + (uint32_t)(wg >> 2) * 128u;
+    const uint32_t t_odd = t_seq + 64u, t_rec = t_seq + 96u;
 
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         const int64_t sq = a.q0 + tile;                    // stored wave vector
@@ -1077,7 +1088,8 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
         const float2* xg = a.blocked ? spec + (tile >> 4) * (int64_t)N * 16 + (tile & 15) : spec + sq;
         const int64_t nq = a.blocked ? 16 : a.n_q;
         __syncthreads();                                   // previous wave vector's reads done
-        // ---- time sequence (thread i holds t = i + T u) and its mean
+        // ---- time sequence (thread i holds t = i + T u), read from global memory once; its
+        // first and last 32 samples for the trailing lags; its mean
         float2 v[P];
         float2 part = make_float2(0.f, 0.f);
 #pragma unroll
@@ -1085,6 +1097,8 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
             const int t = i + T * u;
             v[u] = (t < N) ? __ldg(xg + (int64_t)t * nq) : make_float2(0.f, 0.f);
             part = cadd(part, v[u]);
+            if (t < 32) head[t] = v[u];
+            if (t >= N - 32 && t < N) tail[t - (N - 32)] = v[u];
         }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1100,47 +1114,60 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
             const float rn = 1.0f / (float)N;
             mean = make_float2(mean.x * rn, mean.y * rn);
         }
-        // ---- pass 0, odd bins: DFT of g(t) e^{-i pi t / L}, |.|^2 parked in ab;
-        //      pass 1, even bins: DFT of g (read again)
+#pragma unroll
+        for (int u = 0; u < P; ++u)
+            if (i + T * u < N) v[u] = csub(v[u], mean);
+        // the mean-removed sequence into tensor memory: the even-bin transform and the power
+        // sums take it from there instead of reading global memory again
+        tmem_st_seq(t_seq, v);
+        // ---- pass 0, odd bins: DFT of g(t) e^{-i pi t / L}, |.|^2 parked in tensor memory;
+        //      pass 1, even bins: DFT of g (from tensor memory)
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 0) {
 #pragma unroll
-            for (int u = 0; u < P; ++u) {
-                const int t = i + T * u;
-                if (pass == 0)
-                    v[u] = (t < N) ? cmul(cmul(csub(v[u], mean), c_i), w64[u]) : make_float2(0.f, 0.f);
-                else
-                    v[u] = (t < N) ? csub(__ldg(xg + (int64_t)t * nq), mean) : make_float2(0.f, 0.f);
-                if ((u & 7) == 7) hoist_fence();
+                for (int u = 0; u < P; ++u) {
+                    v[u] = cmul(cmul(v[u], c_i), w64[u]);          // zero past N stays zero
+                    if ((u & 7) == 7) hoist_fence();
+                }
+            } else {
+                tmem_st_wait();
+                tmem_ld_seq(t_seq, v);
             }
             fft_cyclic3<L, false, 1, C::PAD>(v, i, i, 0, xs, tw1, twi, SyncBlock{});
             if (pass == 0) {
+                float o2[P];
 #pragma unroll
-                for (int u = 0; u < P; ++u) ab[u * T + i] = cabs2(v[u]);
+                for (int u = 0; u < P; ++u) o2[u] = cabs2(v[u]);
+                tmem_st32(t_odd, o2);
             }
         }
+        {
+            float o2[P];
+            tmem_st_wait();
+            tmem_ld32(t_odd, o2);
 #pragma unroll
-        for (int u = 0; u < P; ++u) {
-            v[u] = make_float2(cabs2(v[u]), ab[u * T + i]);
-            if ((u & 7) == 7) hoist_fence();
+            for (int u = 0; u < P; ++u) v[u] = make_float2(cabs2(v[u]), o2[u]);
         }
         // ---- inverse of Z = |X_even|^2 + i |X_odd|^2 (input order s1), then Re C in cyclic
-        // order from the 2-for-1 split, into ab by lag
+        // order from the 2-for-1 split, into tensor memory
         fft_cyclic3<L, true, 1, C::PAD, true>(v, s1, i, 0, xs, tw1, twi, SyncBlock{});
 #pragma unroll
         for (int u = 0; u < P; ++u) xs[zs1 + T * u] = v[u];
         __syncthreads();
         {
             const float scale = 0.25f / (float)L;
+            float rc[P];
 #pragma unroll
             for (int u = 0; u < P; ++u) {
                 const int m = i + T * u;
                 const float2 z = xs[zsi + T * u];
                 const float2 zr = xs[zslot((L - m) & (L - 1))];
                 const float2 w = cmul(c_i, w64[u]);        // e^{-i pi m / L}
-                ab[m] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
+                rc[u] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
                 if ((u & 7) == 7) hoist_fence();
             }
+            tmem_st32(t_rec, rc);
         }
         __syncthreads();                                   // xs becomes the power sums
         // ---- |g - mean|^2 at padded positions t + t / 32, then the power sums of Eq. B1 as
@@ -1149,10 +1176,11 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
         // P1(m) = S(N - m) and P2(m) = S(N) - S(m) are each read either directly or as S(N)
         // minus at most about half of it (no S(N) - S(m) cancellation at the largest lags,
         // where it grows like N / (N - m)).  Thread i owns frames 32 i .. 32 i + 31.
+        tmem_ld_seq(t_seq, v);                             // zero past N
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             const int t = i + T * u;
-            xf[t + (t >> 5)] = (t < N) ? cabs2(csub(__ldg(xg + (int64_t)t * nq), mean)) : 0.f;
+            xf[t + (t >> 5)] = cabs2(v[u]);
         }
         __syncthreads();
         const int hc = (N + 63) / 64, h = 32 * hc;
@@ -1198,14 +1226,18 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
                 xf[i * (P + 1) + jj] = off;
             }
         }
-        // ---- the trailing lags by direct differences (Eq. 1): at most kd pairs each
+        // ---- the trailing lags by direct differences (Eq. 1): at most kd pairs each, from the
+        // saved head and tail (t < N - m <= kd <= 32, t + m >= N - kd >= N - 32)
         float tl = 0.f;
         if (m_tail < N) {
             for (int t = 0; t < N - m_tail; ++t)
-                tl += cabs2(csub(__ldg(xg + (int64_t)(t + m_tail) * nq), __ldg(xg + (int64_t)t * nq)));
+                tl += cabs2(csub(tail[t + m_tail - (N - 32)], head[t]));
             tl *= __frcp_rn((float)(N - m_tail));
             chk = fmaf(tl, 0.f, chk);
         }
+        float rcv[P];
+        tmem_st_wait();
+        tmem_ld32(t_rec, rcv);                             // Re C(i + T u)
         __syncthreads();
         // ---- D(m) = (P1 + P2 - 2 Re C) / (N - m), m = i + T u, straight to global memory
         float* drow = D + (int64_t)public_q((int)sq, a) * N;
@@ -1219,7 +1251,7 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
                 const int ta = N - 1 - m;
                 const float p1 = ta < h ? xf[ta + (ta >> 5)] : total - xf[(ta + 1) + ((ta + 1) >> 5)];
                 const float p2 = m >= h ? xf[m + (m >> 5)] : total - xf[(m - 1) + ((m - 1) >> 5)];
-                d = (p1 + p2 - 2.f * ab[m]) * __frcp_rn((float)(N - m));
+                d = (p1 + p2 - 2.f * rcv[u]) * __frcp_rn((float)(N - m));
                 chk = fmaf(d, 0.f, chk);
             } else if (m >= m_lo) {
                 d = tl;                                    // m == m_tail
@@ -1228,6 +1260,11 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
         }
     }
     if (chk != chk) atomicOr(a.status, 1u);
+    tmem_st_wait();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (wg == 0) seq_tmem_free(tmem_slot);
 }
 
 // =====================================================================================
