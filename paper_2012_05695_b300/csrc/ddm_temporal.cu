@@ -276,27 +276,83 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32]) {
           "=f"(r[24]), "=f"(r[25]), "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31])
         : "r"(taddr) : "memory");
 }
-// the 32 complex samples of a thread: v[0..15] in columns [0, 32), v[16..31] in [32, 64)
+// 16-column forms, for kernels with less register room
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&r)[16]) {
+    __syncwarp();
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16};"
+        ::"r"(taddr), "f"(r[0]), "f"(r[1]), "f"(r[2]), "f"(r[3]), "f"(r[4]), "f"(r[5]), "f"(r[6]), "f"(r[7]),
+          "f"(r[8]), "f"(r[9]), "f"(r[10]), "f"(r[11]), "f"(r[12]), "f"(r[13]), "f"(r[14]), "f"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
+    __syncwarp();
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];\n tcgen05.wait::ld.sync.aligned;"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]),
+          "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15])
+        : "r"(taddr) : "memory");
+}
+// the 32 complex samples of a thread in columns [0, 64), (re, im) of v[0], v[1], ...;
+// moved in pieces of 32 columns, or of 16 (SMALL) where registers are short
+template <bool SMALL = false>
 __device__ __forceinline__ void tmem_st_seq(uint32_t taddr, const float2 (&v)[32]) {
+    if constexpr (SMALL) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float r[32];
+        for (int h = 0; h < 4; ++h) {
+            float r[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            r[2 * k] = v[16 * h + k].x;
-            r[2 * k + 1] = v[16 * h + k].y;
+            for (int k = 0; k < 8; ++k) {
+                r[2 * k] = v[8 * h + k].x;
+                r[2 * k + 1] = v[8 * h + k].y;
+            }
+            tmem_st16(taddr + 16u * h, r);
         }
-        tmem_st32(taddr + 32u * h, r);
+    } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float r[32];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                r[2 * k] = v[16 * h + k].x;
+                r[2 * k + 1] = v[16 * h + k].y;
+            }
+            tmem_st32(taddr + 32u * h, r);
+        }
     }
 }
+template <bool SMALL = false>
 __device__ __forceinline__ void tmem_ld_seq(uint32_t taddr, float2 (&v)[32]) {
+    if constexpr (SMALL) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float r[32];
-        tmem_ld32(taddr + 32u * h, r);
+        for (int h = 0; h < 4; ++h) {
+            float r[16];
+            tmem_ld16(taddr + 16u * h, r);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[16 * h + k] = make_float2(r[2 * k], r[2 * k + 1]);
+            for (int k = 0; k < 8; ++k) v[8 * h + k] = make_float2(r[2 * k], r[2 * k + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float r[32];
+            tmem_ld32(taddr + 32u * h, r);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[16 * h + k] = make_float2(r[2 * k], r[2 * k + 1]);
+        }
     }
+}
+
+template <int NCOLS>
+__device__ __forceinline__ void long_tmem_alloc(uint32_t* slot) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(slot)), "n"(NCOLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+template <int NCOLS>
+__device__ __forceinline__ void long_tmem_free(uint32_t tmem) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(NCOLS) : "memory");
 }
 
 template <int LOG2L, int NGROUPS, bool FIXUP>
@@ -677,13 +733,15 @@ struct LShape {
     static constexpr size_t OFF_W64 = OFF_CI + (size_t)T * sizeof(float2);         // 32 entries
     static constexpr size_t OFF_XS = (OFF_W64 + 32 * sizeof(float2) + 1023) & ~size_t(1023);
     static constexpr size_t OFF_AB = OFF_XS + XS_ELEMS * sizeof(float2);
-    static constexpr size_t OFF_RED = OFF_AB + cmax((size_t)L * QG, (size_t)QG * DS) * sizeof(float);
+    // ab: the padded |g|^2 / prefix rows ((L + L/32) QG floats), then the D rows
+    static constexpr size_t AB_FLOATS = cmax(cmax((size_t)L * QG, (size_t)QG * DS), (size_t)(L + L / P) * QG);
+    static constexpr size_t OFF_RED = OFF_AB + AB_FLOATS * sizeof(float);
     static constexpr int FIX_MAX = 8;
     static constexpr size_t OFF_FIX = OFF_RED + (size_t)T * QG * sizeof(float);
     static constexpr size_t BYTES = OFF_FIX + (size_t)FIX_MAX * NWG * QG * sizeof(float);
     static_assert(T % P == 0 && QG * T == NT && QG >= 2, "long kernel: L = 2048 .. 8192");
     static_assert(CTAS_PER_SM * (BYTES + 1024) <= 233472, "shared memory per SM");
-    static_assert((size_t)(L + L / P) * QG <= 2 * XS_ELEMS, "padded prefix chunks must fit");
+    static_assert(NT % 128 == 0, "tensor memory: 128 columns per warp, NT columns per CTA");
     static_assert((size_t)NWG * QG * 2 <= (size_t)T * QG, "mean partials must fit");
     static_assert((DS % 4) == 0 && (OFF_AB % 16) == 0, "D rows 16-byte aligned for bulk copies");
 };
@@ -704,13 +762,14 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
     constexpr int DS = C::DS, PAD = C::PAD, FM = C::FIX_MAX;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t tile_bar;
+    __shared__ uint32_t tmem_slot;
     float2* twq = reinterpret_cast<float2*>(smem_raw + C::OFF_TWQ);
     float2* twi = reinterpret_cast<float2*>(smem_raw + C::OFF_TWI);
     float2* ci = reinterpret_cast<float2*>(smem_raw + C::OFF_CI);
     float2* w64 = reinterpret_cast<float2*>(smem_raw + C::OFF_W64);
     float2* xs = reinterpret_cast<float2*>(smem_raw + C::OFF_XS);
-    float* xf = reinterpret_cast<float*>(xs);
     float* ab = reinterpret_cast<float*>(smem_raw + C::OFF_AB);
+    float* xf = ab;                              // the padded |g|^2 / prefix rows
     float* red = reinterpret_cast<float*>(smem_raw + C::OFF_RED);
     float2* red2 = reinterpret_cast<float2*>(red);
     float* fixw = reinterpret_cast<float*>(smem_raw + C::OFF_FIX);
@@ -726,10 +785,17 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
         ci[k] = tb.ci[k];
     }
     if (tid < 32) w64[tid] = tb.w64[tid];
+    if (tid < 32) long_tmem_alloc<NT>(&tmem_slot);
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
 
     const int ql = tid % QG, i = tid / QG;
     const int lane = tid & 31, wg = tid >> 5;
+    // tensor-memory columns of this thread (lane 32 (warp mod 4) + lane, 128 columns per warp
+    // of a lane quarter): the mean-removed sequence, |X_odd|^2, Re C
+    const uint32_t t_seq = tmem_slot + ((uint32_t)(32 * (wg & 3)) << 16) + (uint32_t)(wg >> 2) * 128u;
+    const uint32_t t_odd = t_seq + 64u, t_rec = t_seq + 96u;
     const int s1 = fft3_sigma(i, P, R);          // forward output order
     const float2 c_i = ci[i];
     // Transform outputs come in the order s1 = sigma(i) (a warp's lanes 32 / R apart in
@@ -797,70 +863,15 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
             const float rn = 1.0f / (float)N;
             mean = make_float2(mean.x * rn, mean.y * rn);
         }
-        // ---- pass 0, odd bins: DFT of g(t) e^{-i pi t / L}, |.|^2 parked in ab;
-        //      pass 1, even bins: DFT of g (the tile again).  One copy of the transform's
-        //      code for both (the unrolled transform is most of the kernel's instructions).
-        bool tile_lost = false;
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-            if (pass == 0) {
 #pragma unroll
-                for (int u = 0; u < P; ++u) {
-                    const int t = i + T * u;
-                    v[u] = (t < N) ? cmul(cmul(csub(v[u], mean), c_i), w64[u]) : make_float2(0.f, 0.f);
-                    if ((u & 7) == 7) hoist_fence();
-                }
-            } else {
-                issue(tile);
-                if (!wait()) { tile_lost = true; break; }
-#pragma unroll
-                for (int u = 0; u < P; ++u) {
-                    const int t = i + T * u;
-                    v[u] = (t < N) ? csub(xs[t * QG + ql], mean) : make_float2(0.f, 0.f);
-                }
-                __syncthreads();
-            }
-            fft_cyclic3<L, false, QG, PAD>(v, i, i, ql, xs, tw1, twi, SyncBlock{});
-            if (pass == 0) {
-                // parked by (u, i): the same thread reads it back with the same indices
-#pragma unroll
-                for (int u = 0; u < P; ++u) ab[(u * T + i) * QG + ql] = cabs2(v[u]);
-            }
-        }
-        if (tile_lost) { timed_out = true; break; }
-#pragma unroll
-        for (int u = 0; u < P; ++u) {
-            v[u] = make_float2(cabs2(v[u]), ab[(u * T + i) * QG + ql]);
-            if ((u & 7) == 7) hoist_fence();
-        }
-        // ---- inverse of Z = |X_even|^2 + i |X_odd|^2: input order s1, groups by i, output
-        // order s1
-        fft_cyclic3<L, true, QG, PAD, true>(v, s1, i, ql, xs, tw1, twi, SyncBlock{});
-#pragma unroll
-        for (int u = 0; u < P; ++u) xs[(zs1 + T * u) * QG + ql] = v[u];
-        __syncthreads();
-        {
-            const float scale = 0.25f / (float)L;
-#pragma unroll
-            for (int u = 0; u < P; ++u) {
-                const int m = i + T * u;
-                const float2 z = xs[(zsi + T * u) * QG + ql];
-                const float2 zr = xs[zslot((L - m) & (L - 1)) * QG + ql];
-                const float2 w = cmul(c_i, w64[u]);        // e^{-i pi m / L}
-                ab[m * QG + ql] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
-                if ((u & 7) == 7) hoist_fence();
-            }
-        }
-        // ---- the tile a third time: |g - mean|^2 and the trailing lags (Eq. 1)
-        __syncthreads();                                   // partner reads done: xs is free
-        issue(tile);
-        if (!wait()) { timed_out = true; break; }
-        float e[P];
-#pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int t = i + T * u;
-            e[u] = (t < N) ? cabs2(csub(xs[t * QG + ql], mean)) : 0.f;
-        }
+        for (int u = 0; u < P; ++u)
+            if (i + T * u < N) v[u] = csub(v[u], mean);
+        // the mean-removed sequence into tensor memory: both forward transforms and the power
+        // sums take it from there (so the tile is copied from global memory once, and the
+        // registers are free for the sums below)
+        tmem_st_seq<true>(t_seq, v);
+        // ---- from the tile while it is still in xs: the trailing lag by differences (Eq. 1)
+        // and, in the FP64-fixup tier, the leading lags' partial sums
         float tl = 0.f;
         if (m_tail < N) {
             for (int t = 0; t < N - m_tail; ++t)
@@ -892,12 +903,74 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
                 if (lane < QG) fixw[(k * NWG + wg) * QG + ql] = fp[k];
             }
         }
-        __syncthreads();                                   // tile read
-        // |g|^2 at padded positions t + t / 32 (chunk-wise reads below are conflict-free)
+        __syncthreads();                                   // every read of the tile is done
+        // ---- pass 0, odd bins: DFT of g(t) e^{-i pi t / L}, |.|^2 parked in tensor memory;
+        //      pass 1, even bins: DFT of g (from tensor memory).  One copy of the transform's
+        //      code for both (the unrolled transform is most of the kernel's instructions).
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            tmem_st_wait();
+            tmem_ld_seq<true>(t_seq, v);
+            if (pass == 0) {
+#pragma unroll
+                for (int u = 0; u < P; ++u) {
+                    v[u] = cmul(cmul(v[u], c_i), w64[u]);          // zero past N stays zero
+                    if ((u & 7) == 7) hoist_fence();
+                }
+            }
+            fft_cyclic3<L, false, QG, PAD>(v, i, i, ql, xs, tw1, twi, SyncBlock{});
+            if (pass == 0) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float o2[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) o2[k] = cabs2(v[16 * h + k]);
+                    tmem_st16(t_odd + 16u * h, o2);
+                }
+            }
+        }
+        tmem_st_wait();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float o2[16];
+            tmem_ld16(t_odd + 16u * h, o2);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[16 * h + k] = make_float2(cabs2(v[16 * h + k]), o2[k]);
+        }
+        // ---- inverse of Z = |X_even|^2 + i |X_odd|^2: input order s1, groups by i, output
+        // order s1
+        fft_cyclic3<L, true, QG, PAD, true>(v, s1, i, ql, xs, tw1, twi, SyncBlock{});
+#pragma unroll
+        for (int u = 0; u < P; ++u) xs[(zs1 + T * u) * QG + ql] = v[u];
+        __syncthreads();
+        {
+            const float scale = 0.25f / (float)L;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float rc[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int u = 16 * h + k;
+                    const int m = i + T * u;
+                    const float2 z = xs[(zsi + T * u) * QG + ql];
+                    const float2 zr = xs[zslot((L - m) & (L - 1)) * QG + ql];
+                    const float2 w = cmul(c_i, w64[u]);    // e^{-i pi m / L}
+                    rc[k] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
+                    if ((k & 7) == 7) hoist_fence();
+                }
+                tmem_st16(t_rec + 16u * h, rc);
+            }
+        }
+        __syncthreads();                                   // partner reads done: xs is free
+        // ---- the next tile's copy overlaps the power sums, the combination and the stores
+        if (tile + gridDim.x < a.n_tiles) issue(tile + gridDim.x);
+        // |g - mean|^2 (from tensor memory) at padded positions t + t / 32 of ab (chunk-wise
+        // reads below are conflict-free)
+        tmem_ld_seq<true>(t_seq, v);                             // zero past N
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             const int t = i + T * u;
-            xf[(t + (t >> 5)) * QG + ql] = e[u];
+            xf[(t + (t >> 5)) * QG + ql] = cabs2(v[u]);
         }
         __syncthreads();
         // ---- inclusive prefix sums: thread i owns frames 32 i .. 32 i + 31; the offsets of
@@ -940,6 +1013,14 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
         }
         // ---- D(m) = (P1 + P2 - 2 Re C) / (N - m) for 0 < m < N - kd, m = i + T u
         float dv[P];
+        tmem_st_wait();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {                      // Re C(i + T u)
+            float rc[16];
+            tmem_ld16(t_rec + 16u * h, rc);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) dv[16 * h + k] = rc[k];
+        }
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             const int m = i + T * u;
@@ -948,15 +1029,13 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
                 const int ta = N - 1 - m, tb2 = m - 1;
                 const float p1 = xf[(ta + (ta >> 5)) * QG + ql];
                 const float p2 = total - xf[(tb2 + (tb2 >> 5)) * QG + ql];
-                d = (p1 + p2 - 2.f * ab[m * QG + ql]) * __frcp_rn((float)(N - m));
+                d = (p1 + p2 - 2.f * dv[u]) * __frcp_rn((float)(N - m));
                 chk = fmaf(d, 0.f, chk);
             }
             dv[u] = d;
             if ((u & 7) == 7) hoist_fence();
         }
-        __syncthreads();                                   // reads of S and Re C done
-        // ---- the next tile's copy overlaps the staging and the stores of this one
-        if (tile + gridDim.x < a.n_tiles) issue(tile + gridDim.x);
+        __syncthreads();                                   // reads of S done: ab takes the D rows
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             const int m = i + T * u;
@@ -990,6 +1069,11 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
     }
     if (tid < QG) bulk_wait_all();
     if (chk != chk) atomicOr(a.status, 1u);
+    tmem_st_wait();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid < 32) long_tmem_free<NT>(tmem_slot);
 }
 
 // =====================================================================================
