@@ -808,6 +808,27 @@ def run_ours(args):
         torch.cuda.synchronize()
         tiers["fp32_fp64fix"] = {"temporal_ms": f0.elapsed_time(f1) / 10, "fix_lags": 8}
 
+    # ---- the tensor-core DFT-as-GEMM column pass (DDM_PREC_TC_TF32X3) on the same stack:
+    # step one's time beside the CUDA-core pass, and (with the oracle leg) its error
+    D_tc = None
+    if rank == 0 and H == 512:
+        plan_tc = ddm.Plan(H, W, N_FRAMES, dtype="u16", precision=ddm.DDM_PREC_TC_TF32X3)
+        for _ in range(3):
+            plan_tc.spatial_fft(frames, spec, stream)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(10):
+            plan_tc.spatial_fft(frames, spec, stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        D_tc = torch.empty_like(D)
+        plan_tc.structure_function(frames, D_tc, stream)
+        torch.cuda.synchronize()
+        tiers["tc_tf32x3"] = {"spatial_ms": f0.elapsed_time(f1) / 10, "spatial_ms_fp32": sp_ms,
+                              "column_pass": "tcgen05.mma kind::tf32, 512 = 16 x 32, two-term operand splits",
+                              "device_status": plan_tc.last_device_status()}
+        plan_tc.close()
+
     # ---- the FP64 tier on the same stack (the precision sweep's reference): both steps
     D64 = None
     if rank == 0 and N_FRAMES <= 4096 and not args.no_fp64:
@@ -906,6 +927,9 @@ def run_ours(args):
             D6 = D64.view(H, W // 2 + 1, N_FRAMES)[:, cols, :].cpu().numpy()
             tiers["fp64"]["max_rel_err"] = oracle.scaled_error(D6, D_or, s_q)
             tiers["fp64"]["small_lag_err_rel_D"] = float(np.max(np.abs(D6[..., 1:9] - ref) / ref))
+        if D_tc is not None:
+            Dt = D_tc.view(H, W // 2 + 1, N_FRAMES)[:, cols, :].cpu().numpy()
+            tiers["tc_tf32x3"]["max_rel_err"] = oracle.scaled_error(Dt, D_or, s_q)
         if D_fix is not None:
             Df = D_fix.view(H, W // 2 + 1, N_FRAMES)[:, cols, :].cpu().numpy()
             tiers["fp32_fp64fix"]["max_rel_err"] = oracle.scaled_error(Df, D_or, s_q)

@@ -58,13 +58,19 @@ typedef enum ddm_precision {
                                  differences (Eq. 1), FP32 over each thread's 32 frames and
                                  FP64 across threads: no cancellation against the power
                                  sums.  Implemented for 257 <= N <= 8192, fix_lags <= 8 */
-    DDM_PREC_FP64 = 2    /* everything in FP64 on the GPU (the precision sweep's reference
+    DDM_PREC_FP64 = 2,   /* everything in FP64 on the GPU (the precision sweep's reference
                             tier; D is still written as float32): spatial and time
                             transforms, power sums and combination.  About 1/64 of the
                             FP32 rate.  Implemented for power-of-two sides, N <= 4096, kmax = 0,
                             the whole wave-vector range, ddm_structure_function only
                             (ddm_spatial_fft / ddm_temporal_sf / the static entry return
                             DDM_ERR_UNSUPPORTED: the spectrum workspace is complex128) */
+    DDM_PREC_TC_TF32X3 = 3 /* as DDM_PREC_FP32, but step one's column transform runs on the
+                              tensor cores as DFT-as-GEMM (512 = 16 x 32: two GEMM stages of
+                              tcgen05.mma kind::tf32, every operand split into two TF32 terms,
+                              three products per term pair, FP32 accumulation).  Implemented
+                              for H = 512 and power-of-two W of 32 .. 1024, whole plane, two-
+                              pass step one (DDM_ERR_UNSUPPORTED otherwise) */
 } ddm_precision;
 
 /* Kernels of step one.  Both give the same spectrum (to FP32 rounding). */

@@ -6,5 +6,6 @@ zero-padded time sequence, behind the C ABI of include/ddm.h.  This package is t
 Python binding; all arithmetic runs in the CUDA library built from csrc/.
 """
 from ._binding import (DDM_IN_F32, DDM_IN_U16, DDM_PREC_FP32, DDM_PREC_FP32_FP64FIX, DDM_PREC_FP64,  # noqa: F401
+                       DDM_PREC_TC_TF32X3,
                        DDMError, LIB_PATH, MLP, Plan, header_functions, lib, selftest_bounded_wait,
                        spectrum_index_map, status_string)

@@ -29,6 +29,7 @@ DDM_IN_F32 = 1
 DDM_PREC_FP32 = 0
 DDM_PREC_FP32_FP64FIX = 1
 DDM_PREC_FP64 = 2
+DDM_PREC_TC_TF32X3 = 3
 
 DDM_SPATIAL_TWO_PASS = 0
 DDM_SPATIAL_FUSED = 1

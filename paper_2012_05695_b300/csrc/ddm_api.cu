@@ -84,6 +84,7 @@ void free_plan(ddm_plan_s* p) {
         cudaFree(b->twin);
     }
     cudaFree(p->tw_long);
+    cudaFree(p->tc_tables);
     cudaFree(p->tw2);
     cudaFree(p->inv);
     cudaFree(p->bin_start);
@@ -246,8 +247,9 @@ ddm_status validate(const ddm_plan_desc* d) {
     if (d->N > kMaxFrames) return DDM_ERR_UNSUPPORTED;
     if (d->dtype != DDM_IN_U16 && d->dtype != DDM_IN_F32) return DDM_ERR_INVALID_ARG;
     if (d->precision != DDM_PREC_FP32 && d->precision != DDM_PREC_FP32_FP64FIX &&
-        d->precision != DDM_PREC_FP64)
+        d->precision != DDM_PREC_FP64 && d->precision != DDM_PREC_TC_TF32X3)
         return DDM_ERR_INVALID_ARG;
+    if (d->precision == DDM_PREC_TC_TF32X3 && !tc_columns_supported(*d)) return DDM_ERR_UNSUPPORTED;
     if (d->precision == DDM_PREC_FP32_FP64FIX) {
         // built for the time transforms whose tiles arrive whole in shared memory
         const int Lf = 1 << ilog2(d->N);
@@ -527,6 +529,11 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
         }
         st = upload(&p->tw64, t64);
         if (st == DDM_OK) st = upload(&p->tw64_half, h64);
+    }
+    if (st == DDM_OK && desc->precision == DDM_PREC_TC_TF32X3) {
+        std::vector<float> t(tc_column_table_floats());
+        tc_column_tables(t.data());
+        st = upload(&p->tc_tables, t);
     }
     if (st == DDM_OK) st = make_fit_tables(p);
     if (st == DDM_OK) {

@@ -59,6 +59,8 @@ struct ddm_plan_s {
                         // i < L/32; exp(-i pi u / 32) for u < 32
     float2* tw2;        // exp(-i pi t / L), t < L
     float* inv;         // 1 / (N - m), m < N; 0 at m = 0
+    float* tc_tables = nullptr;     // DDM_PREC_TC_TF32X3: DFT matrix images and twiddles of
+                                    // the tensor-core column pass (tc_column_tables)
     int* bin_start;     // [n_bins + 1] CSR offsets into bin_q
     int* bin_q;         // per bin, ascending: (public q << 1) | (q stands for itself and -q)
     int* bin_count;     // [n_bins] full-plane modes per bin
@@ -133,6 +135,10 @@ struct SpecOut {
 };
 
 bool fp64_supported(const ddm_plan_desc& d);
+bool tc_columns_supported(const ddm_plan_desc& d);
+void tc_column_tables(float* out);
+size_t tc_column_table_floats();
+cudaError_t launch_cols_tc(const ddm_plan_s* p, float2* spec, cudaStream_t s);
 ddm_status launch_fp64(const ddm_plan_s* p, const void* frames, void* workspace, float* D, cudaStream_t s);
 void mixed_shape(int n, int* P, int* T);
 cudaError_t launch_rows_mixed(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s);

@@ -386,6 +386,15 @@ ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
         (reinterpret_cast<uintptr_t>(frames) & 15) == 0)
         return launch_spatial_fused(p, frames, spec, s);
     cudaError_t e;
+    if (p->d.precision == DDM_PREC_TC_TF32X3) {
+        // the column transform on the tensor cores, in place (a blocked copy, if the time
+        // kernels want one, is then made by step two)
+        e = rows_bulk_supported(p, frames) ? launch_rows_bulk(p, frames, spec, s)
+            : ((p->d.dtype == DDM_IN_U16) ? dispatch_rows<uint16_t>(p, frames, spec, s)
+                                          : dispatch_rows<float>(p, frames, spec, s));
+        if (e != cudaSuccess) return DDM_ERR_CUDA;
+        return launch_cols_tc(p, spec, s) == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
+    }
     if (rows_bulk_supported(p, frames))
         e = launch_rows_bulk(p, frames, spec, s);
     else

@@ -61,7 +61,8 @@ def test_desc_init_defaults():
     ("N", 16385, B.DDM_ERR_UNSUPPORTED),
     ("dtype", 7, B.DDM_ERR_INVALID_ARG),
     ("precision", 9, B.DDM_ERR_INVALID_ARG),
-    ("precision", 3, B.DDM_ERR_INVALID_ARG),
+    ("precision", 4, B.DDM_ERR_INVALID_ARG),
+    ("precision", 3, B.DDM_ERR_UNSUPPORTED),      # tensor-core column pass: H = 512 only
     ("precision", 1, B.DDM_ERR_UNSUPPORTED),      # FP64 fixup needs N >= 257
     ("M", 6, B.DDM_ERR_INVALID_ARG),          # M < 2N - 1 wraps around (App. B)
     ("M", 7, B.DDM_ERR_UNSUPPORTED),          # legal pad length, not the one built
