@@ -1398,6 +1398,14 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
     float2* red2 = reinterpret_cast<float2*>(smem_raw + C::OFF_RED);
 
     const int tid = threadIdx.x;
+    // at P = 32 (L >= 32) every thread's mean-removed sequence waits in tensor memory for the
+    // even-bin transform and the power sums (two fewer reads of the tile from L2); each of the
+    // 8 warps owns 128 columns of its lane quarter, 256 per CTA
+    constexpr bool STASH = (P == 32);
+    __shared__ uint32_t tmem_slot;
+    if constexpr (STASH) {
+        if (tid < 32) long_tmem_alloc<NT>(&tmem_slot);
+    }
     if constexpr (T > 1) {
         for (int k = tid; k < L; k += NT) tw[k] = a.tw[k];
     }
@@ -1405,7 +1413,12 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
         tw2[k] = a.tw2[k];
         inv[k] = a.inv[k];
     }
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const uint32_t t_seq = STASH ? tmem_slot + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
+                                       (uint32_t)(tid >> 7) * 128u
+                                 : 0u;
 
     const int ql = tid % QT;
     const int i = tid / QT;
@@ -1460,6 +1473,7 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
             if (t < kd) head[t * QT + ql] = v[u];
             if (t >= N - kd && t < N) tail[(t - (N - kd)) * QT + ql] = v[u];
         }
+        if constexpr (STASH) tmem_st_seq<true>(t_seq, v);
         __syncthreads();   // head/tail visible; the mean buffer may be reused
 
         // ---- odd bins: L-point DFT of g(t) e^{-i pi t / L}; |.|^2 parked in ab
@@ -1472,8 +1486,11 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
 #pragma unroll
         for (int u = 0; u < P; ++u) ab[(i + T * u) * QT + ql] = cabs2(v[u]);
 
-        // ---- even bins: L-point DFT of g (reloaded; the tile is still in L2)
-        {
+        // ---- even bins: L-point DFT of g (from tensor memory, or reloaded from L2 at P < 32)
+        if constexpr (STASH) {
+            tmem_st_wait();
+            tmem_ld_seq<true>(t_seq, v);
+        } else {
             const float2* src2 = opaque_ptr(src);
 #pragma unroll
             for (int u = 0; u < P; ++u) {
@@ -1506,8 +1523,15 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
         __syncthreads();   // partner reads done: the exchange buffer is free
 
         // ---- power terms: inclusive prefix sums S(t) of |g|^2.  Thread i owns the rows
-        // r = i + T g of T consecutive t (reloaded from L2), sums them in registers, and
-        // adds the offset of the rows before it.
+        // r = i + T g of T consecutive t (at P = 32 |g|^2 comes from tensor memory through
+        // the free exchange buffer [t][QT]; below that the tile is reloaded from L2), sums
+        // them in registers, and adds the offset of the rows before it.
+        if constexpr (STASH) {
+            tmem_ld_seq<true>(t_seq, v);                   // zero past N and past q1
+#pragma unroll
+            for (int u = 0; u < P; ++u) xf[(i + T * u) * QT + ql] = cabs2(v[u]);
+            __syncthreads();
+        }
         const float2* src3 = opaque_ptr(src);
         constexpr int G = P / T;
         float rowv[G][T];
@@ -1518,7 +1542,11 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
 #pragma unroll
             for (int jj = 0; jj < T; ++jj) {
                 const int t = r * T + jj;
-                if (valid && t < N) acc += cabs2(csub(__ldg(src3 + (uint32_t)t * nq32), mean));
+                if constexpr (STASH) {
+                    acc += xf[t * QT + ql];
+                } else {
+                    if (valid && t < N) acc += cabs2(csub(__ldg(src3 + (uint32_t)t * nq32), mean));
+                }
                 rowv[g][jj] = acc;
             }
             red[r * QT + ql] = acc;
@@ -1593,6 +1621,13 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
         __syncthreads();
     }
     if (bad) atomicOr(a.status, 1u);
+    if constexpr (STASH) {
+        tmem_st_wait();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid < 32) long_tmem_free<NT>(tmem_slot);
+    }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
