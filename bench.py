@@ -70,7 +70,10 @@ def parse_args():
     ap.add_argument("--no-precision-sweep", action="store_true",
                     help="skip the 1024x1024x4096 float32 precision sweep (three tiers)")
     ap.add_argument("--crossover", action="store_true",
-                    help="also time WITH_FT vs WITHOUT_FT step two at 512^2 for N = 128 .. 16384")
+                    help="also time WITH_FT vs WITHOUT_FT step two at the frame side (512^2 unless "
+                         "--shape) for N = 128 .. 16384")
+    ap.add_argument("--crossover-ns", default="128,256,512,1024,2048,4096,8192,16384",
+                    help="stack lengths of the crossover sweep (comma-separated)")
     ap.add_argument("--no-long", action="store_true",
                     help="skip the 512x512x16384 (longest stacks) timing")
     ap.add_argument("--kmax", type=int, default=63,
@@ -885,7 +888,10 @@ def run_ours(args):
     if rank == 0 and not args.no_long:
         long_stack = time_long_stack(ddm, dev, stream, args.seed)
     sweep = image_size_sweep(ddm, dev, stream, args.seed) if (rank == 0 and args.sweep) else None
-    crossover = crossover_sweep(ddm, dev, stream, args.seed) if (rank == 0 and args.crossover) else None
+    crossover = None
+    if rank == 0 and args.crossover:
+        crossover = crossover_sweep(ddm, dev, stream, args.seed, side=H,
+                                    Ns=tuple(int(x) for x in args.crossover_ns.split(",")))
     psweep = None
     if rank == 0 and not args.no_precision_sweep:
         psweep = precision_sweep(ddm, dev, stream, args.seed,
