@@ -371,8 +371,10 @@ ddm_status ddm_plan_create(ddm_plan* out, const ddm_plan_desc* desc) {
     p->q1 = ranged ? desc->q_end : p->n_q;
     p->blocked = spectrum_blocked(*desc);
     p->blk_offset = spectrum_bytes(*desc);
-    const int KD = std::min(32, p->L / 2);
-    p->kd = std::min(KD, desc->N - 1);
+    // trailing lags taken by differences: the FFT route's FP32 error in D(m) grows like
+    // N / (N - m), so the last N / 32 lags (at most 32, at least 1) go by differences and
+    // the factor stays below 32 at every N
+    p->kd = std::min(std::min(32, std::max(1, desc->N / 32)), desc->N - 1);
     p->fix_lags = desc->fix_lags > 0 ? desc->fix_lags : 8;
     if (cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();

@@ -484,9 +484,18 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             const int m = m0 + k * T;
             float acc = 0.f;
             if (m < N) {
-                for (int t = 0; t < N - m; ++t)
-                    acc += cabs2(csub(xs[(t + m) * QG + ql], xs[t * QG + ql]));
-                acc *= inv[m];
+                // four partial sums: the group waits at its next barrier for the thread with
+                // the most pairs (kd of them), so its chain of dependent adds is kept short
+                const int n = N - m;
+                float a4[4] = {0.f, 0.f, 0.f, 0.f};
+                int t = 0;
+                for (; t + 4 <= n; t += 4) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        a4[j] += cabs2(csub(xs[(t + j + m) * QG + ql], xs[(t + j) * QG + ql]));
+                }
+                for (; t < n; ++t) a4[0] += cabs2(csub(xs[(t + m) * QG + ql], xs[t * QG + ql]));
+                acc = ((a4[0] + a4[1]) + (a4[2] + a4[3])) * inv[m];
                 chk = fmaf(acc, 0.f, chk);
             }
             tl[k] = acc;
@@ -1352,8 +1361,12 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
 }
 
 // =====================================================================================
-// L <= 256: one group per CTA, per-thread loads
+// L <= 256: one group per CTA, per-thread loads; two CTAs per SM at L = 128, 256 and
+// L <= 16 (shared memory), one at L = 32, 64
 // =====================================================================================
+// The first and last kd samples of each wave vector go through the exchange buffer before
+// the transforms need it, and the trailing lags are taken from them there; the D rows are
+// staged [q][m] and each warp copies whole rows out (lanes on consecutive lags).
 template <int LOG2L>
 struct TShape {
     static constexpr int L = 1 << LOG2L;
@@ -1361,7 +1374,10 @@ struct TShape {
     static constexpr int P = S::P, T = S::T;
     static constexpr int NT = 256;                         // threads per CTA
     static constexpr int QT = NT / T;                      // wave vectors per tile (>= 32)
-    static constexpr int KD = (L / 2 < 32) ? L / 2 : 32;  // max directly evaluated lags
+    // most trailing lags taken by differences: the plan's kd = min(32, max(1, N / 32), N - 1)
+    // never exceeds L / 32 (at least 1 where L >= 2); one lag per thread
+    static constexpr int KD = L >= 32 ? L / 32 : (L >= 2 ? 1 : 0);
+    static constexpr int KT = KD > 0 ? (KD + T - 1) / T : 0;
     static constexpr int DSTRIDE = L + 1;                  // D staging row stride
     static constexpr int RED = (P > 2 * T ? P : 2 * T);
     static constexpr size_t OFF_TW = 0;
@@ -1369,21 +1385,22 @@ struct TShape {
     static constexpr size_t OFF_INV = OFF_TW2 + (size_t)L * sizeof(float2);
     static constexpr size_t OFF_XS = (OFF_INV + (size_t)L * sizeof(float) + 1023) & ~size_t(1023);
     static constexpr size_t OFF_AB = OFF_XS + (size_t)L * QT * sizeof(float2);
-    static constexpr size_t OFF_HT = OFF_AB + (size_t)L * QT * sizeof(float);
-    static constexpr size_t OFF_MU = OFF_HT + (size_t)2 * (KD > 0 ? KD : 1) * QT * sizeof(float2);
+    static constexpr size_t OFF_MU = OFF_AB + (size_t)L * QT * sizeof(float);
     static constexpr size_t OFF_RED = OFF_MU + (size_t)QT * sizeof(float2);
     static constexpr size_t BYTES = OFF_RED + (size_t)RED * QT * sizeof(float);
     static_assert(L <= 256 && QT >= 32, "per-thread-load kernel: L <= 256");
     static_assert(BYTES <= 232448, "temporal kernel shared memory exceeds 227 KB");
     static_assert((size_t)QT * DSTRIDE <= (size_t)2 * L * QT, "D staging must fit the exchange buffer");
+    static_assert(2 * KD <= L, "the head and tail samples fit the exchange buffer");
+    // two CTAs per SM where their shared memory allows (tensor memory: 256 columns each)
+    static constexpr int CTAS_PER_SM = 2 * (BYTES + 1024) <= 233472 ? 2 : 1;
 };
 
-// (shared memory allows one CTA per SM at every L: the register file is all this CTA's)
 template <int LOG2L>
-__global__ void __launch_bounds__(TShape<LOG2L>::NT, 1)
+__global__ void __launch_bounds__(TShape<LOG2L>::NT, TShape<LOG2L>::CTAS_PER_SM)
 temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs a) {
     using C = TShape<LOG2L>;
-    constexpr int L = C::L, P = C::P, T = C::T, NT = C::NT, QT = C::QT, KD = C::KD;
+    constexpr int L = C::L, P = C::P, T = C::T, NT = C::NT, QT = C::QT, KD = C::KD, KT = C::KT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2* tw = reinterpret_cast<float2*>(smem_raw + C::OFF_TW);
     float2* tw2 = reinterpret_cast<float2*>(smem_raw + C::OFF_TW2);
@@ -1391,8 +1408,8 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
     float2* xs = reinterpret_cast<float2*>(smem_raw + C::OFF_XS);
     float* xf = reinterpret_cast<float*>(smem_raw + C::OFF_XS);     // same bytes as xs
     float* ab = reinterpret_cast<float*>(smem_raw + C::OFF_AB);
-    float2* head = reinterpret_cast<float2*>(smem_raw + C::OFF_HT);
-    float2* tail = head + (KD > 0 ? KD : 1) * QT;
+    float2* head = xs;                   // the first kd samples [t][QT], then the last kd,
+    float2* tail = xs + KD * QT;         // while the exchange buffer is free
     float2* mu = reinterpret_cast<float2*>(smem_raw + C::OFF_MU);
     float* red = reinterpret_cast<float*>(smem_raw + C::OFF_RED);
     float2* red2 = reinterpret_cast<float2*>(smem_raw + C::OFF_RED);
@@ -1470,11 +1487,32 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
         for (int u = 0; u < P; ++u) {
             const int t = i + T * u;
             if (t < N) v[u] = csub(v[u], mean);
-            if (t < kd) head[t * QT + ql] = v[u];
-            if (t >= N - kd && t < N) tail[(t - (N - kd)) * QT + ql] = v[u];
+            if constexpr (KD > 0) {
+                if (t < kd) head[t * QT + ql] = v[u];
+                if (t >= N - kd && t < N) tail[(t - (N - kd)) * QT + ql] = v[u];
+            }
         }
         if constexpr (STASH) tmem_st_seq<true>(t_seq, v);
         __syncthreads();   // head/tail visible; the mean buffer may be reused
+
+        // ---- the last kd lags (N - m <= kd pairs) directly from Eq. 1, by differences of the
+        // head and tail samples; kept in registers until the D rows are staged
+        const int m_lo = (N - kd > 1) ? N - kd : 1;
+        const int m_first = m_lo + ((i - m_lo) % T + T) % T;   // first lag >= m_lo owned by i
+        float tl[KT > 0 ? KT : 1];
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const int m = m_first + k * T;
+            float acc = 0.f;
+            if (m < N) {
+                const int base = m - (N - kd);
+                for (int t = 0; t < N - m; ++t)
+                    acc += cabs2(csub(tail[(t + base) * QT + ql], head[t * QT + ql]));
+                acc *= inv[m];
+            }
+            tl[k] = acc;
+        }
+        if constexpr (KT > 0) __syncthreads();   // head and tail read: the transforms take xs
 
         // ---- odd bins: L-point DFT of g(t) e^{-i pi t / L}; |.|^2 parked in ab
 #pragma unroll
@@ -1588,34 +1626,32 @@ temporal_sf_small_kernel(const float2* __restrict__ spec, float* __restrict__ D,
         }
         __syncthreads();   // prefix reads done: the exchange buffer now stages D
 
-        // ---- stage D as [q][m]; the last kd lags (N - m <= kd pairs) come directly from
-        // Eq. 1 by differences of the stored head and tail samples
+        // ---- stage D as [q][m] (the trailing lags from registers), then each warp copies
+        // whole rows out: lanes on consecutive lags
         constexpr int DS = C::DSTRIDE;
 #pragma unroll
         for (int u = 0; u < P; ++u) {
             const int m = i + T * u;
             if (m < N) xf[ql * DS + m] = dv[u];
         }
-        {
-            const int m_lo = (N - kd > 1) ? N - kd : 1;
-            int m = m_lo + ((i - m_lo) % T + T) % T;     // first lag >= m_lo owned by i
-            for (; m < N; m += T) {
-                float acc = 0.f;
-                const int base = m - (N - kd);
-                for (int t = 0; t < N - m; ++t)
-                    acc += cabs2(csub(tail[(t + base) * QT + ql], head[t * QT + ql]));
-                xf[ql * DS + m] = acc * inv[m];
-            }
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const int m = m_first + k * T;
+            if (m < N) xf[ql * DS + m] = tl[k];
         }
         __syncthreads();
-        for (int r = 0; r < QT; ++r) {
-            const int64_t sr = q0 + tile * QT + r;
-            if (sr >= q1) break;
-            float* drow = D + (int64_t)public_q((int)sr, a) * N;
-            for (int m = tid; m < N; m += NT) {
-                const float d = xf[r * DS + m];
-                bad |= !isfinite(d);
-                drow[m] = d;
+        {
+            const int64_t left = q1 - (q0 + tile * QT);
+            const int nr = left < QT ? (int)left : QT;
+            const int lane = tid & 31;
+#pragma unroll 2
+            for (int r = tid >> 5; r < nr; r += NT / 32) {
+                float* drow = D + (int64_t)public_q((int)(q0 + tile * QT + r), a) * N;
+                for (int m = lane; m < N; m += 32) {
+                    const float d = xf[r * DS + m];
+                    bad |= !isfinite(d);
+                    drow[m] = d;
+                }
             }
         }
         __syncthreads();
@@ -1819,7 +1855,12 @@ ddm_status launch_small(const ddm_plan_s* p, const float2* spec, float* D, cudaS
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
         cudaSuccess)
         return DDM_ERR_CUDA;
-    const int64_t grid = a.n_tiles < p->n_sm ? a.n_tiles : p->n_sm;
+    if (C::CTAS_PER_SM > 1 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return DDM_ERR_CUDA;
+    const int64_t slots = (int64_t)C::CTAS_PER_SM * p->n_sm;
+    const int64_t grid = a.n_tiles < slots ? a.n_tiles : slots;
     k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(spec, D, a);
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
