@@ -393,12 +393,20 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
     tc_fence_before();
     __syncthreads();   // the only CTA-wide barrier before the end: the groups run on their own
     tc_fence_after();
-    // this thread's tensor-memory columns: the sequence at t_seq, Re C at t_rec
+    // this thread's tensor-memory columns: the sequence at t_seq, Re C at t_rec, and at t_inv
+    // the normalisations 1 / (N - m) of its lags m = i + T u (the same for every tile)
     const uint32_t t_seq = tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(warp >> 2) * 128u;
     const uint32_t t_rec = t_seq + 64u;
+    const uint32_t t_inv = t_seq + 96u;
 
     const int ql = tg % QG;
     const int i = tg / QG;
+    {
+        float iv[P];
+#pragma unroll
+        for (int u = 0; u < P; ++u) iv[u] = inv[i + T * u];
+        tmem_st32(t_inv, iv);
+    }
     const int lane = tid & 31, wg = tg >> 5;
     const SyncGroup<GT> sync{bar_id};
     const AddrPaddedInterleaved<QG, T> xaddr{ql};
@@ -645,17 +653,23 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
         tmem_st_wait();
         tmem_ld32(t_rec, dv);                              // Re C(i + T u)
 #pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int m = i + T * u;
-            float d = 0.f;
-            if (m > 0 && m < N - kd) {
-                const float p1 = ab[(base2 - u * (T + 1)) * QG + ql];
-                const float p2 = total - ab[(base1 + u * (T + 1)) * QG + ql];
-                d = (p1 + p2 - 2.f * dv[u]) * inv[m];
-                chk = fmaf(d, 0.f, chk);
+        for (int h = 0; h < 2; ++h) {
+            float iv[16];
+            tmem_ld16(t_inv + 16u * h, iv);                // 1 / (N - m)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int u = 16 * h + k;
+                const int m = i + T * u;
+                float d = 0.f;
+                if (m > 0 && m < N - kd) {
+                    const float p1 = ab[(base2 - u * (T + 1)) * QG + ql];
+                    const float p2 = total - ab[(base1 + u * (T + 1)) * QG + ql];
+                    d = (p1 + p2 - 2.f * dv[u]) * iv[k];
+                    chk = fmaf(d, 0.f, chk);
+                }
+                dv[u] = d;
+                if ((u & 7) == 7) hoist_fence();
             }
-            dv[u] = d;
-            if ((u & 7) == 7) hoist_fence();
         }
         sync();   // reads of S done: ab takes the D rows
 
@@ -1361,8 +1375,7 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
 }
 
 // =====================================================================================
-// L <= 256: one group per CTA, per-thread loads; two CTAs per SM at L = 128, 256 and
-// L <= 16 (shared memory), one at L = 32, 64
+// L <= 256: one group per CTA, per-thread loads; two CTAs per SM
 // =====================================================================================
 // The first and last kd samples of each wave vector go through the exchange buffer before
 // the transforms need it, and the trailing lags are taken from them there; the D rows are
@@ -1386,8 +1399,15 @@ struct TShape {
     static constexpr size_t OFF_XS = (OFF_INV + (size_t)L * sizeof(float) + 1023) & ~size_t(1023);
     static constexpr size_t OFF_AB = OFF_XS + (size_t)L * QT * sizeof(float2);
     static constexpr size_t OFF_MU = OFF_AB + (size_t)L * QT * sizeof(float);
-    static constexpr size_t OFF_RED = OFF_MU + (size_t)QT * sizeof(float2);
-    static constexpr size_t BYTES = OFF_RED + (size_t)RED * QT * sizeof(float);
+    // at L = 64 the mean's partials and the prefix sums' row totals live in the upper half of
+    // the exchange buffer (free in both phases: the power sums use its lower half as floats),
+    // which makes room for a second CTA per SM (512^2 x 64: 0.114 -> 0.085 ms); at L = 32 the
+    // same move measured slower than one CTA per SM with the registers of a whole SM half
+    static constexpr bool RED_IN_XS = (L == 64);
+    static constexpr size_t OFF_RED = RED_IN_XS ? OFF_XS + (size_t)L * QT * sizeof(float)
+                                                : OFF_MU + (size_t)QT * sizeof(float2);
+    static constexpr size_t BYTES = RED_IN_XS ? OFF_MU + (size_t)QT * sizeof(float2)
+                                              : OFF_RED + (size_t)RED * QT * sizeof(float);
     static_assert(L <= 256 && QT >= 32, "per-thread-load kernel: L <= 256");
     static_assert(BYTES <= 232448, "temporal kernel shared memory exceeds 227 KB");
     static_assert((size_t)QT * DSTRIDE <= (size_t)2 * L * QT, "D staging must fit the exchange buffer");
