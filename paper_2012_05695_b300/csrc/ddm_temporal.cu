@@ -1101,11 +1101,15 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
 
 // =====================================================================================
 // L = 16384 (N up to 16384, M = 32768): one wave vector per 512-thread CTA.  Its time
-// sequence (128 KB) and the transform's exchange (128 KB) cannot share shared memory, so
-// the sequence goes straight from global memory (L2) into registers, three times (odd
-// bins, even bins, power sums); shared memory holds the exchange, the parked |X_odd|^2
-// and small twiddle tables.  Pass-1 twiddles from two 2.5 KB tables (w^j = hi[j / 64]
-// lo[j mod 64]) instead of a 32 KB quarter wave.
+// sequence (128 KB) and the transform's exchange (128 KB) cannot share shared memory: the
+// sequence arrives by TMA in chunks of 256 frames (boxes of two neighbouring wave vectors,
+// 16 bytes x 256 rows: the narrowest box a TMA row allows) through a ring of 16 stages,
+// each thread takes its samples from there into registers and keeps the mean-removed
+// sequence in tensor memory (then |X_odd|^2 and Re C: 128 columns per thread).  The first
+// round of the next wave vector's chunks is issued as soon as the current one has been
+// read, and lands while this one is transformed.  Shared memory holds the exchange, the
+// ring, a 32-sample head and tail for the trailing lags and small twiddle tables (pass-1
+// twiddles from two 2.5 KB tables, w^j = hi[j / 64] lo[j mod 64]).
 // =====================================================================================
 template <int L_>
 struct TwiddleTwoLevel {
@@ -1131,7 +1135,16 @@ struct XLShape {
     static constexpr size_t OFF_XS = (OFF_RED + (size_t)NWG * 16 + 1023) & ~size_t(1023);
     static constexpr size_t XS_ELEMS = (size_t)P * (T + PAD);                // handover; >= L
     static constexpr size_t OFF_HT = OFF_XS + XS_ELEMS * sizeof(float2);    // 32 head + 32 tail
-    static constexpr size_t BYTES = OFF_HT + 64 * sizeof(float2);
+    // the TMA ring: NST stages of one box [256 frames][2 wave vectors] each
+    static constexpr int BOX_T = 256, NCH = L / BOX_T, NST = 16, NROUND = NCH / NST;
+    static constexpr uint32_t BOX_BYTES = BOX_T * 2 * sizeof(float2);
+    static constexpr size_t OFF_RING = OFF_HT + 64 * sizeof(float2);
+    static constexpr size_t BYTES = OFF_RING + (size_t)NST * BOX_BYTES;
+    static_assert(NT == 2 * BOX_T && NST % 2 == 0 && NCH % NST == 0,
+                  "thread i's sample t = i + T u sits in chunk (i / 256) + 2 u: round u / 8, "
+                  "stage (i / 256) + 2 (u mod 8)");
+    static_assert(NST == 2 * (P / NROUND), "a round holds 8 of each thread's 32 samples");
+    static_assert(OFF_RING % 128 == 0, "TMA destinations 128-byte aligned");
     static_assert(XS_ELEMS >= (size_t)L && (size_t)(L + L / 32) * sizeof(float) <= XS_ELEMS * sizeof(float2),
                   "exchange holds the transform and the padded power sums");
     static_assert(BYTES + 1024 <= 233472, "one CTA per SM");
@@ -1147,9 +1160,9 @@ struct XLTables {
 };
 
 __global__ void __launch_bounds__(XLShape::NT, 1)
-temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TArgs a, XLTables tb) {
+temporal_sf_xl_kernel(float* __restrict__ D, TArgs a, XLTables tb, const __grid_constant__ CUtensorMap tmap) {
     using C = XLShape;
-    constexpr int L = C::L, P = C::P, T = C::T, R = C::R, NWG = C::NWG;
+    constexpr int L = C::L, P = C::P, T = C::T, R = C::R, NWG = C::NWG, NST = C::NST, BOX_T = C::BOX_T;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2* lo = reinterpret_cast<float2*>(smem_raw + C::OFF_LO);
     float2* hi = reinterpret_cast<float2*>(smem_raw + C::OFF_HI);
@@ -1161,11 +1174,17 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
     float* xf = reinterpret_cast<float*>(xs);
     float2* head = reinterpret_cast<float2*>(smem_raw + C::OFF_HT);   // g(t), t < 32
     float2* tail = head + 32;                                          // g(N - 32 + t), t < 32
+    float2* ring = reinterpret_cast<float2*>(smem_raw + C::OFF_RING);
     __shared__ uint32_t tmem_slot;
+    __shared__ uint64_t ring_bar[C::NST];
 
     const int i = threadIdx.x;
     const int lane = i & 31, wg = i >> 5;
     if (wg == 0) seq_tmem_alloc(&tmem_slot);
+    if (i == 0) {
+        for (int st = 0; st < NST; ++st) mbar_init(&ring_bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     for (int k = i; k < 64; k += C::NT) lo[k] = tb.lo[k];
     for (int k = i; k < L / 64; k += C::NT) hi[k] = tb.hi[k];
     for (int k = i; k < T; k += C::NT) twi[k] = tb.inner[k];
@@ -1181,9 +1200,30 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
     const int m_lo = N - kd;
     const int m_tail = m_lo + ((i - m_lo) % T + T) % T;    // this thread's trailing lag, if < N
     float chk = 0.f;
+    // the ring: chunk c (frames 256 c .. 256 c + 255) of a wave vector in stage c mod NST;
+    // chunks from nch on hold no frame (N <= 256 nch) and are neither copied nor waited for
+    const int nch = (N + BOX_T - 1) / BOX_T;
+    bool timed_out = false;
+    // copies of round r of stored wave vector `tile` (relative to q0); the box holds the
+    // pair of wave vectors (2 k, 2 k + 1) that contains it (q0 and n_q are even)
+    auto issue_round = [&](int64_t tile, int r) {
+        fence_proxy_async();
+        for (int st = 0; st < NST; ++st) {
+            const int c = r * NST + st;
+            if (c >= nch) break;
+            mbar_expect_tx(&ring_bar[st], C::BOX_BYTES);
+            if (a.blocked)
+                tma_load_3d(ring + (size_t)st * BOX_T * 2, &tmap, (int)(2 * ((tile & 15) & ~1)), c * BOX_T,
+                            (int)(tile >> 4), &ring_bar[st]);
+            else
+                tma_load_2d(ring + (size_t)st * BOX_T * 2, &tmap, (int)(2 * ((a.q0 + tile) & ~(int64_t)1)),
+                            c * BOX_T, &ring_bar[st]);
+        }
+    };
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (i == 0 && blockIdx.x < a.n_tiles) issue_round(blockIdx.x, 0);
     // tensor-memory columns of this thread (lane 32 (warp mod 4) + lane, 128 columns per warp
     // of a lane quarter): the mean-removed sequence, |X_odd|^2, Re C
     const uint32_t t_seq = tmem_slot + ((uint32_t)(32 * (wg & 3)) << 16) + (uint32_t)(wg >> 2) * 128u;
@@ -1191,21 +1231,47 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
 
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
         const int64_t sq = a.q0 + tile;                    // stored wave vector
-        // x(t) = xg[t * nq]: the [t][q] spectrum, or its 16-wave-vector blocks [b][t][16]
-        const float2* xg = a.blocked ? spec + (tile >> 4) * (int64_t)N * 16 + (tile & 15) : spec + sq;
-        const int64_t nq = a.blocked ? 16 : a.n_q;
+        const int half = (int)(sq & 1);                    // its column in the ring's boxes
+        const int hb = i / BOX_T;                          // thread i reads the chunks hb + 2 u
+        // stage st completes once per round that uses it: ceil((nch - st) / NST) times per
+        // wave vector, so its parity in round r follows from the wave vectors done before
+        const uint32_t done = (uint32_t)((tile - blockIdx.x) / gridDim.x);
+        uint32_t pending = 0, pending_par = 0;             // stages this thread gave up on
         __syncthreads();                                   // previous wave vector's reads done
-        // ---- time sequence (thread i holds t = i + T u), read from global memory once; its
-        // first and last 32 samples for the trailing lags; its mean
+        // ---- time sequence (thread i holds t = i + T u) from the ring, round by round (8 of
+        // a thread's samples per round); its first and last 32 samples for the trailing lags;
+        // its mean
         float2 v[P];
         float2 part = make_float2(0.f, 0.f);
+        bool ok = true;
 #pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int t = i + T * u;
-            v[u] = (t < N) ? __ldg(xg + (int64_t)t * nq) : make_float2(0.f, 0.f);
-            part = cadd(part, v[u]);
-            if (t < 32) head[t] = v[u];
-            if (t >= N - 32 && t < N) tail[t - (N - 32)] = v[u];
+        for (int r = 0; r < C::NROUND; ++r) {
+            if (r > 0) {
+                // every thread is done with the previous round's stages before they refill
+                if (__syncthreads_or(!ok)) break;
+                if (i == 0) issue_round(tile, r);
+            }
+            // this thread's stages of the round: hb, hb + 2, ..., hb + 14 (chunks hb + 2 u)
+#pragma unroll 1
+            for (int st = hb; st < NST; st += 2) {
+                if (r * NST + st >= nch) break;
+                const uint32_t par = (done * (uint32_t)((nch - st + NST - 1) / NST) + (uint32_t)r) & 1u;
+                if (!mbar_wait_bounded(&ring_bar[st], par)) {
+                    ok = false;
+                    pending |= 1u << st;
+                    pending_par |= par << st;
+                }
+            }
+            const float2* rb = ring + (size_t)(hb * BOX_T + (i & (BOX_T - 1))) * 2 + half;
+#pragma unroll
+            for (int k = 0; k < P / C::NROUND; ++k) {
+                const int u = r * (P / C::NROUND) + k;
+                const int t = i + T * u;                   // in chunk hb + 2 u = r NST + hb + 2 k
+                v[u] = (ok && t < N) ? rb[(size_t)k * 2 * BOX_T * 2] : make_float2(0.f, 0.f);
+                part = cadd(part, v[u]);
+                if (t < 32) head[t] = v[u];
+                if (t >= N - 32 && t < N) tail[t - (N - 32)] = v[u];
+            }
         }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1213,7 +1279,18 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
             part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
         }
         if (lane == 0) red2[wg] = part;
-        __syncthreads();
+        // a copy that never landed ends the kernel for the whole CTA (status bit 2); the copies
+        // this thread gave up on get a last bounded chance to land before the CTA's shared
+        // memory goes away
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            for (int st = 0; st < NST; ++st)
+                if ((pending >> st) & 1u) mbar_wait_bounded(&ring_bar[st], (pending_par >> st) & 1u);
+            break;
+        }
+        // the ring is free: the next wave vector's first round lands while this one is
+        // transformed
+        if (i == 0 && tile + gridDim.x < a.n_tiles) issue_round(tile + gridDim.x, 0);
         float2 mean = make_float2(0.f, 0.f);
 #pragma unroll
         for (int w = 0; w < NWG; ++w) mean = cadd(mean, red2[w]);
@@ -1366,6 +1443,7 @@ temporal_sf_xl_kernel(const float2* __restrict__ spec, float* __restrict__ D, TA
             drow[m] = d;
         }
     }
+    if (timed_out && i == 0) atomicOr(a.status, 2u);
     if (chk != chk) atomicOr(a.status, 1u);
     tmem_st_wait();
     tc_fence_before();
@@ -1844,7 +1922,12 @@ ddm_status launch_xl(const ddm_plan_s* p, const float2* spec, float* D, cudaStre
     bool ok = true;
     const float2* blk = blocked_copy(p, spec, s, pre_blocked, &ok);
     if (!ok) return DDM_ERR_CUDA;
-    if (blk) spec = blk;
+    if ((reinterpret_cast<uintptr_t>(blk ? blk : spec) & 15) != 0) return DDM_ERR_INVALID_ARG;
+    CUtensorMap tmap;                             // boxes of 2 wave vectors x 256 frames
+    memset(&tmap, 0, sizeof(tmap));
+    if (blk ? !make_blocked_map(&tmap, blk, (p->q1 - p->q0 + 15) / 16, p->d.N, 2)
+            : !make_spectrum_map(&tmap, spec, p->n_q, p->d.N, 2))
+        return DDM_ERR_CUDA;
     TArgs a;
     fill_args(a, p, D, 1);
     a.blocked = blk != nullptr;
@@ -1862,7 +1945,7 @@ ddm_status launch_xl(const ddm_plan_s* p, const float2* spec, float* D, cudaStre
     tb.hi = tb.lo + 64;
     tb.inner = p->tw_tin;
     const int64_t grid = a.n_tiles < p->n_sm ? a.n_tiles : p->n_sm;
-    k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(spec, D, a, tb);
+    k<<<(unsigned)grid, C::NT, C::BYTES, s>>>(D, a, tb, tmap);
     return cudaGetLastError() == cudaSuccess ? DDM_OK : DDM_ERR_CUDA;
 }
 
