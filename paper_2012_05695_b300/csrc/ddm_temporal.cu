@@ -1052,7 +1052,7 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
                 const int ta = N - 1 - m, tb2 = m - 1;
                 const float p1 = xf[(ta + (ta >> 5)) * QG + ql];
                 const float p2 = total - xf[(tb2 + (tb2 >> 5)) * QG + ql];
-                d = (p1 + p2 - 2.f * dv[u]) * __frcp_rn((float)(N - m));
+                d = __fdividef(p1 + p2 - 2.f * dv[u], (float)(N - m));   // within 2 ulp
                 chk = fmaf(d, 0.f, chk);
             }
             dv[u] = d;
@@ -1435,7 +1435,7 @@ temporal_sf_xl_kernel(float* __restrict__ D, TArgs a, XLTables tb, const __grid_
                 const int ta = N - 1 - m;
                 const float p1 = ta < h ? xf[ta + (ta >> 5)] : total - xf[(ta + 1) + ((ta + 1) >> 5)];
                 const float p2 = m >= h ? xf[m + (m >> 5)] : total - xf[(m - 1) + ((m - 1) >> 5)];
-                d = (p1 + p2 - 2.f * rcv[u]) * __frcp_rn((float)(N - m));
+                d = __fdividef(p1 + p2 - 2.f * rcv[u], (float)(N - m));  // within 2 ulp
                 chk = fmaf(d, 0.f, chk);
             } else if (m >= m_lo) {
                 d = tl;                                    // m == m_tail
