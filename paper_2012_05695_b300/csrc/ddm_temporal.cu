@@ -1987,11 +1987,13 @@ ddm_status launch_temporal(const ddm_plan_s* p, const float2* spec, float* D, cu
         case 6: return launch_small<6>(p, spec, D, s);
         case 7: return launch_small<7>(p, spec, D, s);
         case 8: return launch_small<8>(p, spec, D, s);
-        // groups per CTA: the choice that gives 64-byte TMA rows (QG = 8 wave vectors) at
-        // both lengths.  Measured at 512x512x1024 (L = 1024): 1 group of 512 threads (128-byte
-        // rows, lockstep) 1.13 ms, 2 groups 1.05 ms, 4 groups (32-byte rows) 1.15 ms.
+        // groups per CTA.  Measured at 512x512x1024 (L = 1024) when each tile was copied three
+        // times: 1 group of 512 threads (128-byte TMA rows, lockstep) 1.13 ms, 2 groups 1.05 ms,
+        // 4 groups (32-byte rows) 1.15 ms.  With one copy per tile (tensor-memory stash) four
+        // groups of 128 threads lead by about 1 % (0.773 against 0.781 ms); at L = 512 eight
+        // groups of 64 do not (0.377 against 0.375 ms), four stay.
         case 9: return fix ? launch_grouped<9, true, 4>(p, spec, D, s) : launch_grouped<9, false, 4>(p, spec, D, s);
-        case 10: return fix ? launch_grouped<10, true, 2>(p, spec, D, s) : launch_grouped<10, false, 2>(p, spec, D, s);
+        case 10: return fix ? launch_grouped<10, true, 4>(p, spec, D, s) : launch_grouped<10, false, 4>(p, spec, D, s);
         case 11: return fix ? launch_long<11, true>(p, spec, D, s, pre_blocked) : launch_long<11, false>(p, spec, D, s, pre_blocked);
         case 12: return fix ? launch_long<12, true>(p, spec, D, s, pre_blocked) : launch_long<12, false>(p, spec, D, s, pre_blocked);
         case 13: return fix ? launch_long<13, true>(p, spec, D, s, pre_blocked) : launch_long<13, false>(p, spec, D, s, pre_blocked);
