@@ -19,6 +19,22 @@
 namespace ddm {
 namespace {
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// A bounded wait on an mbarrier phase: about two seconds of polling (SM clock cycles), then
+// false.
+__device__ __forceinline__ bool mbar_wait_bounded_m(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > 4000000000LL) return false;
+    }
+}
+
 // exchange row stride: the smallest r >= T with r QT = QT (mod 16), so that in pass 2 the
 // QT-lane groups of consecutive k1 tile the 16 bank pairs (8-byte elements)
 constexpr int mixed_row(int T, int QT) {
@@ -42,6 +58,10 @@ struct MShape {
     static constexpr size_t OUT = STG;
     static constexpr size_t XE = XCH > STG ? (XCH > OUT ? XCH : OUT) : (STG > OUT ? STG : OUT);
     static constexpr size_t BYTES = sizeof(float2) * (XE + (size_t)N);
+    // bulk staging of uint16 rows (row kernel): the 2 QT rows of the frame and the same rows
+    // of frame 0, each at a pitch of its bytes plus a 16-byte pad, inside the exchange region
+    static constexpr int RAW_PITCH = ((N * 2 + 15) / 16) * 16 + 16;
+    static constexpr bool BULK_FITS = (N * 2) % 16 == 0 && (size_t)4 * QT * RAW_PITCH <= XE * sizeof(float2);
     static_assert(P <= 40 && T <= 50 && QT >= 1, "mixed-radix shapes");
     static_assert(P <= T, "pass 2 gives each k1 < P its own thread: P <= T");
 };
@@ -88,77 +108,131 @@ __device__ __forceinline__ void load4(const float* p, float (&f)[4]) {
     f[3] = r.w;
 }
 
-template <int P, int T, typename In, bool VEC>
+// STAGE: 0 one pixel per load; 1 four pixels per load (frames aligned to four pixels);
+// 2 (uint16 frames, 16-byte aligned rows) each row of the CTA and of frame 0 by one
+// cp.async.bulk copy into shared memory, converted from there straight into registers
+template <int P, int T, typename In, int STAGE>
 __global__ void __launch_bounds__(256)
 row_mixed_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H, size_t frame_stride,
-                 int subtract_ref, const float2* __restrict__ tw_g) {
+                 int subtract_ref, const float2* __restrict__ tw_g, unsigned* status) {
     using C = MShape<P, T>;
     constexpr int W = C::N, QT = C::QT, NT = C::NT, WS = C::WS;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2* xs = reinterpret_cast<float2*>(smem_raw);
     float2* tw = xs + C::XE;
     const int tid = threadIdx.x;
-    for (int k = tid; k < W; k += NT) tw[k] = tw_g[k];
     const int t = blockIdx.y;
     const int pair0 = blockIdx.x * QT;
     const int npairs = min(QT, H / 2 - pair0);
     const In* src = frames + ((size_t)t * H + 2 * pair0) * W;
     const In* ref = frames + (size_t)(2 * pair0) * W;
-    if constexpr (VEC) {
-        // four pixels of rows 2q and 2q + 1 per thread and iteration: a warp moves 256 B (uint16)
-        // or 512 B (float) of each row per load, enough bytes in flight to cover HBM latency.  The
-        // 32 B of four staged pairs go out as two 16 B halves; a quad whose 32 B chunk lies at an
-        // odd multiple of 128 B writes its upper half first, so that each store by a warp meets all
-        // 32 banks.  The differences of integers below 2^16 are exact in float, as on the scalar path.
-        static_assert(W % 4 == 0 && WS % 4 == 0, "vector staging: W and WS multiples of 4");
-        constexpr int W4 = W / 4;
-#pragma unroll 4
-        for (int e = tid; e < npairs * W4; e += NT) {
-            const int q = e / W4, x4 = e - q * W4, x = 4 * x4;
-            const size_t ia = (size_t)(2 * q) * W + x, ib = ia + W;
-            float a[4], b[4];
-            load4(src + ia, a);
-            load4(src + ib, b);
-            if (subtract_ref) {
-                float ra[4], rb[4];
-                load4(ref + ia, ra);
-                load4(ref + ib, rb);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    a[j] -= ra[j];
-                    b[j] -= rb[j];
-                }
-            }
-            const float4 lo = make_float4(a[0], b[0], a[1], b[1]), hi = make_float4(a[2], b[2], a[3], b[3]);
-            float4* dst = reinterpret_cast<float4*>(xs + q * WS + x);
-            const int h = ((q * (WS / 4) + x4) >> 2) & 1;
-            dst[h] = h ? hi : lo;
-            dst[1 - h] = h ? lo : hi;
-        }
-    } else {
-#pragma unroll 4
-        for (int e = tid; e < npairs * W; e += NT) {        // 4 iterations of loads in flight
-            const int q = e / W, x = e - q * W;
-            const size_t ia = (size_t)(2 * q) * W + x, ib = ia + W;
-            float a, b;
-            if constexpr (sizeof(In) == 2) {
-                a = (float)((int)__ldg(src + ia) - (subtract_ref ? (int)__ldg(ref + ia) : 0));
-                b = (float)((int)__ldg(src + ib) - (subtract_ref ? (int)__ldg(ref + ib) : 0));
-            } else {
-                a = subtract_ref ? __ldg(src + ia) - __ldg(ref + ia) : __ldg(src + ia);
-                b = subtract_ref ? __ldg(src + ib) - __ldg(ref + ib) : __ldg(src + ib);
-            }
-            xs[q * WS + x] = make_float2(a, b);
-        }
-    }
-    __syncthreads();
     const int ql = tid % QT, i = tid / QT;
     const bool live = i < T;
     const bool active = live && ql < npairs;
     float2 v[P], w[T];
+    if constexpr (STAGE == 2) {
+        static_assert(sizeof(In) == 2 && C::BULK_FITS, "bulk staging: uint16 rows of 16-byte multiples");
+        constexpr int RP = C::RAW_PITCH;
+        constexpr uint32_t ROWB = (uint32_t)W * 2u;
+        __shared__ uint64_t bar;
+        unsigned char* rawf = smem_raw;                               // rows of this frame
+        unsigned char* rawr = smem_raw + (size_t)2 * QT * RP;         // the same rows of frame 0
+        const uint32_t nrows = (uint32_t)(2 * npairs);
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)),
+                         "r"((subtract_ref ? 2u : 1u) * nrows * ROWB) : "memory");
+        }
+        for (int k = tid; k < W; k += NT) tw[k] = tw_g[k];
+        __syncthreads();                                   // the barrier expects the bytes
+        for (uint32_t r = tid; r < nrows; r += NT) {
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                ::"r"(smem_addr(rawf + (size_t)r * RP)), "l"(src + (size_t)r * W), "r"(ROWB),
+                "r"(smem_addr(&bar)) : "memory");
+            if (subtract_ref)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                    ::"r"(smem_addr(rawr + (size_t)r * RP)), "l"(ref + (size_t)r * W), "r"(ROWB),
+                    "r"(smem_addr(&bar)) : "memory");
+        }
+        const bool ok = mbar_wait_bounded_m(&bar, 0);
+        // rows 2 ql and 2 ql + 1 as the real and imaginary parts; integer differences below
+        // 2^16 are exact in float, as on the other staging paths
+        const uint16_t* fa = reinterpret_cast<const uint16_t*>(rawf + (size_t)(2 * ql) * RP);
+        const uint16_t* ra = reinterpret_cast<const uint16_t*>(rawr + (size_t)(2 * ql) * RP);
 #pragma unroll
-    for (int u = 0; u < P; ++u) v[u] = active ? xs[ql * WS + i + T * u] : make_float2(0.f, 0.f);
-    __syncthreads();                                        // staging read: xs becomes the exchange
+        for (int u = 0; u < P; ++u) {
+            const int x = i + T * u;
+            float a = 0.f, b = 0.f;
+            if (active && ok) {
+                a = (float)((int)fa[x] - (subtract_ref ? (int)ra[x] : 0));
+                b = (float)((int)fa[RP / 2 + x] - (subtract_ref ? (int)ra[RP / 2 + x] : 0));
+            }
+            v[u] = make_float2(a, b);
+        }
+        if (!ok) {
+            // report it (status bit 2); the copies get a last bounded chance to land before
+            // the region becomes the exchange
+            if (tid == 0) atomicOr(status, 2u);
+            mbar_wait_bounded_m(&bar, 0);
+        }
+        __syncthreads();                                   // staging read: xs becomes the exchange
+    } else {
+        for (int k = tid; k < W; k += NT) tw[k] = tw_g[k];
+        if constexpr (STAGE == 1) {
+            // four pixels of rows 2q and 2q + 1 per thread and iteration: a warp moves 256 B (uint16)
+            // or 512 B (float) of each row per load, enough bytes in flight to cover HBM latency.  The
+            // 32 B of four staged pairs go out as two 16 B halves; a quad whose 32 B chunk lies at an
+            // odd multiple of 128 B writes its upper half first, so that each store by a warp meets all
+            // 32 banks.  The differences of integers below 2^16 are exact in float, as on the scalar path.
+            static_assert(W % 4 == 0 && WS % 4 == 0, "vector staging: W and WS multiples of 4");
+            constexpr int W4 = W / 4;
+#pragma unroll 4
+            for (int e = tid; e < npairs * W4; e += NT) {
+                const int q = e / W4, x4 = e - q * W4, x = 4 * x4;
+                const size_t ia = (size_t)(2 * q) * W + x, ib = ia + W;
+                float a[4], b[4];
+                load4(src + ia, a);
+                load4(src + ib, b);
+                if (subtract_ref) {
+                    float ra[4], rb[4];
+                    load4(ref + ia, ra);
+                    load4(ref + ib, rb);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        a[j] -= ra[j];
+                        b[j] -= rb[j];
+                    }
+                }
+                const float4 lo = make_float4(a[0], b[0], a[1], b[1]), hi = make_float4(a[2], b[2], a[3], b[3]);
+                float4* dst = reinterpret_cast<float4*>(xs + q * WS + x);
+                const int h = ((q * (WS / 4) + x4) >> 2) & 1;
+                dst[h] = h ? hi : lo;
+                dst[1 - h] = h ? lo : hi;
+            }
+        } else {
+#pragma unroll 4
+            for (int e = tid; e < npairs * W; e += NT) {        // 4 iterations of loads in flight
+                const int q = e / W, x = e - q * W;
+                const size_t ia = (size_t)(2 * q) * W + x, ib = ia + W;
+                float a, b;
+                if constexpr (sizeof(In) == 2) {
+                    a = (float)((int)__ldg(src + ia) - (subtract_ref ? (int)__ldg(ref + ia) : 0));
+                    b = (float)((int)__ldg(src + ib) - (subtract_ref ? (int)__ldg(ref + ib) : 0));
+                } else {
+                    a = subtract_ref ? __ldg(src + ia) - __ldg(ref + ia) : __ldg(src + ia);
+                    b = subtract_ref ? __ldg(src + ib) - __ldg(ref + ib) : __ldg(src + ib);
+                }
+                xs[q * WS + x] = make_float2(a, b);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < P; ++u) v[u] = active ? xs[ql * WS + i + T * u] : make_float2(0.f, 0.f);
+        __syncthreads();                                        // staging read: xs becomes the exchange
+    }
     fft_mixed<P, T>(v, w, i, ql, live, xs, tw);
     if (live && i < P) {
 #pragma unroll
@@ -240,14 +314,19 @@ col_mixed_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride, const f
 template <int P, int T, typename In>
 cudaError_t rows_t(const ddm_plan_s* p, const void* frames, float2* spec, cudaStream_t s) {
     using C = MShape<P, T>;
-    // vector staging needs the frames 4-pixel aligned (every row offset is: W is a multiple of 4)
-    const bool vec = reinterpret_cast<uintptr_t>(frames) % (4 * sizeof(In)) == 0;
-    auto k = vec ? row_mixed_kernel<P, T, In, true> : row_mixed_kernel<P, T, In, false>;
+    // vector staging needs the frames 4-pixel aligned (every row offset is: W is a multiple of
+    // 4); bulk staging uint16 frames 16-byte aligned with rows of a multiple of 16 bytes
+    const uintptr_t a = reinterpret_cast<uintptr_t>(frames);
+    const bool vec = a % (4 * sizeof(In)) == 0;
+    auto k = vec ? row_mixed_kernel<P, T, In, 1> : row_mixed_kernel<P, T, In, 0>;
+    if constexpr (sizeof(In) == 2 && C::BULK_FITS) {
+        if (a % 16 == 0) k = row_mixed_kernel<P, T, In, 2>;
+    }
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
     if (e != cudaSuccess) return e;
     dim3 grid((p->d.H / 2 + C::QT - 1) / C::QT, p->d.N);
     k<<<grid, C::NT, C::BYTES, s>>>((const In*)frames, spec, p->d.H, (size_t)p->n_q, p->d.subtract_ref,
-                                     p->mix_w.tw);
+                                     p->mix_w.tw, p->dev_status);
     return cudaGetLastError();
 }
 

@@ -94,25 +94,33 @@ def test_spatial_fft_non_power_of_two_without_reference_subtraction():
     (600, 800, "u16", 1), (480, 640, "f32", 1), (540, 900, "u16", 0), (384, 1000, "f32", 0),
 ])
 def test_mixed_rows_unaligned_frames_match_aligned(H, W, dtype, sub):
-    """The row kernels stage four pixels per load when the frames pointer allows it and one
-    otherwise; one element past an aligned allocation takes the scalar path.  Both do the same
-    arithmetic, so their spectra agree bit for bit, and both match the oracle's DFT."""
+    """The row kernels stage uint16 rows by bulk copies when the frames are 16-byte aligned
+    (and a row is a multiple of 16 bytes), four pixels per load when the frames pointer is
+    aligned to four pixels, and one pixel per load otherwise; frames one and four elements
+    past an aligned allocation take the other paths.  All do the same arithmetic, so their
+    spectra agree bit for bit, and all match the oracle's DFT."""
     import torch
     N = 3
     frames = _frames(N, H, W, dtype, seed=W + 7 * sub)
-    host = np.empty(frames.size + 1, dtype=frames.dtype)
-    host[1:] = frames.ravel()
-    buf = to_device(host)
-    shifted = buf[1:]
-    assert shifted.data_ptr() % (4 * shifted.element_size()) != 0
     plan = ddm.Plan(H, W, N, dtype=dtype, subtract_ref=sub)
+    inputs = [to_device(frames)]
+    # uint16: bulk (16-byte aligned), four-pixel (8-byte aligned) and one-pixel staging;
+    # float32: four-pixel (16-byte aligned) and one-pixel staging
+    for shift in ((1, 4) if dtype == "u16" else (1,)):
+        host = np.empty(frames.size + shift, dtype=frames.dtype)
+        host[shift:] = frames.ravel()
+        shifted = to_device(host)[shift:]
+        align = 4 * shifted.element_size() if shift == 1 else 16
+        assert shifted.data_ptr() % align != 0
+        inputs.append(shifted)
     specs = []
-    for f in (to_device(frames), shifted):
+    for f in inputs:
         spec = torch.empty(2 * N * plan.n_q, dtype=torch.float32, device="cuda")
         plan.spatial_fft(f, spec)
         specs.append(spec)
     torch.cuda.synchronize()
-    assert torch.equal(specs[0], specs[1])
+    for sp in specs[1:]:
+        assert torch.equal(specs[0], sp)
     s = specs[0].cpu().numpy().view(np.complex64).reshape(N, plan.n_q).astype(np.complex128)
     F = storage_to_plane(s, H, W)
     x = frames.astype(np.float64)
