@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units (not installed).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -134,6 +135,11 @@ struct SpecOut {
 #endif
 };
 
+// A TMA tensor map of float32 elements (no swizzle, zero fill out of bounds, 256-byte L2
+// promotion): dims innermost first, strides in bytes of dimensions 1 .. rank - 1 (multiples
+// of 16), box extents in elements.  False if the driver's encoder is missing or refuses.
+bool encode_f32_tensor_map(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims,
+                           const cuuint64_t* strides, const cuuint32_t* box);
 bool fp64_supported(const ddm_plan_desc& d);
 bool tc_columns_supported(const ddm_plan_desc& d);
 void tc_column_tables(float* out);

@@ -12,6 +12,7 @@
 // Nyquist column unpacked by the block that holds it).
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "ddm_fft.cuh"
 #include "ddm_internal.h"
@@ -62,6 +63,11 @@ struct MShape {
     // of frame 0, each at a pitch of its bytes plus a 16-byte pad, inside the exchange region
     static constexpr int RAW_PITCH = ((N * 2 + 15) / 16) * 16 + 16;
     static constexpr bool BULK_FITS = (N * 2) % 16 == 0 && (size_t)4 * QT * RAW_PITCH <= XE * sizeof(float2);
+    // TMA staging of QT columns (column kernel): NBOX boxes of BOXR rows x QT complex (QT even:
+    // 16-byte multiples), landing [row][QT] in the exchange region, each box at a 128-byte
+    // aligned shared-memory address
+    static constexpr int NBOX = (N + 255) / 256, BOXR = (N + NBOX - 1) / NBOX;
+    static constexpr bool TMA_FITS = QT % 2 == 0 && (BOXR * QT) % 16 == 0 && (size_t)NBOX * BOXR * QT <= XE;
     static_assert(P <= 40 && T <= 50 && QT >= 1, "mixed-radix shapes");
     static_assert(P <= T, "pass 2 gives each k1 < P its own thread: P <= T");
 };
@@ -259,27 +265,59 @@ row_mixed_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H
 
 // ------------------------------------------------------------- columns (H = P T)
 // grid: (ceil(Wh / QT), N); block: NTC (256, or 512 for the wide shapes: 12 columns of T = 40
-// threads, 96-byte row segments).  In place, QT stored columns of one frame.
-template <int P, int T, int NTC>
+// threads, 96-byte row segments).  In place, QT stored columns of one frame.  TMA: the CTA's
+// H x QT block arrives by TMA copies (tensor map over the spectrum as float32
+// [N][H][2 Wh], boxes of BOXR rows x 2 QT floats) instead of per-thread strided loads.
+template <int P, int T, int NTC, bool TMA>
 __global__ void __launch_bounds__(NTC)
 col_mixed_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride, const float2* __restrict__ tw_g,
-                 SpecOut out) {
+                 SpecOut out, const __grid_constant__ CUtensorMap tmap, unsigned* status) {
     using C = MShape<P, T, NTC>;
     constexpr int H = C::N, QT = C::QT, NT = C::NT;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float2* xs = reinterpret_cast<float2*>(smem_raw);
     float2* tw = xs + C::XE;
     const int tid = threadIdx.x;
-    for (int k = tid; k < H; k += NT) tw[k] = tw_g[k];
-    __syncthreads();
     const int ql = tid % QT, i = tid / QT;
     const bool live = i < T;
     const int kx = blockIdx.x * QT + ql;
     const bool valid = live && kx < Wh;
     float2* base = spec + (size_t)blockIdx.y * frame_stride;
     float2 v[P], w[T];
+    if constexpr (TMA) {
+        static_assert(C::TMA_FITS, "TMA staging: QT even, the staged rows fit the exchange region");
+        __shared__ uint64_t bar;
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)),
+                         "r"((uint32_t)(C::NBOX * C::BOXR * QT * sizeof(float2))) : "memory");
 #pragma unroll
-    for (int u = 0; u < P; ++u) v[u] = valid ? base[(size_t)(i + T * u) * Wh + kx] : make_float2(0.f, 0.f);
+            for (int b = 0; b < C::NBOX; ++b)
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4}], [%5];"
+                    ::"r"(smem_addr(xs + (size_t)b * C::BOXR * QT)), "l"(&tmap), "r"(2 * (int)blockIdx.x * QT),
+                    "r"(b * C::BOXR), "r"((int)blockIdx.y), "r"(smem_addr(&bar)) : "memory");
+        }
+        for (int k = tid; k < H; k += NT) tw[k] = tw_g[k];
+        __syncthreads();                                   // the twiddles; the barrier is armed
+        const bool ok = mbar_wait_bounded_m(&bar, 0);
+#pragma unroll
+        for (int u = 0; u < P; ++u) v[u] = (valid && ok) ? xs[(i + T * u) * QT + ql] : make_float2(0.f, 0.f);
+        if (!ok) {
+            // report it (status bit 2); the copies get a last bounded chance to land before the
+            // region becomes the exchange
+            if (tid == 0) atomicOr(status, 2u);
+            mbar_wait_bounded_m(&bar, 0);
+        }
+        __syncthreads();                                   // staging read: xs becomes the exchange
+    } else {
+        for (int k = tid; k < H; k += NT) tw[k] = tw_g[k];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < P; ++u) v[u] = valid ? base[(size_t)(i + T * u) * Wh + kx] : make_float2(0.f, 0.f);
+    }
     fft_mixed<P, T, NTC>(v, w, i, ql, live, xs, tw);
     const bool holds = live && i < P;                       // holds X[i + P k2], k2 < T
     const int t = blockIdx.y;
@@ -333,11 +371,24 @@ cudaError_t rows_t(const ddm_plan_s* p, const void* frames, float2* spec, cudaSt
 template <int P, int T, int NTC = 256>
 cudaError_t cols_t(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecOut out) {
     using C = MShape<P, T, NTC>;
-    auto k = col_mixed_kernel<P, T, NTC>;
+    auto k = col_mixed_kernel<P, T, NTC, false>;
+    // the TMA path needs 16-byte rows and frames (Wh and n_q even) and an aligned spectrum;
+    // it is taken for the 256-thread shapes (600x800x3000 step one 4.75 -> 4.28 ms), not for
+    // the 512-thread ones (1080x1920x256 2.21 -> 2.24 ms)
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    if constexpr (C::TMA_FITS && NTC == 256) {
+        const cuuint64_t dims[3] = {(cuuint64_t)(2 * p->Wh), (cuuint64_t)C::N, (cuuint64_t)p->d.N};
+        const cuuint64_t strides[2] = {(cuuint64_t)p->Wh * sizeof(float2), (cuuint64_t)p->n_q * sizeof(float2)};
+        const cuuint32_t box[3] = {(cuuint32_t)(2 * C::QT), (cuuint32_t)C::BOXR, 1};
+        if (p->Wh % 2 == 0 && p->n_q % 2 == 0 && reinterpret_cast<uintptr_t>(spec) % 16 == 0 &&
+            encode_f32_tensor_map(&tmap, spec, 3, dims, strides, box))
+            k = col_mixed_kernel<P, T, NTC, true>;
+    }
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
     if (e != cudaSuccess) return e;
     dim3 grid((p->Wh + C::QT - 1) / C::QT, p->d.N);
-    k<<<grid, C::NT, C::BYTES, s>>>(spec, p->Wh, (size_t)p->n_q, p->mix_h.tw, out);
+    k<<<grid, C::NT, C::BYTES, s>>>(spec, p->Wh, (size_t)p->n_q, p->mix_h.tw, out, tmap, p->dev_status);
     return cudaGetLastError();
 }
 

@@ -1970,6 +1970,16 @@ ddm_status launch_small(const ddm_plan_s* p, const float2* spec, float* D, cudaS
 
 }  // namespace
 
+bool encode_f32_tensor_map(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims,
+                           const cuuint64_t* strides, const cuuint32_t* box) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || rank < 1 || rank > 5) return false;
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base), dims, strides,
+              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_wait_selftest(unsigned* status, long long cap_cycles, cudaStream_t s) {
     wait_selftest_kernel<<<1, 32, 0, s>>>(status, cap_cycles);
     return cudaGetLastError();
