@@ -1304,21 +1304,30 @@ temporal_sf_xl_kernel(float* __restrict__ D, TArgs a, XLTables tb, const __grid_
         // the mean-removed sequence into tensor memory: the even-bin transform and the power
         // sums take it from there instead of reading global memory again
         tmem_st_seq(t_seq, v);
-        // ---- pass 0, odd bins: DFT of g(t) e^{-i pi t / L}, |.|^2 parked in tensor memory;
-        //      pass 1, even bins: DFT of g (from tensor memory)
+        // ---- the three transforms through one copy of the code (the unrolled transform is
+        // most of the kernel's instructions): pass 0, odd bins: DFT of g(t) e^{-i pi t / L},
+        // |.|^2 parked in tensor memory; pass 1, even bins: DFT of g (from tensor memory);
+        // pass 2, the inverse of Z = |X_even|^2 + i |X_odd|^2 as conj(DFT(conj Z)), fed in the
+        // forward transforms' output order s1
 #pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
+        for (int pass = 0; pass < 3; ++pass) {
             if (pass == 0) {
 #pragma unroll
                 for (int u = 0; u < P; ++u) {
                     v[u] = cmul(cmul(v[u], c_i), w64[u]);          // zero past N stays zero
                     if ((u & 7) == 7) hoist_fence();
                 }
-            } else {
+            } else if (pass == 1) {
                 tmem_st_wait();
                 tmem_ld_seq(t_seq, v);
+            } else {
+                float o2[P];
+                tmem_st_wait();
+                tmem_ld32(t_odd, o2);
+#pragma unroll
+                for (int u = 0; u < P; ++u) v[u] = make_float2(cabs2(v[u]), -o2[u]);
             }
-            fft_cyclic3<L, false, 1, C::PAD>(v, i, i, 0, xs, tw1, twi, SyncBlock{});
+            fft_cyclic3<L, false, 1, C::PAD, true>(v, pass == 2 ? s1 : i, i, 0, xs, tw1, twi, SyncBlock{});
             if (pass == 0) {
                 float o2[P];
 #pragma unroll
@@ -1326,16 +1335,9 @@ temporal_sf_xl_kernel(float* __restrict__ D, TArgs a, XLTables tb, const __grid_
                 tmem_st32(t_odd, o2);
             }
         }
-        {
-            float o2[P];
-            tmem_st_wait();
-            tmem_ld32(t_odd, o2);
 #pragma unroll
-            for (int u = 0; u < P; ++u) v[u] = make_float2(cabs2(v[u]), o2[u]);
-        }
-        // ---- inverse of Z = |X_even|^2 + i |X_odd|^2 (input order s1), then Re C in cyclic
-        // order from the 2-for-1 split, into tensor memory
-        fft_cyclic3<L, true, 1, C::PAD, true>(v, s1, i, 0, xs, tw1, twi, SyncBlock{});
+        for (int u = 0; u < P; ++u) v[u].y = -v[u].y;   // conj: the inverse transform of Z
+        // ---- Re C in cyclic order from the 2-for-1 split, into tensor memory
 #pragma unroll
         for (int u = 0; u < P; ++u) xs[zs1 + T * u] = v[u];
         __syncthreads();
