@@ -538,22 +538,30 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
             if ((u & 7) == 7) hoist_fence();
         }
         sync();   // every read of the tile is done: xs becomes the exchange
-        fft_cyclic<L, false>(v, i, xs, xaddr, tw, sync);
+        // ---- one copy of the transform's code for the three: pass 0 the odd bins (|.|^2 parked
+        // in ab), pass 1 the even bins (g taken back from tensor memory), pass 2 the inverse of
+        // Z = |X_even|^2 + i |X_odd|^2 as conj(DFT(conj Z))
+#pragma unroll 1
+        for (int pass = 0; pass < 3; ++pass) {
+            if (pass == 1) {
+                tmem_st_wait();
+                tmem_ld_seq(t_seq, v);
+            } else if (pass == 2) {
 #pragma unroll
-        for (int u = 0; u < P; ++u) ab[(i + T * u) * QG + ql] = cabs2(v[u]);
-
-        // ---- even bins: L-point DFT of g, taken back from tensor memory
-        tmem_st_wait();
-        tmem_ld_seq(t_seq, v);
-        fft_cyclic<L, false>(v, i, xs, xaddr, tw, sync);
+                for (int u = 0; u < P; ++u) {
+                    v[u] = make_float2(cabs2(v[u]), -ab[(i + T * u) * QG + ql]);
+                    if ((u & 7) == 7) hoist_fence();
+                }
+            }
+            fft_cyclic<L, false>(v, i, xs, xaddr, tw, sync);
+            if (pass == 0) {
 #pragma unroll
-        for (int u = 0; u < P; ++u) {
-            v[u] = make_float2(cabs2(v[u]), ab[(i + T * u) * QG + ql]);
-            if ((u & 7) == 7) hoist_fence();
+                for (int u = 0; u < P; ++u) ab[(i + T * u) * QG + ql] = cabs2(v[u]);
+            }
         }
-
-        // ---- inverse transform of Z = |X_even|^2 + i |X_odd|^2, then Re C(m) into tensor memory
-        fft_cyclic<L, true>(v, i, xs, xaddr, tw, sync);
+#pragma unroll
+        for (int u = 0; u < P; ++u) v[u].y = -v[u].y;   // conj: the inverse transform of Z
+        // ---- Re C(m) into tensor memory
 #pragma unroll
         for (int u = 0; u < P; ++u) xs[(i + T * u) * QG + ql] = v[u];
         sync();
