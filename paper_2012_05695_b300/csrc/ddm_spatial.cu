@@ -670,7 +670,8 @@ namespace {
 // memory (mbarrier with a bounded wait) instead of 2-byte scattered loads, and the region
 // then serves as the transform's exchange buffer (XOR-swizzled, no padding).  Rows of 128
 // bytes or more are staged one copy per row with a 16-byte pad after each, so that the two
-// row pairs a warp reads sit on different banks.  ~70 KB per CTA, three CTAs per SM.
+// row pairs a warp reads sit on different banks.  Up to ~70 KB per CTA, three CTAs per SM
+// (37 KB and five at 512-pixel rows).
 template <int W, typename In>
 struct RowBulkShape {
     static constexpr int T = FftShape<W>::T, P = FftShape<W>::P;
@@ -679,7 +680,12 @@ struct RowBulkShape {
     static constexpr int ROW_STRIDE = BYTES_ROW + PAD;                   // staged row pitch
     static constexpr int P1 = 256 / T;
     static constexpr int P2 = 16384 / BYTES_ROW > 0 ? 16384 / BYTES_ROW : 1;
-    static constexpr int PAIRS = (P1 < P2 ? P1 : P2) < 1 ? 1 : (P1 < P2 ? P1 : P2);
+    static constexpr int PAIRS0 = (P1 < P2 ? P1 : P2) < 1 ? 1 : (P1 < P2 ? P1 : P2);
+    // 512-pixel rows: 8 row pairs per 128-thread CTA, five CTAs per SM (37 KB each) hide the
+    // staging wait better than 16 pairs at three per SM (512x512x1024 step one 0.683 ->
+    // 0.666 ms); the other widths keep the larger CTA (256 columns: 0.203 against 0.222 ms)
+    static constexpr int PAIRS = (W == 512 && PAIRS0 > 8) ? 8 : PAIRS0;
+    static constexpr int MIN_CTAS = W == 512 ? 5 : 3;
     static constexpr int NT = PAIRS * T;
     static constexpr size_t STAGE = (size_t)2 * 2 * PAIRS * ROW_STRIDE;  // frame rows + frame-0 rows
     static constexpr size_t XCH = (size_t)PAIRS * W * sizeof(float2);
@@ -688,7 +694,7 @@ struct RowBulkShape {
 };
 
 template <int W, typename In>
-__global__ void __launch_bounds__(RowBulkShape<W, In>::NT, 3)
+__global__ void __launch_bounds__(RowBulkShape<W, In>::NT, RowBulkShape<W, In>::MIN_CTAS)
 row_bulk_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H, size_t frame_stride,
                 int subtract_ref, const float2* __restrict__ tw_g, unsigned* status, int kc) {
     using C = RowBulkShape<W, In>;
