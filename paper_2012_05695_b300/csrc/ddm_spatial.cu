@@ -17,12 +17,32 @@
 // rounding relative to the changing part of the signal.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "ddm_fft.cuh"
 #include "ddm_internal.h"
 
 namespace ddm {
 namespace {
+
+// shared-memory address and bounded mbarrier wait (about two seconds of polling, then false),
+// for the staged copies of this file's kernels
+__device__ __forceinline__ uint32_t cvta_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init_s(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cvta_smem(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_s(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok) : "r"(cvta_smem(bar)), "r"(parity) : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > 4000000000LL) return false;
+    }
+}
 
 template <typename In>
 __device__ __forceinline__ float pixel_diff(const In* f, const In* r, size_t idx, bool sub);
@@ -109,20 +129,21 @@ row_r2c_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
 // grid: (Wh / QC, N); block: QC * T threads.  H = L points per column, QC columns.
 // COLRANGE: a kx-column range plan, whose output goes to the range's own store (SpecOut
 // put_col) and whose grid starts at column block bx0.
-template <int H, int QC, bool COLRANGE>
+// TMA: the block's H x QC values arrive by TMA copies (3-D tensor map over the row output as
+// float32 [N][H][2 Wh], boxes of 256 rows x 2 QC floats) into the exchange region, in its
+// [row][QC] layout, instead of per-thread strided loads.
+template <int H, int QC, bool COLRANGE, bool TMA = false>
 __global__ void __launch_bounds__(QC * FftShape<H>::T, (QC * FftShape<H>::T) >= 512 ? 1 : (QC * FftShape<H>::T) >= 256 ? 2 : 4)
 col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
-               const float2* __restrict__ tw_g, SpecOut out, int bx0) {
+               const float2* __restrict__ tw_g, SpecOut out, int bx0,
+               const __grid_constant__ CUtensorMap tmap, unsigned* status) {
     using S = FftShape<H>;
     constexpr int P = S::P, T = S::T, NT = QC * T;
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(1024) float2 smem[];
     float2* tw = smem;                                   // H entries (T > 1)
     float2* xs = smem + (T > 1 ? H : 0);                 // H * QC
 
     const int tid = threadIdx.x;
-    if constexpr (T > 1) {
-        for (int k = tid; k < H; k += NT) tw[k] = tw_g[k];
-    }
     const int ql = tid % QC;
     const int i = tid / QC;
     const int bx = COLRANGE ? (int)blockIdx.x + bx0 : (int)blockIdx.x;   // column block
@@ -133,8 +154,43 @@ col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
     const uint32_t off0 = (uint32_t)(i * Wh + kx), step = (uint32_t)(T * Wh);
 
     float2 v[P];
+    if constexpr (TMA) {
+        static_assert(H % 256 == 0 && (QC * 8) % 16 == 0 && ((T > 1 ? H : 0) * 8) % 128 == 0,
+                      "TMA staging: boxes of 256 rows, 16-byte rows, 128-byte aligned destinations");
+        __shared__ uint64_t bar;
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cvta_smem(&bar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cvta_smem(&bar)),
+                         "r"((uint32_t)(H * QC * sizeof(float2))) : "memory");
 #pragma unroll
-    for (int u = 0; u < P; ++u) v[u] = base[off0 + (uint32_t)u * step];
+            for (int b = 0; b < H / 256; ++b)
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4}], [%5];"
+                    ::"r"(cvta_smem(xs + (size_t)b * 256 * QC)), "l"(&tmap), "r"(2 * bx * QC), "r"(b * 256),
+                    "r"(t), "r"(cvta_smem(&bar)) : "memory");
+        }
+        if constexpr (T > 1) {
+            for (int k = tid; k < H; k += NT) tw[k] = tw_g[k];
+        }
+        __syncthreads();                                 // the twiddles; the barrier is armed
+        const bool ok = mbar_wait_s(&bar, 0);
+#pragma unroll
+        for (int u = 0; u < P; ++u) v[u] = ok ? xs[(i + T * u) * QC + ql] : make_float2(0.f, 0.f);
+        if (!ok) {
+            // report it (status bit 2); the copies get a last bounded chance to land before
+            // the region becomes the exchange
+            if (tid == 0) atomicOr(status, 2u);
+            mbar_wait_s(&bar, 0);
+        }
+    } else {
+        if constexpr (T > 1) {
+            for (int k = tid; k < H; k += NT) tw[k] = tw_g[k];
+        }
+#pragma unroll
+        for (int u = 0; u < P; ++u) v[u] = base[off0 + (uint32_t)u * step];
+    }
     __syncthreads();
     AddrInterleaved<QC> addr{ql};
     fft_cyclic<H, false>(v, i, xs, addr, tw, SyncBlock{});
@@ -276,8 +332,19 @@ cudaError_t launch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecO
         dim3 grid(nblk, N);
         const size_t smem = sizeof(float2) * ((S::T > 1 ? H : 0) + (size_t)H * QC);
         auto k = p->nk > 0 ? col_c2c_kernel<H, QC, true> : col_c2c_kernel<H, QC, false>;
+        CUtensorMap tmap;
+        memset(&tmap, 0, sizeof(tmap));
+        if constexpr (QC == 16 && H % 256 == 0) {
+            // TMA staging: 16-byte rows and frames (Wh, frame stride even), aligned spectrum
+            const cuuint64_t dims[3] = {(cuuint64_t)(2 * Wh), (cuuint64_t)H, (cuuint64_t)N};
+            const cuuint64_t strides[2] = {(cuuint64_t)Wh * sizeof(float2), (cuuint64_t)frame_stride * sizeof(float2)};
+            const cuuint32_t box[3] = {(cuuint32_t)(2 * QC), 256u, 1u};
+            if (Wh % 2 == 0 && frame_stride % 2 == 0 && reinterpret_cast<uintptr_t>(spec) % 16 == 0 &&
+                encode_f32_tensor_map(&tmap, spec, 3, dims, strides, box))
+                k = p->nk > 0 ? col_c2c_kernel<H, QC, true, true> : col_c2c_kernel<H, QC, false, true>;
+        }
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, QC * S::T, smem, s>>>(spec, Wh, frame_stride, p->tw_col, out, bx0);
+        k<<<grid, QC * S::T, smem, s>>>(spec, Wh, frame_stride, p->tw_col, out, bx0, tmap, p->dev_status);
         return cudaGetLastError();
     };
     if (Wh >= 16) return go(std::integral_constant<int, 16>{});
@@ -426,7 +493,6 @@ ddm_status launch_spatial(const ddm_plan_s* p, const void* frames, float2* spec,
 namespace ddm {
 namespace {
 
-__device__ __forceinline__ uint32_t cvta_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
@@ -440,21 +506,6 @@ __device__ __forceinline__ void st_cluster_f2(uint32_t local_addr, uint32_t rank
     uint32_t remote;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
     asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(remote), "f"(v.x), "f"(v.y) : "memory");
-}
-__device__ __forceinline__ void mbar_init_s(uint64_t* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cvta_smem(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_wait_s(uint64_t* bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok) : "r"(cvta_smem(bar)), "r"(parity) : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > 4000000000LL) return false;
-    }
 }
 
 template <int S, int CL>
