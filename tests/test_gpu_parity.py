@@ -68,6 +68,26 @@ def test_spatial_fft_fused_cluster_path_matches_oracle(S, N, dtype):
     assert plan.last_device_status() == 0
 
 
+@pytest.mark.parametrize("H,W,N,dtype", [(512, 512, 4, "u16"), (256, 64, 3, "f32"), (600, 800, 2, "u16")])
+def test_spatial_fft_unaligned_spectrum_matches_aligned(H, W, N, dtype):
+    """A caller's spectrum that is 8-byte but not 16-byte aligned takes the column passes'
+    per-thread loads instead of their TMA staging (which needs 16-byte rows and base); both
+    do the same arithmetic, so the spectra agree bit for bit."""
+    import torch
+    frames = to_device(_frames(N, H, W, dtype, seed=H + W))
+    plan = ddm.Plan(H, W, N, dtype=dtype)
+    n = 2 * N * plan.n_q
+    aligned = torch.empty(n, dtype=torch.float32, device="cuda")
+    buf = torch.empty(n + 2, dtype=torch.float32, device="cuda")
+    shifted = buf[2:]
+    assert aligned.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 8
+    plan.spatial_fft(frames, aligned)
+    plan.spatial_fft(frames, shifted)
+    torch.cuda.synchronize()
+    assert plan.last_device_status() == 0
+    assert torch.equal(aligned, shifted)
+
+
 def test_spatial_fft_without_reference_subtraction():
     import torch
     H, W, N = 64, 32, 3
