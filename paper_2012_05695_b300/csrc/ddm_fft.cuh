@@ -470,39 +470,6 @@ __device__ __forceinline__ void fft_cyclic(float2 (&v)[FftShape<L>::P], int i, f
     }
 }
 
-// As fft_cyclic, for T == P (one pass-2 transform per thread), with the exchange done in
-// two halves through a float buffer of (L + L/T) * QT floats: real parts, then imaginary
-// parts.  Half the scratch of fft_cyclic (for the same addr layout, in float units), two
-// more barriers, no extra registers: the thread's new real parts land in the slots whose
-// old real parts have already been written out.
-template <int L, bool INV, typename Addr, typename Sync>
-__device__ __forceinline__ void fft_cyclic_split(float2 (&v)[FftShape<L>::P], int i, float* xf,
-                                                 Addr addr, const float2* tw, Sync sync) {
-    constexpr int P = FftShape<L>::P;
-    constexpr int T = FftShape<L>::T;
-    static_assert(T == P, "split exchange: one pass-2 transform per thread");
-    dft_reg<P, INV>(v);
-#pragma unroll
-    for (int k1 = 1; k1 < P; ++k1) {
-        const float2 w = tw[k1 * T + i];
-        v[k1] = INV ? cmul_conj(v[k1], w) : cmul(v[k1], w);
-        if ((k1 & 7) == 7) hoist_fence();
-    }
-#pragma unroll
-    for (int k1 = 0; k1 < P; ++k1) xf[addr.template at<T>(k1, i)] = v[k1].x;
-    sync();
-#pragma unroll
-    for (int ip = 0; ip < T; ++ip) v[ip].x = xf[addr.template at<T>(i, ip)];
-    sync();
-#pragma unroll
-    for (int k1 = 0; k1 < P; ++k1) xf[addr.template at<T>(k1, i)] = v[k1].y;
-    sync();
-#pragma unroll
-    for (int ip = 0; ip < T; ++ip) v[ip].y = xf[addr.template at<T>(i, ip)];
-    sync();
-    dft_reg<T, INV>(v);
-}
-
 // ------------------------------------------------------------------ three-pass FFT
 // L = P * T with T = P * R threads per transform (R <= P): lengths 2048 .. 32768 at P = 32.
 // Pass 1: P-point DFT over u inside each thread (data x[i + T u]), twiddle w_L^{i k1}; one
