@@ -131,9 +131,11 @@ row_r2c_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
 // put_col) and whose grid starts at column block bx0.
 // TMA: the block's H x QC values arrive by TMA copies (3-D tensor map over the row output as
 // float32 [N][H][2 Wh], boxes of 256 rows x 2 QC floats) into the exchange region, in its
-// [row][QC] layout, instead of per-thread strided loads.
+// [row][QC] layout, instead of per-thread strided loads.  At H = 512 the TMA instance asks for
+// three CTAs per SM (80 registers): with the loads gone its registers allow it, and three
+// CTAs hide the copies better than two (512x512x1024 step one 0.655 -> 0.622 ms).
 template <int H, int QC, bool COLRANGE, bool TMA = false>
-__global__ void __launch_bounds__(QC * FftShape<H>::T, (QC * FftShape<H>::T) >= 512 ? 1 : (QC * FftShape<H>::T) >= 256 ? 2 : 4)
+__global__ void __launch_bounds__(QC * FftShape<H>::T, (QC * FftShape<H>::T) >= 512 ? 1 : (QC * FftShape<H>::T) >= 256 ? (TMA && H == 512 ? 3 : 2) : 4)
 col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
                const float2* __restrict__ tw_g, SpecOut out, int bx0,
                const __grid_constant__ CUtensorMap tmap, unsigned* status) {
@@ -344,6 +346,7 @@ cudaError_t launch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecO
                 k = p->nk > 0 ? col_c2c_kernel<H, QC, true, true> : col_c2c_kernel<H, QC, false, true>;
         }
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
         k<<<grid, QC * S::T, smem, s>>>(spec, Wh, frame_stride, p->tw_col, out, bx0, tmap, p->dev_status);
         return cudaGetLastError();
     };
