@@ -18,19 +18,24 @@
 // The last kd lags (N - m <= kd pairs) are taken directly from Eq. 1 by differences
 // instead: few terms, and no cancellation against the much larger power sums.
 //
-// Two kernels share this arithmetic:
-//  * L >= 512 (the production sizes): 512-thread CTAs split into independent groups (two
-//    of 256 threads at L = 1024, four of 128 at L = 512).  A group owns QG = 8 consecutive
-//    stored wave vectors at a time; their tile ([L frames][QG] complex) arrives by TMA bulk
-//    tensor copies, the group's threads synchronise on a named barrier of their own, so the
-//    groups drift apart and one group's copy wait hides behind the others' transforms.  The next tile's copy is issued
-//    before the D rows are staged, and the D rows leave shared memory by bulk async copies.
-//    The tile is copied twice at L = 1024 (once from DRAM, once from L2 for the power
-//    sums: the odd-bin transform exchanges through the spare buffer, in halves, so the tile
-//    survives for the even-bin one) and three times at L = 512.
-//  * L <= 256: one group per CTA, each thread loads its own samples (every warp load
-//    instruction covers whole 128-byte row segments F[t][q0 .. q0+QT) of the [t][q]
-//    spectrum).
+// Four kernel families share this arithmetic; each thread holds 32 samples of a transform in
+// the cyclic layout (thread i of T holds t = i + T u; fewer below L = 32), and the
+// mean-removed sequence waits in tensor memory (tcgen05.st / ld, 128 columns per thread)
+// between the transforms, so every tile is read from global memory once (below L = 32 it is
+// read again from L2):
+//  * L = 512, 1024 (the production sizes): 512-thread CTAs split into four independent
+//    groups of 128 threads, each owning QG = 128 / T consecutive stored wave vectors at a
+//    time; the tile ([L frames][QG] complex) arrives by TMA bulk tensor copies, each group
+//    synchronises on a named barrier of its own, so the groups drift apart and one group's
+//    copy wait hides behind the others' transforms.  Two-pass transforms, the three of them
+//    through one copy of the code; the next tile's copy is issued after the partner step and
+//    the D rows leave shared memory by bulk async copies.
+//  * L = 2048 .. 8192: 256-thread CTAs (512 at 8192), three-pass transforms, TMA tiles of
+//    (threads per CTA) / T wave vectors (from a blocked copy [q/16][t][16] for large n_q).
+//  * L = 16384: one wave vector per 512-thread CTA; its sequence arrives by TMA through a
+//    ring of 16 stages; the three transforms through one copy of the code.
+//  * L <= 256: 256-thread CTAs, each thread loads its own samples (every warp load covers
+//    whole row segments F[t][q0 .. q0+QT) of the [t][q] spectrum); D rows stored by warps.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
