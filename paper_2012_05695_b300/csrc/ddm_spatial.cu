@@ -133,9 +133,11 @@ row_r2c_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
 // float32 [N][H][2 Wh], boxes of 256 rows x 2 QC floats) into the exchange region, in its
 // [row][QC] layout, instead of per-thread strided loads.  At H = 512 the TMA instance asks for
 // three CTAs per SM (80 registers): with the loads gone its registers allow it, and three
-// CTAs hide the copies better than two (512x512x1024 step one 0.655 -> 0.622 ms).
+// CTAs hide the copies better than two (512x512x1024 step one 0.655 -> 0.622 ms).  At
+// H = 1024 the block is 8 columns (256 threads, 72 KB), three CTAs per SM, in place of one
+// 512-thread CTA of 16 columns (1024x1024x512 step one 1.60 -> 1.31 ms).
 template <int H, int QC, bool COLRANGE, bool TMA = false>
-__global__ void __launch_bounds__(QC * FftShape<H>::T, (QC * FftShape<H>::T) >= 512 ? 1 : (QC * FftShape<H>::T) >= 256 ? (TMA && H == 512 ? 3 : 2) : 4)
+__global__ void __launch_bounds__(QC * FftShape<H>::T, (QC * FftShape<H>::T) >= 512 ? 1 : (QC * FftShape<H>::T) >= 256 ? (TMA && (H == 512 || H == 1024) ? 3 : 2) : 4)
 col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
                const float2* __restrict__ tw_g, SpecOut out, int bx0,
                const __grid_constant__ CUtensorMap tmap, unsigned* status) {
@@ -336,7 +338,7 @@ cudaError_t launch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecO
         auto k = p->nk > 0 ? col_c2c_kernel<H, QC, true> : col_c2c_kernel<H, QC, false>;
         CUtensorMap tmap;
         memset(&tmap, 0, sizeof(tmap));
-        if constexpr (QC == 16 && H % 256 == 0) {
+        if constexpr ((QC == 16 || (H == 1024 && QC == 8)) && H % 256 == 0) {
             // TMA staging: 16-byte rows and frames (Wh, frame stride even), aligned spectrum
             const cuuint64_t dims[3] = {(cuuint64_t)(2 * Wh), (cuuint64_t)H, (cuuint64_t)N};
             const cuuint64_t strides[2] = {(cuuint64_t)Wh * sizeof(float2), (cuuint64_t)frame_stride * sizeof(float2)};
@@ -350,6 +352,7 @@ cudaError_t launch_cols(const ddm_plan_s* p, float2* spec, cudaStream_t s, SpecO
         k<<<grid, QC * S::T, smem, s>>>(spec, Wh, frame_stride, p->tw_col, out, bx0, tmap, p->dev_status);
         return cudaGetLastError();
     };
+    if (H == 1024 && Wh >= 16) return go(std::integral_constant<int, 8>{});   // 3 CTAs per SM
     if (Wh >= 16) return go(std::integral_constant<int, 16>{});
     if (Wh == 8) return go(std::integral_constant<int, 8>{});
     if (Wh == 4) return go(std::integral_constant<int, 4>{});

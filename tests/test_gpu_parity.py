@@ -68,7 +68,8 @@ def test_spatial_fft_fused_cluster_path_matches_oracle(S, N, dtype):
     assert plan.last_device_status() == 0
 
 
-@pytest.mark.parametrize("H,W,N,dtype", [(512, 512, 4, "u16"), (256, 64, 3, "f32"), (600, 800, 2, "u16")])
+@pytest.mark.parametrize("H,W,N,dtype", [(512, 512, 4, "u16"), (256, 64, 3, "f32"), (600, 800, 2, "u16"),
+                                         (1024, 256, 2, "f32")])
 def test_spatial_fft_unaligned_spectrum_matches_aligned(H, W, N, dtype):
     """A caller's spectrum that is 8-byte but not 16-byte aligned takes the column passes'
     per-thread loads instead of their TMA staging (which needs 16-byte rows and base); both
