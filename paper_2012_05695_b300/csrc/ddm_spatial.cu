@@ -135,9 +135,10 @@ row_r2c_kernel(const In* __restrict__ frames, float2* __restrict__ spec, int H,
 // three CTAs per SM (80 registers): with the loads gone its registers allow it, and three
 // CTAs hide the copies better than two (512x512x1024 step one 0.655 -> 0.622 ms).  At
 // H = 1024 the block is 8 columns (256 threads, 72 KB), three CTAs per SM, in place of one
-// 512-thread CTA of 16 columns (1024x1024x512 step one 1.60 -> 1.31 ms).
+// 512-thread CTA of 16 columns (1024x1024x512 step one 1.60 -> 1.31 ms); at H = 256 six
+// 128-thread CTAs per SM instead of four (256x256x1024 0.20 -> 0.195 ms).
 template <int H, int QC, bool COLRANGE, bool TMA = false>
-__global__ void __launch_bounds__(QC * FftShape<H>::T, (QC * FftShape<H>::T) >= 512 ? 1 : (QC * FftShape<H>::T) >= 256 ? (TMA && (H == 512 || H == 1024) ? 3 : 2) : 4)
+__global__ void __launch_bounds__(QC * FftShape<H>::T, (QC * FftShape<H>::T) >= 512 ? 1 : (QC * FftShape<H>::T) >= 256 ? (TMA && (H == 512 || H == 1024) ? 3 : 2) : (TMA && H == 256 ? 6 : 4))
 col_c2c_kernel(float2* __restrict__ spec, int Wh, size_t frame_stride,
                const float2* __restrict__ tw_g, SpecOut out, int bx0,
                const __grid_constant__ CUtensorMap tmap, unsigned* status) {
