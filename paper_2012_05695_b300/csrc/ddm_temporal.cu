@@ -211,7 +211,9 @@ struct GShape {
     //        D rows [QG][DS]
     //   red: row totals of the prefix sums; the mean's warp partials
     //   fix: warp partials of the FP64-fixup lags
-    // (the mean-removed sequence and Re C live in tensor memory)
+    // (the mean-removed sequence and Re C live in tensor memory; |X_odd|^2 waits in shared
+    // memory: parked in tensor memory it measured 2 % slower, 0.782 against 0.764 ms at
+    // 512^2 x 1024)
     static constexpr size_t G_XS = (size_t)(L + L / T) * QG * sizeof(float2);
     static constexpr size_t G_AB = cmax(cmax((size_t)L * QG * sizeof(float), (size_t)QG * DS * sizeof(float)),
                                         (size_t)(L + L / T) * QG * sizeof(float));
@@ -360,7 +362,10 @@ __device__ __forceinline__ void long_tmem_free(uint32_t tmem) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(NCOLS) : "memory");
 }
 
-template <int LOG2L, int NGROUPS, bool FIXUP>
+// FULL: the instance for N = L (hence kd = T): every bound that depends on N is a
+// compile-time constant, so the per-sample range tests fold away (512^2 x 1024:
+// 0.761 -> 0.751 ms; 512^2 x 512: 0.363 -> 0.350 ms, bitwise the same D).
+template <int LOG2L, int NGROUPS, bool FIXUP, bool FULL>
 __global__ void __launch_bounds__(GShape<LOG2L, NGROUPS>::NT, 1)
 temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUtensorMap tmap) {
     using C = GShape<LOG2L, NGROUPS>;
@@ -415,8 +420,8 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
     const int lane = tid & 31, wg = tg >> 5;
     const SyncGroup<GT> sync{bar_id};
     const AddrPaddedInterleaved<QG, T> xaddr{ql};
-    const int N = a.N;
-    const int kd = a.kd;
+    const int N = FULL ? L : a.N;
+    const int kd = FULL ? T : a.kd;
     const int64_t q0 = a.q0, q1 = a.q1;
     const int64_t gstride = (int64_t)gridDim.x * NG;
     bool timed_out = false;
@@ -545,8 +550,9 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
         sync();   // every read of the tile is done: xs becomes the exchange
         // ---- one copy of the transform's code for the three: pass 0 the odd bins (|.|^2 parked
         // in ab), pass 1 the even bins (g taken back from tensor memory), pass 2 the inverse of
-        // Z = |X_even|^2 + i |X_odd|^2 as conj(DFT(conj Z)); the FP64-fixup tier unrolls the
-        // three (1.20 -> 1.16 ms at 512^2 x 1024: the loop costs it more than it saves)
+        // Z = |X_even|^2 + i |X_odd|^2 as DFT(conj Z), the conjugate of the inverse (folded into
+        // the partner step below); the FP64-fixup tier unrolls the three (1.20 -> 1.16 ms at
+        // 512^2 x 1024: the loop costs it more than it saves)
 #pragma unroll (FIXUP ? 3 : 1)
         for (int pass = 0; pass < 3; ++pass) {
             if (pass == 1) {
@@ -565,9 +571,9 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
                 for (int u = 0; u < P; ++u) ab[(i + T * u) * QG + ql] = cabs2(v[u]);
             }
         }
-#pragma unroll
-        for (int u = 0; u < P; ++u) v[u].y = -v[u].y;   // conj: the inverse transform of Z
-        // ---- Re C(m) into tensor memory
+        // ---- Re C(m) into tensor memory.  v = conj(z), z the unnormalised inverse DFT of Z:
+        // the partner formula below is the one of the file header with z = conj(v),
+        // z(L - m) = conj(xs[L - m])
 #pragma unroll
         for (int u = 0; u < P; ++u) xs[(i + T * u) * QG + ql] = v[u];
         sync();
@@ -577,10 +583,10 @@ temporal_sf_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUten
 #pragma unroll
             for (int u = 0; u < P; ++u) {
                 const int m = i + T * u;
-                const float2 z = v[u];
-                const float2 zr = xs[((L - m) & (L - 1)) * QG + ql];
+                const float2 y = v[u];
+                const float2 yr = xs[((L - m) & (L - 1)) * QG + ql];
                 const float2 w = tw2[m];                   // (cos(pi m/L), -sin(pi m/L))
-                rc[u] = scale * ((z.x + zr.x) + w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
+                rc[u] = scale * ((y.x + yr.x) - w.x * (y.y + yr.y) - w.y * (y.x - yr.x));
                 if ((u & 7) == 7) hoist_fence();
             }
             tmem_st32(t_rec, rc);
@@ -1883,13 +1889,14 @@ void fill_args(TArgs& a, const ddm_plan_s* p, float* D, int qt) {
 template <int LOG2L, bool FIXUP, int NGROUPS>
 ddm_status launch_grouped(const ddm_plan_s* p, const float2* spec, float* D, cudaStream_t s) {
     using C = GShape<LOG2L, NGROUPS>;
+    const bool full = p->d.N == C::L && p->kd == C::T;   // the FULL instance's premise
     if ((reinterpret_cast<uintptr_t>(spec) & 15) != 0) return DDM_ERR_INVALID_ARG;
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof(tmap));
     if (!make_spectrum_map(&tmap, spec, p->n_q, p->d.N, C::QG)) return DDM_ERR_CUDA;
     TArgs a;
     fill_args(a, p, D, C::QG);
-    auto k = temporal_sf_kernel<LOG2L, NGROUPS, FIXUP>;
+    auto k = full ? temporal_sf_kernel<LOG2L, NGROUPS, FIXUP, true> : temporal_sf_kernel<LOG2L, NGROUPS, FIXUP, false>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
         cudaSuccess)
         return DDM_ERR_CUDA;
