@@ -796,7 +796,10 @@ struct LTables {
     const float2* w64;       // exp(-i pi u / 32), u < 32
 };
 
-template <int LOG2L, bool FIXUP>
+// FULL: the instance for N = L (hence kd = 32), as for the grouped kernel above (random
+// spectrum, kernel alone: 512^2 x 2048 2.645 -> 2.535 ms, x 4096 5.754 -> 5.494 ms, FP64-fixup
+// tier 7.33 -> 6.76 ms, x 8192 12.92 -> 12.54 ms; bitwise the same D).
+template <int LOG2L, bool FIXUP, bool FULL>
 __global__ void __launch_bounds__(LShape<LOG2L>::NT, LShape<LOG2L>::CTAS_PER_SM)
 temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ CUtensorMap tmap,
                         LTables tb) {
@@ -849,7 +852,7 @@ temporal_sf_long_kernel(float* __restrict__ D, TArgs a, const __grid_constant__ 
     static_assert(((T >> ZS) & 7) == 0, "zslot(j + T u) = zslot(j) + T u");
     const int zs1 = zslot(s1), zsi = zslot(i);
     const TwiddleQuarter<L> tw1{twq};
-    const int N = a.N, kd = a.kd;
+    const int N = FULL ? L : a.N, kd = FULL ? 32 : a.kd;
     const int64_t q0 = a.q0, q1 = a.q1;
     bool timed_out = false;
     float chk = 0.f;
@@ -1179,6 +1182,10 @@ struct XLTables {
     const float2* w64;       // exp(-i pi u / 32), u < 32
 };
 
+// FULL: the instance for N = L (hence kd = 32), as for the grouped kernel above
+// (256^2 x 16384 through ddm_temporal_sf, blocked copy included: 8.47 -> 7.62 ms; bitwise the
+// same D).
+template <bool FULL>
 __global__ void __launch_bounds__(XLShape::NT, 1)
 temporal_sf_xl_kernel(float* __restrict__ D, TArgs a, XLTables tb, const __grid_constant__ CUtensorMap tmap) {
     using C = XLShape;
@@ -1216,7 +1223,7 @@ temporal_sf_xl_kernel(float* __restrict__ D, TArgs a, XLTables tb, const __grid_
     static_assert(((T >> 5) & 15) == 0, "zslot(j + T u) = zslot(j) + T u");
     const int zs1 = zslot(s1), zsi = zslot(i);
     const TwiddleTwoLevel<L> tw1{lo, hi};
-    const int N = a.N, kd = a.kd;
+    const int N = FULL ? L : a.N, kd = FULL ? 32 : a.kd;
     const int m_lo = N - kd;
     const int m_tail = m_lo + ((i - m_lo) % T + T) % T;    // this thread's trailing lag, if < N
     float chk = 0.f;
@@ -1921,7 +1928,8 @@ ddm_status launch_long(const ddm_plan_s* p, const float2* spec, float* D, cudaSt
     TArgs a;
     fill_args(a, p, D, C::QG);
     a.blocked = blk != nullptr;
-    auto k = temporal_sf_long_kernel<LOG2L, FIXUP>;
+    const bool full = p->d.N == C::L && p->kd == 32;     // the FULL instance's premise
+    auto k = full ? temporal_sf_long_kernel<LOG2L, FIXUP, true> : temporal_sf_long_kernel<LOG2L, FIXUP, false>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
         cudaSuccess)
         return DDM_ERR_CUDA;
@@ -1954,7 +1962,8 @@ ddm_status launch_xl(const ddm_plan_s* p, const float2* spec, float* D, cudaStre
     TArgs a;
     fill_args(a, p, D, 1);
     a.blocked = blk != nullptr;
-    auto k = temporal_sf_xl_kernel;
+    const bool full = p->d.N == C::L && p->kd == 32;     // the FULL instance's premise
+    auto k = full ? temporal_sf_xl_kernel<true> : temporal_sf_xl_kernel<false>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES) !=
         cudaSuccess)
         return DDM_ERR_CUDA;
