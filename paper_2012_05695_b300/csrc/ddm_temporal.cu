@@ -36,6 +36,9 @@
 //    ring of 16 stages; the three transforms through one copy of the code.
 //  * L <= 256: 256-thread CTAs, each thread loads its own samples (every warp load covers
 //    whole row segments F[t][q0 .. q0+QT) of the [t][q] spectrum); D rows stored by warps.
+// From L = 512 on, every kernel also has an instance for N = L (a stack that fills the
+// transform length, kd = min(32, N / 32) with it), in which every bound that depends on N is
+// a compile-time constant; the launchers pick it whenever the plan's N and kd match.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
