@@ -225,7 +225,9 @@ ddm_status ddm_spatial_fft(ddm_plan p, const void* frames, float* spectrum, void
  *   D        [n_q][N] float32, device, written
  * Per wave vector q: remove the time mean of F(q, .) (D is unchanged by any constant),
  * P1(m) = sum_{t < N-m} |F|^2 and P2(m) = sum_{t >= m} |F|^2 (Eqs. B1, B3), Re C(m) by the
- * zero-padded transform in time (Eq. B4), D = (P1 + P2 - 2 Re C) / (N - m). */
+ * zero-padded transform in time (Eq. B4), D = (P1 + P2 - 2 Re C) / (N - m).
+ * Performance note: a power-of-two N >= 512 fills the transform length exactly and runs a
+ * kernel instance with N fixed at compile time (the same D, 1-10 % faster). */
 ddm_status ddm_temporal_sf(ddm_plan p, const float* spectrum, float* D, void* stream);
 
 /* The paper's WITHOUT_FT scheme (Sec. 2; the comparison method of its Figs. 1 and 3) on
