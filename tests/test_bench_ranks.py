@@ -54,3 +54,23 @@ def test_fit_label_targets_invert_the_network_head():
     t = bench.head_targets(phys, p8)
     np.testing.assert_allclose(t[:, [0, 1, 3]], o[:, [0, 1, 3]], rtol=0, atol=1e-12)
     np.testing.assert_allclose(t[:, 2], phys[:, 2], rtol=0, atol=0)
+
+
+def test_traffic_is_reported_only_for_the_profiled_source(tmp_path, monkeypatch):
+    """The bench line's roofline `traffic` comes from the committed ncu summary only while
+    that summary's source hash is the hash of the step-two sources being built; any edit of
+    those sources turns it into null."""
+    csrc = tmp_path / "paper_2012_05695_b300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "ddm_temporal.cu").write_text("// kernel v1\n")
+    (csrc / "ddm_fft.cuh").write_text("// fft\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    prof = tmp_path / "profiles" / "temporal_sf_512x512x1024.md"
+    prof.write_text(f"# t\n\nsource_sha256_16: {bench.kernel_source_hash()}\n"
+                    "dram_bytes_per_launch: 1586487552\n")
+    assert bench.profiled_traffic() == 1586487552.0
+    (csrc / "ddm_temporal.cu").write_text("// kernel v2\n")
+    assert bench.profiled_traffic() is None
+    prof.unlink()
+    assert bench.profiled_traffic() is None
