@@ -127,7 +127,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("ddm_temporal.cu", "ddm_fft.cuh"):
+    for name in ("ddm_temporal.cu", "ddm_fft.cuh", "ddm_internal.h"):
         with open(os.path.join(ROOT, "paper_2012_05695_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

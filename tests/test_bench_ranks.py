@@ -64,6 +64,7 @@ def test_traffic_is_reported_only_for_the_profiled_source(tmp_path, monkeypatch)
     csrc.mkdir(parents=True)
     (csrc / "ddm_temporal.cu").write_text("// kernel v1\n")
     (csrc / "ddm_fft.cuh").write_text("// fft\n")
+    (csrc / "ddm_internal.h").write_text("// internal\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     (tmp_path / "profiles").mkdir()
     prof = tmp_path / "profiles" / "temporal_sf_512x512x1024.md"
